@@ -1,0 +1,179 @@
+"""FP64 CPU oracle for the two-component Shan-Chen lattice Boltzmann step.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, ``__graft_entry__.smoke``
+and the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA path (``paper_1112_5547_gb300``) and never imports it.
+
+The arithmetic lives in ``sc_oracle.c`` (plain C, FP64, no fused multiply-add);
+this module builds it with gcc and wraps it with ctypes + numpy.  Each function
+follows the paper's Sec. 2.1 (Eq. eq:be, the moment definitions, Eq. FORCE, the
+isotropy sums) and the F dt/2 momentum shift of Sec. 2.3; see the C file's
+header for the formulas.
+
+Array conventions (numpy, float64):
+  * scalar fields: shape (nz, ny, nx) (x fastest), or (ny, nx) for D2Q9;
+  * velocity fields: shape field_shape + (3,) (component last);
+  * populations: opaque node-major array of shape (N, 2, Q).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sc_oracle.c")
+_LIB = os.path.join(_HERE, "libsc_oracle.so")
+
+D2Q9 = 0
+D3Q19 = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile sc_oracle.c into libsc_oracle.so next to it (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared",
+           "-fPIC", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double),
+                ("G", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(_Params)
+        lib.oracle_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
+        lib.oracle_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp]
+        lib.oracle_init.argtypes = [pp, dp, dp, dp, dp]
+        lib.oracle_step.argtypes = [pp, dp, dp, ctypes.c_int]
+        lib.oracle_moments.argtypes = [pp, dp, dp, dp, dp, dp]
+        lib.oracle_total_momentum.argtypes = [pp, dp, dp]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().oracle_set_num_threads(int(n))
+
+
+def lattice(lat: int):
+    """Velocity set of the oracle: (c as (Q, 3) int array, w as (Q,) float64)."""
+    lib = _load()
+    c = (ctypes.c_int * (19 * 3))()
+    w = np.zeros(19)
+    q = lib.oracle_lattice(lat, c, _ptr(w))
+    return np.array(c[: q * 3], dtype=np.int64).reshape(q, 3), w[:q].copy()
+
+
+def equilibrium(lat: int, rho: float, u) -> np.ndarray:
+    """Second-order truncated Maxwellian of one node (Sec. 2.1)."""
+    lib = _load()
+    u3 = np.zeros(3)
+    u3[: len(u)] = u
+    feq = np.zeros(19)
+    q = lib.oracle_equilibrium(lat, float(rho), _ptr(u3), _ptr(feq))
+    return feq[:q].copy()
+
+
+class OracleSC:
+    """One lattice of the two-component Shan-Chen model, advanced by the oracle.
+
+    ``lat`` is D2Q9 (0) or D3Q19 (1); ``shape`` is (ny, nx) for D2Q9 or
+    (nz, ny, nx) for D3Q19; tau_A, tau_B, G as in Eq. eq:be / Eq. FORCE.
+    """
+
+    def __init__(self, lat: int, shape, tau_A: float, tau_B: float, G: float):
+        self.lat = int(lat)
+        shape = tuple(int(s) for s in shape)
+        if self.lat == D2Q9:
+            assert len(shape) == 2
+            ny, nx = shape
+            nz = 1
+        else:
+            assert len(shape) == 3
+            nz, ny, nx = shape
+        self.shape = shape
+        self.p = _Params(self.lat, nx, ny, nz, float(tau_A), float(tau_B), float(G))
+        self.N = nx * ny * nz
+        self.Q = 9 if self.lat == D2Q9 else 19
+        self.f = np.zeros((self.N, 2, self.Q))
+        self._tmp = np.zeros_like(self.f)
+        self.t = 0
+
+    def init(self, rhoA, rhoB, u=None):
+        """Populations at rest-frame equilibrium f^eq(rho_s, u) (u=None: rest)."""
+        lib = _load()
+        rA = np.ascontiguousarray(rhoA, dtype=np.float64).reshape(-1)
+        rB = np.ascontiguousarray(rhoB, dtype=np.float64).reshape(-1)
+        assert rA.size == self.N and rB.size == self.N
+        uu = None
+        if u is not None:
+            u = np.asarray(u, dtype=np.float64)
+            uu = np.zeros((self.N, 3))
+            d = u.shape[-1]
+            uu[:, :d] = u.reshape(self.N, d)
+        rc = lib.oracle_init(ctypes.byref(self.p), _ptr(rA), _ptr(rB), _ptr(uu), _ptr(self.f))
+        if rc != 0:
+            raise ValueError("oracle_init rejected the parameters")
+        self.t = 0
+        return self
+
+    def step(self, nsteps: int = 1):
+        rc = _load().oracle_step(ctypes.byref(self.p), _ptr(self.f), _ptr(self._tmp), int(nsteps))
+        if rc != 0:
+            raise ValueError("oracle_step failed (%d)" % rc)
+        self.t += int(nsteps)
+        return self
+
+    def moments(self):
+        """(rho_A, rho_B, u_phys (shape + (3,)), p) of the current populations."""
+        lib = _load()
+        rA = np.zeros(self.N)
+        rB = np.zeros(self.N)
+        u = np.zeros((self.N, 3))
+        pr = np.zeros(self.N)
+        rc = lib.oracle_moments(ctypes.byref(self.p), _ptr(self.f), _ptr(rA), _ptr(rB), _ptr(u),
+                                _ptr(pr))
+        if rc != 0:
+            raise ValueError("oracle_moments failed")
+        s = self.shape
+        return rA.reshape(s), rB.reshape(s), u.reshape(s + (3,)), pr.reshape(s)
+
+    def total_momentum(self) -> np.ndarray:
+        out = np.zeros(3)
+        _load().oracle_total_momentum(ctypes.byref(self.p), _ptr(self.f), _ptr(out))
+        return out
+
+
+if __name__ == "__main__":  # pragma: no cover - manual build helper
+    print(build(force="--force" in sys.argv))

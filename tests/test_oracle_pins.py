@@ -1,0 +1,350 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them re-types the oracle's
+own formulas: they check exact rational sums, conservation laws, symmetries,
+an exact rational brute-force trace, closed-form decay rates and the paper's
+own worked example, chosen so that a dropped term, a wrong sign or index, or
+a transposed operand in the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1112_5547_gb300 import inputs
+from tests import exact_sc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CS2 = 1.0 / 3.0
+G0 = 2.4 / 1.04  # G * rho_tot = 2.4 with rho_hi + rho_lo = 1.04
+
+
+def _frac_weights(w):
+    return [Fraction(x).limit_denominator(100) for x in w]
+
+
+# --- lattice tables: isotropy sums of Sec. 2.1, in exact rationals ----------
+@pytest.mark.parametrize("lat,q,d", [(0, 9, 2), (1, 19, 3)])
+def test_lattice_isotropy_exact(oracle_mod, lat, q, d):
+    c, w = oracle_mod.lattice(lat)
+    assert c.shape == (q, 3)
+    wf = _frac_weights(w)
+    for wi, wr in zip(w, wf):
+        assert float(wr) == wi  # stored double is the rational's rounding
+    # distinct velocities, closed under c -> -c with equal weights
+    vecs = [tuple(v) for v in c]
+    assert len(set(vecs)) == q
+    for v, wi in zip(vecs, wf):
+        assert wf[vecs.index(tuple(-x for x in v))] == wi
+    if d == 2:
+        assert all(v[2] == 0 for v in vecs)
+    cs2 = Fraction(1, 3)
+    delta = lambda a, b: 1 if a == b else 0  # noqa: E731
+    assert sum(wf) == 1
+    for a in range(d):
+        assert sum(wi * v[a] for v, wi in zip(vecs, wf)) == 0
+    for a, b in itertools.product(range(d), repeat=2):
+        assert sum(wi * v[a] * v[b] for v, wi in zip(vecs, wf)) == cs2 * delta(a, b)
+    for a, b, e in itertools.product(range(d), repeat=3):
+        assert sum(wi * v[a] * v[b] * v[e] for v, wi in zip(vecs, wf)) == 0
+    for a, b, e, k in itertools.product(range(d), repeat=4):
+        lhs = sum(wi * v[a] * v[b] * v[e] * v[k] for v, wi in zip(vecs, wf))
+        rhs = cs2 * cs2 * (delta(a, b) * delta(e, k) + delta(a, k) * delta(b, e) + delta(a, e) * delta(b, k))
+        assert lhs == rhs, (a, b, e, k)
+
+
+# --- equilibrium moments (second-order truncated Maxwellian, Sec. 2.1) -------
+@pytest.mark.parametrize("lat", [0, 1])
+def test_equilibrium_moments(oracle_mod, lat):
+    c, _ = oracle_mod.lattice(lat)
+    d = 2 if lat == 0 else 3
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        rho = rng.uniform(0.01, 2.0)
+        u = np.zeros(3)
+        u[:d] = rng.uniform(-0.1, 0.1, d)
+        feq = oracle_mod.equilibrium(lat, rho, u[:d])
+        assert abs(feq.sum() - rho) < 1e-15 * 4
+        np.testing.assert_allclose(feq @ c, rho * u, rtol=0, atol=1e-15)
+        second = np.einsum("i,ia,ib->ab", feq, c, c)
+        expect = rho * (CS2 * np.eye(3) + np.outer(u, u))
+        if d == 2:
+            expect[2, :] = 0
+            expect[:, 2] = 0
+        np.testing.assert_allclose(second, expect, rtol=0, atol=2e-15)
+
+
+# --- conservation laws -------------------------------------------------------
+def _cfg0(oracle_mod, steps):
+    rA, rB = inputs.drop((64, 64), 16, centre=(32, 32), seed=0)
+    o = oracle_mod.OracleSC(0, (64, 64), 1.0, 1.0, G0).init(rA, rB)
+    return o.step(steps), rA, rB
+
+
+def test_mass_conservation_per_species(oracle_mod):
+    """BGK conserves rho_s and streaming permutes populations (Eq. eq:be)."""
+    o, rA, rB = _cfg0(oracle_mod, 1000)
+    a, b, _, _ = o.moments()
+    assert abs(a.sum() - rA.sum()) / rA.sum() < 1e-13
+    assert abs(b.sum() - rB.sum()) / rB.sum() < 1e-13
+
+
+@pytest.mark.parametrize("lat,shape", [(0, (24, 20)), (1, (6, 8, 10))])
+def test_total_momentum_conservation(oracle_mod, lat, shape):
+    """sum_x sum_s F_s = 0 (w_i = w_-i pairs the A<-B and B<-A terms of Eq. FORCE)
+    and sum_s (rho_s u' - j_s)/tau_s = 0 by the 1/tau_s weighting of u' (Sec. 2.1),
+    so total momentum is conserved; tau_A != tau_B and a moving start make a wrong
+    weighting visible."""
+    rng = np.random.default_rng(5)
+    R = min(shape) / 3.0
+    rA, rB = inputs.drop(shape, R, seed=3, noise=1e-2)
+    u = rng.uniform(-0.02, 0.02, size=tuple(shape) + (2 if lat == 0 else 3,))
+    o = oracle_mod.OracleSC(lat, shape, 0.7, 1.3, 1.8).init(rA, rB, u)
+    m0 = o.total_momentum()
+    assert np.abs(m0).max() > 1e-3
+    o.step(200)
+    np.testing.assert_allclose(o.total_momentum(), m0, rtol=0, atol=1e-12)
+
+
+def test_uniform_state_is_fixed_point(oracle_mod):
+    """Constant densities give F = 0 (sum_i w_i c_i = 0) and f = f^eq: nothing changes."""
+    shape = (5, 4, 6)
+    rA = np.full(shape, 0.75)
+    rB = np.full(shape, 0.5)
+    o = oracle_mod.OracleSC(1, shape, 0.8, 1.1, 2.0).init(rA, rB)
+    f0 = o.f.copy()
+    o.step(7)
+    np.testing.assert_allclose(o.f, f0, rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("lat,shape,shift", [(0, (12, 10), (3, -4)), (1, (6, 5, 7), (2, -1, 3))])
+def test_translation_equivariance_bitwise(oracle_mod, lat, shape, shift):
+    """Shifting the initial fields by a lattice vector shifts the result by it, bitwise."""
+    rA, rB = inputs.drop(shape, min(shape) / 3.0, seed=4, noise=5e-3)
+    o1 = oracle_mod.OracleSC(lat, shape, 0.9, 0.9, 2.1).init(rA, rB).step(25)
+    axes = tuple(range(len(shape)))
+    roll = tuple(reversed(shift))  # arrays are (.., y, x)
+    o2 = oracle_mod.OracleSC(lat, shape, 0.9, 0.9, 2.1).init(np.roll(rA, roll, axes),
+                                                             np.roll(rB, roll, axes)).step(25)
+    for a, b in zip(o1.moments(), o2.moments()):
+        assert np.array_equal(np.roll(a, roll, axes), b)
+
+
+def test_species_mirror_symmetry(oracle_mod):
+    """With tau_A = tau_B the model is symmetric under A <-> B."""
+    shape = (16, 18)
+    rA, rB = inputs.drop(shape, 5, seed=7, noise=5e-3)
+    o1 = oracle_mod.OracleSC(0, shape, 1.1, 1.1, G0).init(rA, rB).step(40)
+    o2 = oracle_mod.OracleSC(0, shape, 1.1, 1.1, G0).init(rB, rA).step(40)
+    a1, b1, u1, p1 = o1.moments()
+    a2, b2, u2, p2 = o2.moments()
+    np.testing.assert_allclose(a1, b2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(b1, a2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(u1, u2, rtol=0, atol=1e-16)
+    np.testing.assert_allclose(p1, p2, rtol=0, atol=1e-15)
+
+
+# --- exact rational brute force on a 4x4 lattice -----------------------------
+@pytest.mark.parametrize("tau_A,tau_B,G", [(1, 1, Fraction(3, 2)), (Fraction(3, 2), Fraction(4, 5), Fraction(2, 1))])
+def test_exact_rational_steps_4x4(oracle_mod, tau_A, tau_B, G):
+    rng = np.random.default_rng(2)
+    nums = rng.integers(1, 40, size=(2, 4, 4))
+    rA = [[Fraction(int(nums[0, y, x]), 20) for x in range(4)] for y in range(4)]
+    rB = [[Fraction(int(nums[1, y, x]), 25) for x in range(4)] for y in range(4)]
+    ex = exact_sc.ExactSC(4, 4, tau_A, tau_B, G).init(rA, rB)
+    o = oracle_mod.OracleSC(0, (4, 4), float(tau_A), float(tau_B), float(G))
+    o.init(np.array(rA, dtype=float), np.array(rB, dtype=float))
+    for _ in range(2):
+        ex.step()
+        o.step(1)
+        a, b, u, p = o.moments()
+        eA, eB, eux, euy, ep = (np.array([float(v) for v in arr]).reshape(4, 4) for arr in ex.fields())
+        np.testing.assert_allclose(a, eA, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(b, eB, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(u[..., 0], eux, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(u[..., 1], euy, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(p, ep, rtol=2e-15, atol=0)
+        assert np.abs(eux).max() > 1e-3  # the trace really exercises the force
+
+
+# --- closed-form decay rates -------------------------------------------------
+def _mode_amp(field, axis):
+    n = field.shape[axis]
+    s = np.sin(2 * np.pi * np.arange(n) / n)
+    shape = [1] * field.ndim
+    shape[axis] = n
+    return 2.0 * (field * s.reshape(shape)).sum() / field.size
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.0])
+def test_shear_wave_viscosity(oracle_mod, tau):
+    """G = 0: u_x = U sin(k y) decays at nu k^2, nu = cs2 (tau - 1/2) (Sec. 2.1)."""
+    L = 64
+    rA, rB, u = inputs.shear_wave((L, 8), 0.5, 0.5, 1e-4)
+    o = oracle_mod.OracleSC(0, (L, 8), tau, tau, 0.0).init(rA, rB, u)
+    o.step(100)
+    a1 = _mode_amp(o.moments()[2][..., 0], 0)
+    o.step(1000)
+    a2 = _mode_amp(o.moments()[2][..., 0], 0)
+    k = 2 * np.pi / L
+    rate = np.log(a1 / a2) / 1000.0
+    assert abs(rate / (CS2 * (tau - 0.5) * k * k) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.0])
+def test_species_diffusion(oracle_mod, tau):
+    """G = 0: J^(A) of Sec. 2.1 reduces to Fickian diffusion with D = cs2 (tau - 1/2)."""
+    L = 64
+    rA, rB = inputs.phi_mode((4, L), 1.0, 1e-4)
+    o = oracle_mod.OracleSC(0, (4, L), tau, tau, 0.0).init(rA, rB)
+    o.step(100)
+    m = o.moments()
+    a1 = _mode_amp(m[0] - m[1], 1)
+    o.step(1000)
+    m = o.moments()
+    a2 = _mode_amp(m[0] - m[1], 1)
+    k = 2 * np.pi / L
+    rate = np.log(a1 / a2) / 1000.0
+    assert abs(rate / (CS2 * (tau - 0.5) * k * k) - 1) < 2e-3
+
+
+def test_streaming_direction_advection(oracle_mod):
+    """G = 0 at uniform velocity U: a phi mode travels at +U (streaming along +c_i)."""
+    L = 64
+    U = 0.02
+    rA, rB = inputs.phi_mode((4, L), 1.0, 1e-4)
+    u = inputs.uniform_velocity((4, L), (U, 0.0))
+    o = oracle_mod.OracleSC(0, (4, L), 0.8, 0.8, 0.0).init(rA, rB, u)
+    t = 400
+    o.step(t)
+    m = o.moments()
+    phi = (m[0] - m[1]).mean(axis=0)
+    coef = np.fft.rfft(phi)[1]
+    # phi ~ sin(k (x - U t)) = Im exp(i k (x - U t)): rfft coefficient phase = -pi/2 - k U t
+    shift = -(np.angle(coef) + np.pi / 2)
+    k = 2 * np.pi / L
+    assert abs(shift / (k * U * t) - 1) < 1e-2
+
+
+@pytest.mark.parametrize("tau,gt", [(1.0, 1.0), (0.7, 1.0), (1.0, 1.5), (0.7, 1.5), (0.6, 1.0)])
+def test_linear_spinodal_rate_with_g_tau(oracle_mod, tau, gt):
+    """Below the spinodal a small phi mode decays at
+    omega = rho (tau - 1/2) [cs2 (1/rho - g_tau/2) k^2 + g_tau cs2^2 k^4 / 4]
+    (linearised J^(phi) = M grad mu^(tau) of Sec. 2.1 with the tau-modified coupling
+    g_tau = tau g / (tau - 1/2)).  With the plain g the rate would be 33-68 % off."""
+    L, rho = 64, 1.0
+    G = gt * (tau - 0.5) / tau
+    rA, rB = inputs.phi_mode((4, L), rho, 1e-4)
+    o = oracle_mod.OracleSC(0, (4, L), tau, tau, G).init(rA, rB)
+    o.step(100)
+    m = o.moments()
+    a1 = _mode_amp(m[0] - m[1], 1)
+    o.step(1000)
+    m = o.moments()
+    a2 = _mode_amp(m[0] - m[1], 1)
+    k = 2 * np.pi / L
+    rate = np.log(a1 / a2) / 1000.0
+    theory = rho * (tau - 0.5) * (CS2 * (1 / rho - gt / 2) * k * k + gt / 4 * CS2 * CS2 * k ** 4)
+    assert abs(rate / theory - 1) < 1e-2
+
+
+# --- the paper's worked example and flat interfaces --------------------------
+def test_paper_coexistence_example(oracle_mod):
+    """Sec. 4: tau = 0.55, rho = 1.4, g = 0.164 give phi = +-1 in the pure phases.
+    Also ln(rho_A/rho_B) = g_tau phi in coexistence (mu^(tau) constant, Sec. 2.1)."""
+    with open(os.path.join(GOLDEN, "paper_sec4_coexistence.json")) as fh:
+        gold = json.load(fh)
+    L = 128
+    rho = gold["rho"]
+    phi0 = gold["phi_bulk"]
+    rA, rB = inputs.slab((4, L), L / 4, rho_hi=(rho + phi0) / 2, rho_lo=(rho - phi0) / 2, noise=0.0)
+    o = oracle_mod.OracleSC(0, (4, L), gold["tau"], gold["tau"], gold["g_AB"]).init(rA, rB)
+    o.step(20000)
+    a, b, u, p = o.moments()
+    phi_in = (a - b)[0, L // 2]
+    phi_out = (a - b)[0, 0]
+    assert abs(phi_in - phi0) < 0.02 * phi0
+    assert abs(phi_out + phi0) < 0.02 * phi0
+    g_tau = gold["tau"] * gold["g_AB"] / (gold["tau"] - 0.5)
+    ra, rb = a[0, L // 2], b[0, L // 2]
+    assert abs(np.log(ra / rb) / (g_tau * (ra - rb)) - 1) < 1e-2
+
+
+def test_flat_interface_stationary_and_shifted_velocity(oracle_mod):
+    """A relaxed flat interface is at rest: u_phys = (sum j + F/2)/rho -> 0 (Sec. 2.3
+    F dt/2 shift), while the unshifted lattice momentum stays at O(F/2)."""
+    L = 64
+    rA, rB = inputs.slab((4, L), L / 4, noise=0.0)
+    o = oracle_mod.OracleSC(0, (4, L), 1.0, 1.0, G0).init(rA, rB)
+    o.step(12000)
+    a1, b1, u1, _ = o.moments()
+    o.step(1000)
+    a2, b2, u2, _ = o.moments()
+    assert np.abs(u2).max() < 1e-5
+    assert np.abs(a2 - a1).max() < 1e-6 and np.abs(b2 - b1).max() < 1e-6
+    c, _ = oracle_mod.lattice(0)
+    j = np.einsum("nsi,ia->na", o.f, c).reshape(4, L, 3)
+    unshifted = j[..., 0] / (a2 + b2)
+    assert np.abs(unshifted).max() > 100 * np.abs(u2).max()
+
+
+@pytest.mark.parametrize("tau,G", [(1.0, 0.0), (1.0, 0.5), (0.8, 0.6), (1.0, -0.5)])
+def test_sound_speed_matches_reported_pressure(oracle_mod, tau, G):
+    """The momentum equation of Sec. 2.1 carries -div P, so a density wave at fixed
+    composition travels at c^2 = dp/drho of the bulk pressure.  The speed measured
+    from the dynamics must equal the finite-difference slope of the pressure the
+    oracle reports (p = cs2 rho + cs2 G rho_A rho_B, Sec. 2.1), and both must equal
+    cs2 (1 + G rho / 2) at rho_A = rho_B = rho / 2."""
+    L = 64
+    shape = (4, L)
+    s = np.sin(2 * np.pi * np.arange(L) / L)
+    rA = np.broadcast_to(0.5 + 1e-5 * s, shape).copy()
+    o = oracle_mod.OracleSC(0, shape, tau, tau, G).init(rA, rA.copy())
+    amps = []
+    for _ in range(800):
+        a, b, _, _ = o.moments()
+        amps.append(((a + b).mean(axis=0) * s).sum() * 2 / L)
+        o.step(1)
+    amps = np.array(amps)
+    idx = np.where(np.sign(amps[:-1]) != np.sign(amps[1:]))[0]
+    tz = np.array([i + amps[i] / (amps[i] - amps[i + 1]) for i in idx])
+    omega = np.pi / np.diff(tz).mean()
+    c2 = (omega / (2 * np.pi / L)) ** 2
+    eps = 1e-4
+    pr = []
+    for r in (1.0 - eps, 1.0 + eps):
+        u = oracle_mod.OracleSC(0, (2, 2), tau, tau, G).init(np.full((2, 2), r / 2), np.full((2, 2), r / 2))
+        pr.append(u.moments()[3][0, 0])
+    dpdrho = (pr[1] - pr[0]) / (2 * eps)
+    assert abs(c2 / dpdrho - 1) < 2e-3
+    assert abs(dpdrho / (CS2 * (1 + G / 2)) - 1) < 1e-6
+
+
+def test_laplace_law(oracle_mod):
+    """sigma = R (P_i - P_o) (Sec. 4.1): the pressure jump is linear in 1/R with a
+    vanishing intercept (a flat interface, 1/R = 0, carries no jump)."""
+    L = 64
+    steps = 3000
+    Rs, dPs = [], []
+    for R in (8, 11, 14, 18):
+        rA, rB = inputs.drop((L, L), R, centre=(L / 2, L / 2), seed=R)
+        o = oracle_mod.OracleSC(0, (L, L), 1.0, 1.0, G0).init(rA, rB).step(steps)
+        a, b, u, p = o.moments()
+        r = inputs.radial_distance((L, L), (L / 2, L / 2))
+        a_in, a_out = a[r < R / 4].mean(), a[r > R + 8].mean()
+        V = (a - a_out).sum() / (a_in - a_out)
+        Rm = np.sqrt(V / np.pi)
+        Rs.append(Rm)
+        dPs.append(p[r < Rm / 4].mean() - p[r > Rm + 8].mean())
+    inv = 1.0 / np.array(Rs)
+    dP = np.array(dPs)
+    A = np.vstack([inv, np.ones_like(inv)]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, dP, rcond=None)
+    pred = A @ np.array([slope, icpt])
+    r2 = 1 - ((dP - pred) ** 2).sum() / ((dP - dP.mean()) ** 2).sum()
+    assert slope > 0
+    assert r2 > 0.99
+    assert abs(icpt) < 0.05 * slope / 8
