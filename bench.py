@@ -1,0 +1,319 @@
+"""Benchmark of the fused two-component Shan-Chen step (MLUPS and HBM roofline).
+
+Default workload: D3Q19 512^3 periodic lattice, FP32, spherical drop R = L/4
+(tau = 1, G rho_tot = 2.4, rho 1.0 / 0.04, tanh width 2, +-1e-3 seeded noise).
+One timed "step" is one lattice time step (one fused-kernel launch) over all
+134,217,728 nodes.  Each population buffer is 20.4 GB, far larger than the
+129 MB L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--L 512] [--precision f32|bf16|f16|f64] [--no-e2e] [--no-cpu-baseline]
+
+Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+lattice (independent replicas, no collective on the data path); the timed
+region is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+G_RHO = 2.4
+RHO_HI, RHO_LO = 1.0, 0.04
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "bf16": "f32 (bf16 storage)", "f16": "f32 (f16 storage)"}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=512)
+    ap.add_argument("--precision", default="f32", choices=list(BYTES_PER_VALUE))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1112_5547_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def drop_fields(L, dtype, seed=2):
+    from paper_1112_5547_gb300 import inputs
+    return inputs.drop((L, L, L), L / 4.0, rho_hi=RHO_HI, rho_lo=RHO_LO, width=2.0, noise=1e-3, seed=seed,
+                       dtype=dtype)
+
+
+def cpu_baseline(seconds: float, L: int = 128):
+    """The FP64 oracle as it stands, on all host cores, on a bounded sample of the
+    same workload (a 128^3 drop with the same recipe): time whole steps until
+    ``seconds`` have passed."""
+    import oracle
+    oracle.build()
+    G = G_RHO / (RHO_HI + RHO_LO)
+    rA, rB = drop_fields(L, np.float64)
+    o = oracle.OracleSC(1, (L, L, L), 1.0, 1.0, G).init(rA, rB)
+    o.step(1)  # warm-up
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= 2:
+            break
+    mlups = L ** 3 * n / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d steps in %.1f s" % (L, n, el)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = cpu_baseline(max(5.0, args.cpu_seconds))
+    line = {"impl": "reference", "metric": "2-comp SC D3Q19 MLUPS & HBM roofline %", "value": cb["value"],
+            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "D3Q19 %d^3 SC drop R=L/4 (oracle sample at 128^3)" % args.L,
+                                            "lattice": "D3Q19", "L": args.L},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1112_5547_gb300 import build as gb
+    from paper_1112_5547_gb300 import lbm_sc
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        gb.build()
+    if dist is not None:
+        dist.barrier()
+    lbm_sc.load()
+
+    # CPU baseline first (before any CUDA work on this process is busy), rank 0 only at N=1.
+    cb = None
+    if not args.no_cpu_baseline and world == 1 and rank == 0:
+        cb = cpu_baseline(args.cpu_seconds)
+
+    L = args.L
+    N = L ** 3
+    G = G_RHO / (RHO_HI + RHO_LO)
+    prec = args.precision
+    cdt = np.float64 if prec == "f64" else np.float32
+    ref = (0.5 * (RHO_HI + RHO_LO), 0.5 * (RHO_HI + RHO_LO)) if prec in ("bf16", "f16") else (0.0, 0.0)
+    rA, rB = drop_fields(L, cdt, seed=2 + rank)
+    stream = torch.cuda.Stream()
+    lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, prec, ref[0], ref[1], stream=stream)
+    with torch.cuda.stream(stream):
+        lat.init(rA, rB)
+    stream.synchronize()
+
+    # warm-up
+    lat.step(args.warmup)
+    stream.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        lat.step(1)
+        ev[k][1].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    d = lat.diagnostics(check=False)
+
+    ms_per_step = total_ms / K
+    value = world * N * K / (total_ms / 1e3) / 1e6
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+    bytes_per_lu = 2 * 19 * 2 * BYTES_PER_VALUE[prec]
+    achieved = bytes_per_lu * N / avg_launch_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tf = json.load(open(TRAFFIC_FILE))
+        key = "d3q19_%s" % prec
+        if key in tf and tf[key].get("source_hash") == kernel_source_hash():
+            traffic = tf[key]["dram_bytes_per_lu"] * N
+
+    # End to end through the C ABI with host buffers: H2D of the initial fields,
+    # init, K steps, moments, D2H of rho_A, rho_B, u, p.
+    e2e = None
+    if not args.no_e2e:
+        lat2 = lat  # reuse the same workspace
+        sb = lbm_sc.lbm_sc_host_staging_bytes(lat2.params)
+        staging = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
+        sp = (staging.data_ptr() + 255) // 256 * 256
+        tdt = torch.float64 if prec == "f64" else torch.float32
+        hA = torch.from_numpy(np.ascontiguousarray(rA).reshape(-1)).pin_memory()
+        hB = torch.from_numpy(np.ascontiguousarray(rB).reshape(-1)).pin_memory()
+        oA, oB, oP = (torch.empty(N, dtype=tdt).pin_memory() for _ in range(3))
+        oU = torch.empty(3 * N, dtype=tdt).pin_memory()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbm_sc.lbm_sc_run_host(lat2.handle, sp, sb, hA.data_ptr(), hB.data_ptr(), None, K, oA.data_ptr(),
+                               oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        esz = 8 if prec == "f64" else 4
+        e2e = {"value": world * N * K / e2e_s / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 2 * N * esz / K, "d2h_bytes_per_step": 6 * N * esz / K,
+               "note": "one job of %d steps: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p; bytes per step = job bytes / steps" % K}
+        del staging, hA, hB, oA, oB, oP, oU
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "2-comp SC D3Q19 MLUPS & HBM roofline %",
+        "value": value,
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": DTYPE_NAME[prec],
+        "data": "synthetic",
+        "config": {"workload": "D3Q19 %d^3 two-component SC drop R=L/4, tau=1, G*rho_tot=2.4, seed 2" % L,
+                   "lattice": "D3Q19", "L": L, "nodes": N, "storage": prec,
+                   "l2": "inputs larger than L2 (%.1f GB per population buffer)" % (N * 38 * BYTES_PER_VALUE[prec] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_lu": bytes_per_lu,
+                     "kernel": "sc_fused_kernel<D3Q19,%s> step" % prec},
+        "gpu_launches": K,
+        "clocks": clk,
+        "diag": {"mass_A": d["mass_A"], "max_speed": d["max_speed"], "status": d["status"]},
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * lbm_sc.h -- C ABI of the GB300 two-component Shan-Chen lattice Boltzmann step.
+ *
+ * The model (Scarbolo et al., Sec. 2.1): two species s in {A, B}, each with
+ * BGK populations f_is on a D2Q9 or D3Q19 lattice, dt = 1,
+ *
+ *   f_is(x + c_i, t + 1) - f_is(x, t) = -(1/tau_s) [f_is - f^eq_is(rho_s, u' + tau_s F_s / rho_s)]
+ *                                                                 (Eq. eq:be)
+ *   rho_s = sum_i f_is,   u' = sum_s (1/tau_s) sum_i f_is c_i / sum_s rho_s / tau_s
+ *   F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x + c_i) c_i             (Eq. FORCE)
+ *
+ * with the second-order equilibrium f^eq_i = w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u]
+ * and fully periodic boundaries (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - The caller owns all device memory and the CUDA stream.  The library never
+ *     allocates or frees device memory and never synchronises the device, except
+ *     where an entry point says it does (lbm_sc_diagnostics, lbm_sc_run_host).
+ *     lbm_sc_create allocates only the small host-side handle (malloc).
+ *   - "Device pointer" arguments must be device (or managed) memory on the
+ *     current device; "host pointer" arguments ordinary host memory (pinned
+ *     memory makes the copies asynchronous-capable and faster).
+ *   - Fields are arrays of nx*ny*nz values, x fastest (index x + nx*(y + ny*z)),
+ *     in the COMPUTE type of the precision: double for LBM_F64, float otherwise.
+ *     Velocity fields hold D planes (D = 2 for D2Q9, 3 for D3Q19) one after the
+ *     other: u_x[N], u_y[N] (, u_z[N]).
+ *   - Every call returns an lbm_status and never aborts the process.  Kernel
+ *     launches are asynchronous: a device fault surfaces as LBM_ERR_CUDA on a
+ *     later call.
+ *   - Calls on one handle must not run concurrently from several host threads.
+ */
+#ifndef LBM_SC_H
+#define LBM_SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_SC_API __attribute__((visibility("default")))
+#else
+#define LBM_SC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1,    /* bad parameter, pointer or size                        */
+    LBM_ERR_OUT_OF_MEMORY = 2,  /* workspace too small, or the host handle malloc failed */
+    LBM_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed           */
+    LBM_ERR_UNSTABLE = 4,       /* diagnostics saw a non-finite value or rho_s <= 0       */
+    LBM_ERR_TIMEOUT = 5         /* a bounded device-side wait expired                    */
+} lbm_status;
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Arithmetic is FP64 for LBM_F64 and FP32 otherwise.  The 16-bit precisions
+ * store h_is = f_is - w_i rho_ref_s (an offset from the rest equilibrium of
+ * a reference density) in bf16 / fp16 and decode to FP32 on load. */
+typedef enum {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F32_STORE_BF16 = 2,
+    LBM_F32_STORE_F16 = 3
+} lbm_precision;
+
+/* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE). */
+typedef struct {
+    int32_t lattice;     /* lbm_lattice                                              */
+    int32_t precision;   /* lbm_precision                                            */
+    int32_t nx, ny, nz;  /* >= 1 each; nz must be 1 for D2Q9; nx*ny*nz < 2^31        */
+    int32_t reserved;    /* set to 0                                                 */
+    double tau_A, tau_B; /* relaxation times tau_s (> 1/2)                           */
+    double G;            /* coupling G_AB = G_BA (> 0 repulsive)                     */
+    double rho_ref_A;    /* reference densities of the 16-bit storage offsets;      */
+    double rho_ref_B;    /* ignored for LBM_F64 / LBM_F32                            */
+} lbm_sc_params;
+
+/* Optional spherical windows for the drop diagnostics: nodes whose periodic
+ * minimum-image distance r from (cx, cy, cz) satisfies r < r_in form the
+ * inner window, r > r_out the outer window (Sec. 4.1, P_i and P_o). */
+typedef struct {
+    double cx, cy, cz;
+    double r_in, r_out;
+} lbm_sc_window;
+
+/* FP64 scalars of the current state.  The velocity is the physical one,
+ * u_phys = (sum_s j_s + (1/2) sum_s F_s) / (rho_A + rho_B) (Sec. 2.3, momentum
+ * shifted by F dt/2); p = cs2 (rho_A + rho_B) + cs2 G rho_A rho_B (bulk part of
+ * the pressure tensor, Sec. 2.1). */
+typedef struct {
+    double mass_A, mass_B;        /* sum_x rho_A, sum_x rho_B                          */
+    double momentum[3];           /* sum_x (j_A + j_B + (F_A + F_B) / 2)               */
+    double kinetic_energy;        /* sum_x (rho/2) |u_phys|^2                          */
+    double max_speed;             /* max_x |u_phys|                                    */
+    double min_rho_A, min_rho_B;  /* minima over the lattice                           */
+    double nonfinite;             /* number of nodes with a non-finite moment          */
+    double in_count, in_rho_A, in_p;    /* inner window: node count, sum rho_A, sum p */
+    double out_count, out_rho_A, out_p; /* outer window: node count, sum rho_A, sum p */
+} lbm_sc_diag;
+
+typedef struct lbm_sc_handle lbm_sc_handle;
+
+/* Bytes of device workspace one lattice needs: two population buffers
+ * (2 species x Q x N values of the storage type each) and the diagnostics
+ * scratch.  Returns 0 if the parameters are invalid. */
+LBM_SC_API size_t lbm_sc_workspace_bytes(const lbm_sc_params* params);
+
+/* Bind a lattice to caller-owned device workspace (>= lbm_sc_workspace_bytes,
+ * 256-byte aligned) and a CUDA stream (cudaStream_t; NULL = legacy default
+ * stream).  The populations are undefined until lbm_sc_init_fields.  On
+ * success *out receives a host handle that lbm_sc_destroy releases. */
+LBM_SC_API lbm_status lbm_sc_create(const lbm_sc_params* params, void* d_workspace, size_t workspace_bytes,
+                         void* cuda_stream, lbm_sc_handle** out);
+
+/* Change the stream later calls are enqueued on. */
+LBM_SC_API lbm_status lbm_sc_set_stream(lbm_sc_handle* h, void* cuda_stream);
+
+/* Populations at equilibrium of the given fields: f_is = f^eq(rho_s, u) (Sec. 2.1),
+ * the state at t = 0.  d_rhoA, d_rhoB: device pointers to N compute-type values;
+ * d_u: device pointer to D*N values, or NULL for a fluid at rest. */
+LBM_SC_API lbm_status lbm_sc_init_fields(lbm_sc_handle* h, const void* d_rhoA, const void* d_rhoB,
+                              const void* d_u);
+
+/* Advance nsteps time steps (Eq. eq:be with Eq. FORCE): one fused kernel per
+ * step pulls the populations along -c_i (periodic), forms rho_s and j_s, the
+ * force from the neighbours' densities, the common velocity u', relaxes each
+ * species to f^eq(rho_s, u' + tau_s F_s / rho_s) and stores.  nsteps >= 0. */
+LBM_SC_API lbm_status lbm_sc_step(lbm_sc_handle* h, int nsteps);
+
+/* Macroscopic fields of the current state (moments of the populations at the
+ * current time, before its collision): rho_A, rho_B, u_phys (D planes) and the
+ * bulk pressure p.  Device pointers; any may be NULL. */
+LBM_SC_API lbm_status lbm_sc_moments(lbm_sc_handle* h, void* d_rhoA, void* d_rhoB, void* d_u, void* d_p);
+
+/* FP64 diagnostics of the current state (window may be NULL: no windows).
+ * Synchronises the handle's stream and copies the result to *host_out.
+ * Returns LBM_ERR_UNSTABLE (with *host_out filled) if a moment is non-finite or
+ * a density is <= 0. */
+LBM_SC_API lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm_sc_diag* host_out);
+
+/* Bytes of device staging lbm_sc_run_host needs for its field copies. */
+LBM_SC_API size_t lbm_sc_host_staging_bytes(const lbm_sc_params* params);
+
+/* End-to-end run from host memory: copies rho_A, rho_B (and u, if not NULL)
+ * from host pointers into d_staging, initialises, advances nsteps, computes the
+ * moments and copies each non-NULL output back to host pointers (same layouts as
+ * lbm_sc_moments).  d_staging: >= lbm_sc_host_staging_bytes, 256-byte aligned.
+ * Synchronises the handle's stream before returning. */
+LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_bytes,
+                           const void* h_rhoA, const void* h_rhoB, const void* h_u, int nsteps,
+                           void* h_rhoA_out, void* h_rhoB_out, void* h_u_out, void* h_p_out);
+
+/* Bytes and population storage layout (for tools): element size of one stored
+ * population value, number of velocities Q, and the current population buffer
+ * (2 x Q planes of N values, index (s*Q + i)*N + node, GPU velocity order). */
+LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, const void** d_populations);
+
+/* Release the host handle.  The workspace stays the caller's. */
+LBM_SC_API void lbm_sc_destroy(lbm_sc_handle* h);
+
+/* Static, human-readable name of a status code. */
+LBM_SC_API const char* lbm_sc_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_SC_H */

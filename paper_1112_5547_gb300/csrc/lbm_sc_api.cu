@@ -1,0 +1,294 @@
+// C-ABI of the GB300 Shan-Chen lattice Boltzmann library (declared in
+// include/lbm_sc.h).  Host code only: validation, workspace carving, stream
+// handling and dispatch to the per-lattice launchers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "../../include/lbm_sc.h"
+#include "sc_launch.cuh"
+
+using lbmsc::Plan;
+
+struct lbm_sc_handle {
+    lbm_sc_params params;
+    Plan plan;
+    char* ws;
+    size_t ws_bytes;
+    void* buf[2];
+    int cur;              // buffer holding the current populations
+    double* partials;     // per-CTA diagnostics partials
+    double* result;       // folded diagnostics (kNumDiag doubles)
+    cudaStream_t stream;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int q_of(int lattice) { return lattice == LBM_D2Q9 ? 9 : 19; }
+int d_of(int lattice) { return lattice == LBM_D2Q9 ? 2 : 3; }
+
+size_t store_bytes(int precision) {
+    switch (precision) {
+        case LBM_F64: return 8;
+        case LBM_F32: return 4;
+        case LBM_F32_STORE_BF16:
+        case LBM_F32_STORE_F16: return 2;
+    }
+    return 0;
+}
+
+size_t compute_bytes(int precision) { return precision == LBM_F64 ? 8 : 4; }
+
+bool valid(const lbm_sc_params* p) {
+    if (!p) return false;
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return false;
+    if (store_bytes(p->precision) == 0) return false;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return false;
+    if (p->lattice == LBM_D2Q9 && p->nz != 1) return false;
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (N >= (1LL << 31)) return false;
+    if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return false;
+    if (!(p->G == p->G) || !(p->rho_ref_A == p->rho_ref_A) || !(p->rho_ref_B == p->rho_ref_B)) return false;
+    return true;
+}
+
+// Planes per CTA along z: enough CTAs to fill the 152 SMs several times over,
+// at least 16 planes per chunk so the two extra density planes stay cheap.
+int pick_zchunk(const lbm_sc_params* p) {
+    if (p->lattice == LBM_D2Q9) return 1;
+    const long long tiles = (long long)((p->nx + lbmsc::kTX - 1) / lbmsc::kTX) * ((p->ny + lbmsc::kTY - 1) / lbmsc::kTY);
+    const long long target = 152LL * 2 * 8;
+    long long chunks = (target + tiles - 1) / tiles;
+    long long max_chunks = p->nz / 16;
+    if (max_chunks < 1) max_chunks = 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    return (int)((p->nz + chunks - 1) / chunks);
+}
+
+Plan make_plan(const lbm_sc_params* p) {
+    Plan pl;
+    pl.lattice = p->lattice;
+    pl.precision = p->precision;
+    pl.nx = p->nx;
+    pl.ny = p->ny;
+    pl.nz = p->nz;
+    pl.N = (long long)p->nx * p->ny * p->nz;
+    pl.zchunk = pick_zchunk(p);
+    pl.tau_A = p->tau_A;
+    pl.tau_B = p->tau_B;
+    pl.G = p->G;
+    pl.ref_A = p->rho_ref_A;
+    pl.ref_B = p->rho_ref_B;
+    return pl;
+}
+
+size_t population_bytes(const lbm_sc_params* p) {
+    return (size_t)2 * q_of(p->lattice) * (size_t)p->nx * p->ny * p->nz * store_bytes(p->precision);
+}
+
+size_t partial_bytes(const Plan& pl) {
+    return (size_t)lbmsc::fused_blocks(pl) * lbmsc::kNumDiag * sizeof(double);
+}
+
+lbm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
+
+cudaError_t launch_step(const Plan& pl, const void* fin, void* fout, cudaStream_t st) {
+    return pl.lattice == LBM_D2Q9 ? lbmsc::d2q9_step(pl, fin, fout, st) : lbmsc::d3q19_step(pl, fin, fout, st);
+}
+
+cudaError_t launch_init(const Plan& pl, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st) {
+    return pl.lattice == LBM_D2Q9 ? lbmsc::d2q9_init(pl, rA, rB, u, fout, st)
+                                  : lbmsc::d3q19_init(pl, rA, rB, u, fout, st);
+}
+
+cudaError_t launch_moments(const Plan& pl, const void* fin, const lbmsc::MomentsOut& o, cudaStream_t st) {
+    return pl.lattice == LBM_D2Q9 ? lbmsc::d2q9_moments(pl, fin, o, st) : lbmsc::d3q19_moments(pl, fin, o, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_sc_workspace_bytes(const lbm_sc_params* p) {
+    if (!valid(p)) return 0;
+    const Plan pl = make_plan(p);
+    return 2 * align_up(population_bytes(p)) + align_up(partial_bytes(pl)) +
+           align_up(lbmsc::kNumDiag * sizeof(double));
+}
+
+lbm_status lbm_sc_create(const lbm_sc_params* p, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
+                         lbm_sc_handle** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid(p) || !d_workspace) return LBM_ERR_INVALID_ARG;
+    if (((uintptr_t)d_workspace) % kAlign != 0) return LBM_ERR_INVALID_ARG;
+    const size_t need = lbm_sc_workspace_bytes(p);
+    if (workspace_bytes < need) return LBM_ERR_OUT_OF_MEMORY;
+    lbm_sc_handle* h = static_cast<lbm_sc_handle*>(malloc(sizeof(lbm_sc_handle)));
+    if (!h) return LBM_ERR_OUT_OF_MEMORY;
+    memset(h, 0, sizeof(*h));
+    h->params = *p;
+    h->plan = make_plan(p);
+    h->ws = static_cast<char*>(d_workspace);
+    h->ws_bytes = workspace_bytes;
+    const size_t pb = align_up(population_bytes(p));
+    h->buf[0] = h->ws;
+    h->buf[1] = h->ws + pb;
+    h->partials = reinterpret_cast<double*>(h->ws + 2 * pb);
+    h->result = reinterpret_cast<double*>(h->ws + 2 * pb + align_up(partial_bytes(h->plan)));
+    h->cur = 0;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_set_stream(lbm_sc_handle* h, void* cuda_stream) {
+    if (!h) return LBM_ERR_INVALID_ARG;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_init_fields(lbm_sc_handle* h, const void* d_rhoA, const void* d_rhoB, const void* d_u) {
+    if (!h || !d_rhoA || !d_rhoB) return LBM_ERR_INVALID_ARG;
+    h->cur = 0;
+    return cuda_status(launch_init(h->plan, d_rhoA, d_rhoB, d_u, h->buf[0], h->stream));
+}
+
+lbm_status lbm_sc_step(lbm_sc_handle* h, int nsteps) {
+    if (!h || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    for (int t = 0; t < nsteps; ++t) {
+        const cudaError_t e = launch_step(h->plan, h->buf[h->cur], h->buf[1 - h->cur], h->stream);
+        if (e != cudaSuccess) return LBM_ERR_CUDA;
+        h->cur = 1 - h->cur;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_moments(lbm_sc_handle* h, void* d_rhoA, void* d_rhoB, void* d_u, void* d_p) {
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (!d_rhoA && !d_rhoB && !d_u && !d_p) return LBM_OK;
+    lbmsc::MomentsOut o;
+    o.rhoA = d_rhoA;
+    o.rhoB = d_rhoB;
+    o.u = d_u;
+    o.p = d_p;
+    o.partials = nullptr;
+    o.win[0] = o.win[1] = o.win[2] = 0.0;
+    o.win[3] = -1.0;
+    o.win[4] = 1e300;
+    return cuda_status(launch_moments(h->plan, h->buf[h->cur], o, h->stream));
+}
+
+lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm_sc_diag* host_out) {
+    if (!h || !host_out) return LBM_ERR_INVALID_ARG;
+    lbmsc::MomentsOut o;
+    o.rhoA = o.rhoB = o.u = o.p = nullptr;
+    o.partials = h->partials;
+    if (window) {
+        o.win[0] = window->cx;
+        o.win[1] = window->cy;
+        o.win[2] = window->cz;
+        o.win[3] = window->r_in;
+        o.win[4] = window->r_out;
+    } else {
+        o.win[0] = o.win[1] = o.win[2] = 0.0;
+        o.win[3] = -1.0;
+        o.win[4] = 1e300;
+    }
+    cudaError_t e = launch_moments(h->plan, h->buf[h->cur], o, h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    e = lbmsc::diag_finish(h->partials, lbmsc::fused_blocks(h->plan), h->result, h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    double r[lbmsc::kNumDiag];
+    e = cudaMemcpyAsync(r, h->result, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    host_out->mass_A = r[lbmsc::kMassA];
+    host_out->mass_B = r[lbmsc::kMassB];
+    host_out->momentum[0] = r[lbmsc::kMomX];
+    host_out->momentum[1] = r[lbmsc::kMomY];
+    host_out->momentum[2] = r[lbmsc::kMomZ];
+    host_out->kinetic_energy = r[lbmsc::kKE];
+    host_out->max_speed = r[lbmsc::kMaxSpeed];
+    host_out->min_rho_A = r[lbmsc::kMinRhoA];
+    host_out->min_rho_B = r[lbmsc::kMinRhoB];
+    host_out->nonfinite = r[lbmsc::kNonFinite];
+    host_out->in_count = r[lbmsc::kInCount];
+    host_out->in_rho_A = r[lbmsc::kInRhoA];
+    host_out->in_p = r[lbmsc::kInP];
+    host_out->out_count = r[lbmsc::kOutCount];
+    host_out->out_rho_A = r[lbmsc::kOutRhoA];
+    host_out->out_p = r[lbmsc::kOutP];
+    if (host_out->nonfinite > 0 || !(host_out->min_rho_A > 0) || !(host_out->min_rho_B > 0))
+        return LBM_ERR_UNSTABLE;
+    return LBM_OK;
+}
+
+size_t lbm_sc_host_staging_bytes(const lbm_sc_params* p) {
+    if (!valid(p)) return 0;
+    const size_t field = align_up((size_t)p->nx * p->ny * p->nz * compute_bytes(p->precision));
+    return field * (size_t)(3 + d_of(p->lattice));
+}
+
+lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_bytes, const void* h_rhoA,
+                           const void* h_rhoB, const void* h_u, int nsteps, void* h_rhoA_out, void* h_rhoB_out,
+                           void* h_u_out, void* h_p_out) {
+    if (!h || !d_staging || !h_rhoA || !h_rhoB || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    if (((uintptr_t)d_staging) % kAlign != 0) return LBM_ERR_INVALID_ARG;
+    if (staging_bytes < lbm_sc_host_staging_bytes(&h->params)) return LBM_ERR_OUT_OF_MEMORY;
+    const size_t fb = (size_t)h->plan.N * compute_bytes(h->params.precision);
+    const size_t field = align_up(fb);
+    const int D = d_of(h->params.lattice);
+    char* s = static_cast<char*>(d_staging);
+    void* dA = s;
+    void* dB = s + field;
+    void* dP = s + 2 * field;
+    void* dU = s + 3 * field;  // D consecutive planes of fb bytes
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+    if (cudaMemcpyAsync(dA, h_rhoA, fb, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemcpyAsync(dB, h_rhoB, fb, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h_u && cudaMemcpyAsync(dU, h_u, fb * D, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    lbm_status st = lbm_sc_init_fields(h, dA, dB, h_u ? dU : nullptr);
+    if (st != LBM_OK) return st;
+    st = lbm_sc_step(h, nsteps);
+    if (st != LBM_OK) return st;
+    st = lbm_sc_moments(h, h_rhoA_out ? dA : nullptr, h_rhoB_out ? dB : nullptr, h_u_out ? dU : nullptr,
+                        h_p_out ? dP : nullptr);
+    if (st != LBM_OK) return st;
+    if (h_rhoA_out && cudaMemcpyAsync(h_rhoA_out, dA, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h_rhoB_out && cudaMemcpyAsync(h_rhoB_out, dB, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h_u_out && cudaMemcpyAsync(h_u_out, dU, fb * D, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h_p_out && cudaMemcpyAsync(h_p_out, dP, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(h->stream));
+}
+
+lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, const void** d_populations) {
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (elem_bytes) *elem_bytes = (int)store_bytes(h->params.precision);
+    if (q) *q = q_of(h->params.lattice);
+    if (d_populations) *d_populations = h->buf[h->cur];
+    return LBM_OK;
+}
+
+void lbm_sc_destroy(lbm_sc_handle* h) { free(h); }
+
+const char* lbm_sc_status_string(lbm_status s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_ERR_INVALID_ARG: return "LBM_ERR_INVALID_ARG: invalid parameter, pointer or size";
+        case LBM_ERR_OUT_OF_MEMORY: return "LBM_ERR_OUT_OF_MEMORY: workspace too small or host allocation failed";
+        case LBM_ERR_CUDA: return "LBM_ERR_CUDA: a CUDA call or kernel launch failed";
+        case LBM_ERR_UNSTABLE: return "LBM_ERR_UNSTABLE: non-finite value or non-positive density";
+        case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT: bounded device wait expired";
+    }
+    return "unknown lbm_status";
+}
+
+}  // extern "C"

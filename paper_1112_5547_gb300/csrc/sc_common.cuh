@@ -1,0 +1,123 @@
+// Shared device-side definitions of the Shan-Chen LBM kernels: velocity sets,
+// storage codecs and kernel argument blocks.
+//
+// Velocity sets (GPU order; opposite directions are adjacent):
+//   D2Q9 : rest, (+-1,0), (0,+-1), (1,1),(-1,-1), (1,-1),(-1,1)
+//          weights 4/9, 1/9, 1/36
+//   D3Q19: rest, (+-1,0,0), (0,+-1,0), (0,0,+-1), then the 12 edge vectors
+//          weights 1/3, 1/18, 1/36
+// Both satisfy sum_i w_i c_ia c_ib = cs2 delta_ab and the fourth-order isotropy
+// condition with cs2 = 1/3 required by Sec. 2.1 of the paper.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmsc {
+
+struct D2Q9 {
+    static constexpr int D = 2;
+    static constexpr int Q = 9;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr signed char t[9][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0},
+                                         {0, 1, 0},  {0, -1, 0},  {1, 1, 0},
+                                         {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+struct D3Q19 {
+    static constexpr int D = 3;
+    static constexpr int Q = 19;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr signed char t[19][3] = {
+            {0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},  {0, 0, 1},  {0, 0, -1},
+            {1, 1, 0},   {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1},
+            {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// Storage codecs: load/store one population value.  16-bit types hold the
+// offset h = f - w_i rho_ref (the caller passes the offset w_i rho_ref).
+template <class S> struct Codec;
+
+template <> struct Codec<double> {
+    using C = double;
+    static constexpr bool kOffset = false;
+    __device__ __forceinline__ static C load(const double* p, C) { return __ldg(p); }
+    __device__ __forceinline__ static void store(double* p, C v, C) { __stcs(p, v); }
+};
+
+template <> struct Codec<float> {
+    using C = float;
+    static constexpr bool kOffset = false;
+    __device__ __forceinline__ static C load(const float* p, C) { return __ldg(p); }
+    __device__ __forceinline__ static void store(float* p, C v, C) { __stcs(p, v); }
+};
+
+template <> struct Codec<__nv_bfloat16> {
+    using C = float;
+    static constexpr bool kOffset = true;
+    __device__ __forceinline__ static C load(const __nv_bfloat16* p, C off) {
+        return __bfloat162float(__ldg(p)) + off;
+    }
+    __device__ __forceinline__ static void store(__nv_bfloat16* p, C v, C off) {
+        *p = __float2bfloat16_rn(v - off);
+    }
+};
+
+template <> struct Codec<__half> {
+    using C = float;
+    static constexpr bool kOffset = true;
+    __device__ __forceinline__ static C load(const __half* p, C off) {
+        return __half2float(__ldg(p)) + off;
+    }
+    __device__ __forceinline__ static void store(__half* p, C v, C off) {
+        *p = __float2half_rn(v - off);
+    }
+};
+
+// Per-lattice arguments of the step / moments kernels (compute type C).
+template <class S> struct LatticeArgs {
+    using C = typename Codec<S>::C;
+    const S* fin;       // populations at the current time (pulled along -c_i)
+    S* fout;            // populations after collision (same node, not pushed)
+    int nx, ny, nz;
+    int zchunk;         // planes per CTA along z (D3Q19)
+    long long N;        // nx * ny * nz
+    C omega_A, omega_B; // 1 / tau_s
+    C tau_A, tau_B;
+    C G;
+    C ref_A, ref_B;     // rho_ref_s of the 16-bit offsets (0 otherwise)
+};
+
+// Outputs of the moments kernel (any pointer may be null).
+template <class C> struct FieldArgs {
+    C* rhoA;
+    C* rhoB;
+    C* u;    // D planes of N
+    C* p;
+    double* partials;  // per-CTA diagnostics partial sums (kNumDiag each), or null
+    double win_c[3];   // window centre
+    double r_in2, r_out2;  // squared window radii (r_in2 < 0: no inner window)
+};
+
+// Order of the diagnostics partials (matches lbm_sc_diag).
+enum DiagSlot {
+    kMassA = 0, kMassB, kMomX, kMomY, kMomZ, kKE, kMaxSpeed, kMinRhoA, kMinRhoB, kNonFinite,
+    kInCount, kInRhoA, kInP, kOutCount, kOutRhoA, kOutP, kNumDiag
+};
+
+__device__ __forceinline__ int wrap_dec(int x, int n) { return x == 0 ? n - 1 : x - 1; }
+__device__ __forceinline__ int wrap_inc(int x, int n) { return x == n - 1 ? 0 : x + 1; }
+
+}  // namespace lbmsc

@@ -1,0 +1,389 @@
+// Fused two-component Shan-Chen step on sm_103a.
+//
+// One kernel performs a whole time step of Eq. eq:be with the force of
+// Eq. FORCE (paper Sec. 2.1): pull-streaming of both species' populations,
+// densities and momenta, the neighbour-density force, the common velocity u',
+// the velocity-shifted equilibrium and BGK relaxation, and the store.
+//
+// Storage: structure of arrays, plane (s*Q + i) holds f_is for all N nodes,
+// node index x + nx*(y + ny*z).  The buffer holds post-collision values at the
+// node where they were produced; pulling f_i(x, t) = f*_i(x - c_i, t - 1) is the
+// streaming step, so stores are always aligned and coalesced.
+//
+// Tiling: a CTA owns a TX x TY tile of (x, y) columns and marches along z over
+// a chunk of planes.  The force at plane z needs the densities of planes z-1,
+// z, z+1 on the tile plus a one-node ring; they live in a three-plane ring of
+// shared memory.  Each iteration pulls the populations of plane z+1 (kept in
+// registers for the next iteration), writes their densities to the ring,
+// computes the densities of the ring's halo nodes (extra pulls served mostly
+// by L2, since neighbouring tiles read the same lines at about the same time),
+// then collides plane z.  The halo costs 2(TX+TY)+4 extra density pulls per
+// TX*TY nodes of a plane, in x and y only: marching removes the z halo.
+#pragma once
+
+#include "sc_common.cuh"
+
+namespace lbmsc {
+
+enum KernelMode { kModeStep = 0, kModeMoments = 1 };
+
+template <class L, class S>
+__device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y, int z,
+                                          typename Codec<S>::C (&f)[2][L::Q]) {
+    using C = typename Codec<S>::C;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int xs[3] = {wrap_inc(x, nx), x, wrap_dec(x, nx)};  // source x for c_x = -1, 0, +1
+    const int ys[3] = {wrap_inc(y, ny), y, wrap_dec(y, ny)};
+    int zs[3] = {z, z, z};
+    if (L::D == 3) {
+        zs[0] = wrap_inc(z, nz);
+        zs[2] = wrap_dec(z, nz);
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int sx = xs[L::c(i, 0) + 1], sy = ys[L::c(i, 1) + 1], sz = zs[L::c(i, 2) + 1];
+        const long long node = (long long)sx + (long long)nx * ((long long)sy + (long long)ny * sz);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+            f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.N + node, off);
+        }
+    }
+}
+
+template <int Q, class C>
+__device__ __forceinline__ C sum_q(const C (&f)[Q]) {
+    C r = f[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) r += f[i];
+    return r;
+}
+
+// BGK relaxation of one species towards f^eq(rho, u) (second-order truncated
+// Maxwellian with cs2 = 1/3): f += omega (f^eq - f).
+template <class L, class C>
+__device__ __forceinline__ void relax(C (&f)[L::Q], C rho, const C (&u)[3], C omega) {
+    C uu = u[0] * u[0] + u[1] * u[1];
+    if (L::D == 3) uu += u[2] * u[2];
+    const C base = (C)1 - (C)1.5 * uu;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        C cu = (C)0;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) cu += u[d];
+            if (L::c(i, d) == -1) cu -= u[d];
+        }
+        const C feq = (C)L::w(i) * rho * (base + cu * ((C)3 + (C)4.5 * cu));
+        f[i] += omega * (feq - f[i]);
+    }
+}
+
+template <class L, class S, int TX, int TY, int MODE, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    sc_fused_kernel(const LatticeArgs<S> a, const FieldArgs<typename Codec<S>::C> fo) {
+    using C = typename Codec<S>::C;
+    constexpr int Q = L::Q;
+    constexpr int FX = TX + 2, FY = TY + 2;
+    constexpr int NPL = L::D == 3 ? 3 : 1;
+    constexpr int H = 2 * FX + 2 * TY;
+    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
+    __shared__ C srho[NPL][2][FY][FX];
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
+    const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+
+    // Halo ring cell handled by this thread (frame coordinates; frame (1,1) = tile (0,0)).
+    const bool halo = tid < H;
+    int hfx = 0, hfy = 0;
+    if (tid < FX) {
+        hfx = tid;
+        hfy = 0;
+    } else if (tid < 2 * FX) {
+        hfx = tid - FX;
+        hfy = FY - 1;
+    } else if (tid < 2 * FX + TY) {
+        hfx = 0;
+        hfy = tid - 2 * FX + 1;
+    } else {
+        hfx = FX - 1;
+        hfy = tid - 2 * FX - TY + 1;
+    }
+    const int hgx = (x0 - 1 + hfx + nx) % nx;
+    const int hgy = (y0 - 1 + hfy + ny) % ny;
+
+    // Diagnostics accumulators (moments mode).
+    double acc[kNumDiag];
+    if (MODE == kModeMoments) {
+#pragma unroll
+        for (int k = 0; k < kNumDiag; ++k) acc[k] = 0.0;
+        acc[kMinRhoA] = 1e300;
+        acc[kMinRhoB] = 1e300;
+    }
+
+    auto density_plane = [&](int slot, int z, C (&f)[2][Q], bool keep_own) {
+        // own column: pull (kept in f), densities to the ring
+        pull_node<L, S>(a, gx, gy, z, f);
+        srho[slot][0][ty + 1][tx + 1] = sum_q<Q>(f[0]);
+        srho[slot][1][ty + 1][tx + 1] = sum_q<Q>(f[1]);
+        (void)keep_own;
+        if (halo) {
+            C h[2][Q];
+            pull_node<L, S>(a, hgx, hgy, z, h);
+            srho[slot][0][hfy][hfx] = sum_q<Q>(h[0]);
+            srho[slot][1][hfy][hfx] = sum_q<Q>(h[1]);
+        }
+    };
+
+    auto process = [&](C (&f)[2][Q], int sm, int sc, int sp, int z) {
+        const C rA = srho[sc][0][ty + 1][tx + 1];
+        const C rB = srho[sc][1][ty + 1][tx + 1];
+        C jA[3] = {0, 0, 0}, jB[3] = {0, 0, 0};
+        C gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0};  // sum_i w_i rho_s'(x + c_i) c_i
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+#pragma unroll
+            for (int d = 0; d < L::D; ++d) {
+                if (L::c(i, d) == 1) { jA[d] += f[0][i]; jB[d] += f[1][i]; }
+                if (L::c(i, d) == -1) { jA[d] -= f[0][i]; jB[d] -= f[1][i]; }
+            }
+            const int slot = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
+            const C wA = (C)L::w(i) * srho[slot][0][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+            const C wB = (C)L::w(i) * srho[slot][1][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+#pragma unroll
+            for (int d = 0; d < L::D; ++d) {
+                if (L::c(i, d) == 1) { gA[d] += wB; gB[d] += wA; }
+                if (L::c(i, d) == -1) { gA[d] -= wB; gB[d] -= wA; }
+            }
+        }
+        // F_s / rho_s = -G sum_i w_i rho_s'(x + c_i) c_i   (Eq. FORCE)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            gA[d] *= -a.G;
+            gB[d] *= -a.G;
+        }
+        if (MODE == kModeStep) {
+            // common velocity u' = sum_s j_s / tau_s / sum_s rho_s / tau_s, shifted by tau_s F_s / rho_s
+            const C inv_den = (C)1 / (rA * a.omega_A + rB * a.omega_B);
+            C uA[3], uB[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const C up = (jA[d] * a.omega_A + jB[d] * a.omega_B) * inv_den;
+                uA[d] = up + a.tau_A * gA[d];
+                uB[d] = up + a.tau_B * gB[d];
+            }
+            relax<L, C>(f[0], rA, uA, a.omega_A);
+            relax<L, C>(f[1], rB, uB, a.omega_B);
+            if (owner) {
+                const long long node = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * z);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                        Codec<S>::store(a.fout + (size_t)(s * Q + i) * (size_t)a.N + node, f[s][i], off);
+                    }
+                }
+            }
+        } else {
+            // physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2 shift, Sec. 2.3)
+            const C rho = rA + rB;
+            C u[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                u[d] = (jA[d] + jB[d] + (C)0.5 * (rA * gA[d] + rB * gB[d])) / rho;
+            const C p = (rho + a.G * rA * rB) * (C)(1.0 / 3.0);
+            if (owner) {
+                const long long node = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * z);
+                if (fo.rhoA) fo.rhoA[node] = rA;
+                if (fo.rhoB) fo.rhoB[node] = rB;
+                if (fo.u)
+#pragma unroll
+                    for (int d = 0; d < L::D; ++d) fo.u[(size_t)d * (size_t)a.N + node] = u[d];
+                if (fo.p) fo.p[node] = p;
+                if (fo.partials) {
+                    const double dA = (double)rA, dB = (double)rB, drho = dA + dB;
+                    double m[3], uu = 0.0;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        m[d] = (double)u[d] * drho;
+                        uu += (double)u[d] * (double)u[d];
+                    }
+                    const bool finite = isfinite(dA) && isfinite(dB) && isfinite(uu) && isfinite((double)p);
+                    if (finite) {
+                        acc[kMassA] += dA;
+                        acc[kMassB] += dB;
+                        acc[kMomX] += m[0];
+                        acc[kMomY] += m[1];
+                        acc[kMomZ] += m[2];
+                        acc[kKE] += 0.5 * drho * uu;
+                        acc[kMaxSpeed] = fmax(acc[kMaxSpeed], sqrt(uu));
+                        acc[kMinRhoA] = fmin(acc[kMinRhoA], dA);
+                        acc[kMinRhoB] = fmin(acc[kMinRhoB], dB);
+                    } else {
+                        acc[kNonFinite] += 1.0;
+                    }
+                    // periodic minimum-image distance from the window centre
+                    double dx = fabs((double)gx - fo.win_c[0]);
+                    double dy = fabs((double)gy - fo.win_c[1]);
+                    double dz = fabs((double)z - fo.win_c[2]);
+                    dx = fmin(dx, (double)nx - dx);
+                    dy = fmin(dy, (double)ny - dy);
+                    dz = fmin(dz, (double)nz - dz);
+                    const double r2 = dx * dx + dy * dy + (L::D == 3 ? dz * dz : 0.0);
+                    if (r2 < fo.r_in2) {
+                        acc[kInCount] += 1.0;
+                        acc[kInRhoA] += dA;
+                        acc[kInP] += (double)p;
+                    }
+                    if (r2 > fo.r_out2) {
+                        acc[kOutCount] += 1.0;
+                        acc[kOutRhoA] += dA;
+                        acc[kOutP] += (double)p;
+                    }
+                }
+            }
+        }
+    };
+
+    C cur[2][Q];
+    if (L::D == 2) {
+        density_plane(0, 0, cur, true);
+        __syncthreads();
+        process(cur, 0, 0, 0, 0);
+    } else {
+        const int z0 = blockIdx.z * a.zchunk;
+        const int z1 = min(z0 + a.zchunk, nz);
+        {
+            C tmp[2][Q];
+            density_plane(0, z0 == 0 ? nz - 1 : z0 - 1, tmp, false);
+        }
+        density_plane(1, z0, cur, true);
+        int sm = 0, sc = 1, sp = 2;
+        for (int z = z0; z < z1; ++z) {
+            C nxt[2][Q];
+            density_plane(sp, z + 1 == nz ? 0 : z + 1, nxt, true);
+            __syncthreads();
+            process(cur, sm, sc, sp, z);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < Q; ++i) cur[s][i] = nxt[s][i];
+            const int t = sm;
+            sm = sc;
+            sc = sp;
+            sp = t;
+            __syncthreads();
+        }
+    }
+
+    if (MODE == kModeMoments && fo.partials) {
+        // CTA reduction of the diagnostics: warp shuffles, then one warp over the warps.
+        constexpr int NW = TX * TY / 32;
+        __shared__ double red[NW][kNumDiag];
+        const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int k = 0; k < kNumDiag; ++k) {
+            double v = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = (k == kMaxSpeed) ? fmax(v, w) : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, w) : v + w;
+            }
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (tid < kNumDiag) {
+            const int k = tid;
+            double v = red[0][k];
+            for (int w = 1; w < NW; ++w)
+                v = (k == kMaxSpeed) ? fmax(v, red[w][k])
+                    : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, red[w][k]) : v + red[w][k];
+            const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+            fo.partials[b * kNumDiag + k] = v;
+        }
+    }
+}
+
+// Second pass of the diagnostics: one CTA folds the per-CTA partials.
+template <int NT>
+__global__ void __launch_bounds__(NT) sc_diag_finish_kernel(const double* __restrict__ partials,
+                                                            long long nparts, double* __restrict__ out) {
+    __shared__ double red[NT / 32][kNumDiag];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double acc[kNumDiag];
+#pragma unroll
+    for (int k = 0; k < kNumDiag; ++k) acc[k] = 0.0;
+    acc[kMinRhoA] = 1e300;
+    acc[kMinRhoB] = 1e300;
+    for (long long b = tid; b < nparts; b += NT) {
+#pragma unroll
+        for (int k = 0; k < kNumDiag; ++k) {
+            const double v = partials[b * kNumDiag + k];
+            acc[k] = (k == kMaxSpeed) ? fmax(acc[k], v)
+                     : (k == kMinRhoA || k == kMinRhoB) ? fmin(acc[k], v) : acc[k] + v;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kNumDiag; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = (k == kMaxSpeed) ? fmax(v, w) : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, w) : v + w;
+        }
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (tid < kNumDiag) {
+        const int k = tid;
+        double v = red[0][k];
+        for (int w = 1; w < NT / 32; ++w)
+            v = (k == kMaxSpeed) ? fmax(v, red[w][k])
+                : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, red[w][k]) : v + red[w][k];
+        out[k] = v;
+    }
+}
+
+// Populations of the rest / moving equilibrium: the buffer slot of direction i
+// at node x holds f^eq_i(rho_s(x + c_i), u(x + c_i)), so pulling it at x + c_i
+// gives f_i(x + c_i, 0) = f^eq_i of that node.
+template <class L, class S>
+__global__ void __launch_bounds__(256)
+    sc_init_kernel(const LatticeArgs<S> a, const typename Codec<S>::C* __restrict__ rhoA,
+                   const typename Codec<S>::C* __restrict__ rhoB, const typename Codec<S>::C* __restrict__ u) {
+    using C = typename Codec<S>::C;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(n % nx);
+        const int y = (int)((n / nx) % ny);
+        const int z = (int)(n / ((long long)nx * ny));
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const int sx = (x + L::c(i, 0) + nx) % nx;
+            const int sy = (y + L::c(i, 1) + ny) % ny;
+            const int sz = L::D == 3 ? (z + L::c(i, 2) + nz) % nz : 0;
+            const long long m = (long long)sx + (long long)nx * ((long long)sy + (long long)ny * sz);
+            C uv[3] = {0, 0, 0};
+            if (u)
+                for (int d = 0; d < L::D; ++d) uv[d] = u[(size_t)d * (size_t)a.N + m];
+            C uu = uv[0] * uv[0] + uv[1] * uv[1] + uv[2] * uv[2];
+            C cu = (C)0;
+            for (int d = 0; d < L::D; ++d) cu += (C)L::c(i, d) * uv[d];
+            const C shape = (C)1 - (C)1.5 * uu + cu * ((C)3 + (C)4.5 * cu);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const C rho = s == 0 ? rhoA[m] : rhoB[m];
+                const C f = (C)L::w(i) * rho * shape;
+                const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.N + n, f, off);
+            }
+        }
+    }
+}
+
+}  // namespace lbmsc

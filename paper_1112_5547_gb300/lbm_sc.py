@@ -1,0 +1,302 @@
+"""Thin ctypes binding of liblbm_sc.so (C ABI in include/lbm_sc.h).
+
+Every function with an ``lbm_sc_`` name marshals its arguments and calls the
+C entry point of the same name; all lattice arithmetic runs in the library's
+CUDA kernels.  PyTorch is used only to own device memory and streams.  There is
+no fallback: if the compiled library is missing the import fails loudly.
+
+``Lattice`` bundles a workspace tensor and a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm_sc.so")
+
+LBM_OK = 0
+LBM_ERR_INVALID_ARG = 1
+LBM_ERR_OUT_OF_MEMORY = 2
+LBM_ERR_CUDA = 3
+LBM_ERR_UNSTABLE = 4
+LBM_ERR_TIMEOUT = 5
+
+LBM_D2Q9 = 0
+LBM_D3Q19 = 1
+
+LBM_F64 = 0
+LBM_F32 = 1
+LBM_F32_STORE_BF16 = 2
+LBM_F32_STORE_F16 = 3
+
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_F32_STORE_BF16, "f16": LBM_F32_STORE_F16}
+
+# Every entry point declared in include/lbm_sc.h.
+EXPORTS = (
+    "lbm_sc_workspace_bytes", "lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step",
+    "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
+    "lbm_sc_destroy", "lbm_sc_status_string",
+)
+
+
+class lbm_sc_params(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double), ("G", ctypes.c_double),
+                ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double)]
+
+
+class lbm_sc_window(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+                ("r_in", ctypes.c_double), ("r_out", ctypes.c_double)]
+
+
+class lbm_sc_diag(ctypes.Structure):
+    _fields_ = [("mass_A", ctypes.c_double), ("mass_B", ctypes.c_double), ("momentum", ctypes.c_double * 3),
+                ("kinetic_energy", ctypes.c_double), ("max_speed", ctypes.c_double),
+                ("min_rho_A", ctypes.c_double), ("min_rho_B", ctypes.c_double), ("nonfinite", ctypes.c_double),
+                ("in_count", ctypes.c_double), ("in_rho_A", ctypes.c_double), ("in_p", ctypes.c_double),
+                ("out_count", ctypes.c_double), ("out_rho_A", ctypes.c_double), ("out_p", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "momentum"}
+        d["momentum"] = tuple(self.momentum)
+        return d
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s" % (where, lbm_sc_status_string(status)))
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm_sc.so (built by paper_1112_5547_gb300.build).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("liblbm_sc.so not found at %s: run paper_1112_5547_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    P = ctypes.POINTER(lbm_sc_params)
+    lib.lbm_sc_workspace_bytes.argtypes = [P]
+    lib.lbm_sc_workspace_bytes.restype = ctypes.c_size_t
+    lib.lbm_sc_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    lib.lbm_sc_set_stream.argtypes = [vp, vp]
+    lib.lbm_sc_init_fields.argtypes = [vp, vp, vp, vp]
+    lib.lbm_sc_step.argtypes = [vp, ctypes.c_int]
+    lib.lbm_sc_moments.argtypes = [vp, vp, vp, vp, vp]
+    lib.lbm_sc_diagnostics.argtypes = [vp, ctypes.POINTER(lbm_sc_window), ctypes.POINTER(lbm_sc_diag)]
+    lib.lbm_sc_host_staging_bytes.argtypes = [P]
+    lib.lbm_sc_host_staging_bytes.restype = ctypes.c_size_t
+    lib.lbm_sc_run_host.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.lbm_sc_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(vp)]
+    lib.lbm_sc_destroy.argtypes = [vp]
+    lib.lbm_sc_destroy.restype = None
+    lib.lbm_sc_status_string.argtypes = [ctypes.c_int]
+    lib.lbm_sc_status_string.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        getattr(lib, name)
+    for name in ("lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step", "lbm_sc_moments",
+                 "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != LBM_OK:
+        raise LbmError(status, where)
+
+
+def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
+                rho_ref_A: float = 0.0, rho_ref_B: float = 0.0) -> lbm_sc_params:
+    """Parameters for a lattice of numpy-style shape (ny, nx) or (nz, ny, nx)."""
+    shape = tuple(int(s) for s in shape)
+    if len(shape) == 2:
+        nz, (ny, nx) = 1, shape
+    else:
+        nz, ny, nx = shape
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return lbm_sc_params(int(lattice), prec, nx, ny, nz, 0, float(tau_A), float(tau_B), float(G),
+                         float(rho_ref_A), float(rho_ref_B))
+
+
+# ---- one Python function per C entry point ----------------------------------
+def lbm_sc_workspace_bytes(params: lbm_sc_params) -> int:
+    return int(load().lbm_sc_workspace_bytes(ctypes.byref(params)))
+
+
+def lbm_sc_host_staging_bytes(params: lbm_sc_params) -> int:
+    return int(load().lbm_sc_host_staging_bytes(ctypes.byref(params)))
+
+
+def lbm_sc_create(params: lbm_sc_params, d_workspace: int, workspace_bytes: int, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().lbm_sc_create(ctypes.byref(params), ctypes.c_void_p(d_workspace), ctypes.c_size_t(workspace_bytes),
+                                ctypes.c_void_p(stream), ctypes.byref(h)), "lbm_sc_create")
+    return h.value
+
+
+def lbm_sc_set_stream(h: int, stream: int) -> None:
+    _check(load().lbm_sc_set_stream(ctypes.c_void_p(h), ctypes.c_void_p(stream)), "lbm_sc_set_stream")
+
+
+def lbm_sc_init_fields(h: int, d_rhoA: int, d_rhoB: int, d_u: Optional[int] = None) -> None:
+    _check(load().lbm_sc_init_fields(ctypes.c_void_p(h), ctypes.c_void_p(d_rhoA), ctypes.c_void_p(d_rhoB),
+                                     ctypes.c_void_p(d_u or 0)), "lbm_sc_init_fields")
+
+
+def lbm_sc_step(h: int, nsteps: int) -> None:
+    _check(load().lbm_sc_step(ctypes.c_void_p(h), int(nsteps)), "lbm_sc_step")
+
+
+def lbm_sc_moments(h: int, d_rhoA=None, d_rhoB=None, d_u=None, d_p=None) -> None:
+    _check(load().lbm_sc_moments(ctypes.c_void_p(h), ctypes.c_void_p(d_rhoA or 0), ctypes.c_void_p(d_rhoB or 0),
+                                 ctypes.c_void_p(d_u or 0), ctypes.c_void_p(d_p or 0)), "lbm_sc_moments")
+
+
+def lbm_sc_diagnostics(h: int, window: Optional[lbm_sc_window] = None, check: bool = True):
+    """Returns (status, lbm_sc_diag).  With check=True a status other than LBM_OK raises."""
+    out = lbm_sc_diag()
+    st = load().lbm_sc_diagnostics(ctypes.c_void_p(h), ctypes.byref(window) if window is not None else None,
+                                   ctypes.byref(out))
+    if check:
+        _check(st, "lbm_sc_diagnostics")
+    return st, out
+
+
+def lbm_sc_run_host(h: int, d_staging: int, staging_bytes: int, h_rhoA: int, h_rhoB: int, h_u: Optional[int],
+                    nsteps: int, h_rhoA_out=None, h_rhoB_out=None, h_u_out=None, h_p_out=None) -> None:
+    v = ctypes.c_void_p
+    _check(load().lbm_sc_run_host(v(h), v(d_staging), ctypes.c_size_t(staging_bytes), v(h_rhoA), v(h_rhoB),
+                                  v(h_u or 0), int(nsteps), v(h_rhoA_out or 0), v(h_rhoB_out or 0), v(h_u_out or 0),
+                                  v(h_p_out or 0)), "lbm_sc_run_host")
+
+
+def lbm_sc_layout(h: int):
+    eb, q, ptr = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+    _check(load().lbm_sc_layout(ctypes.c_void_p(h), ctypes.byref(eb), ctypes.byref(q), ctypes.byref(ptr)),
+           "lbm_sc_layout")
+    return eb.value, q.value, ptr.value
+
+
+def lbm_sc_destroy(h: int) -> None:
+    load().lbm_sc_destroy(ctypes.c_void_p(h))
+
+
+def lbm_sc_status_string(status: int) -> str:
+    return load().lbm_sc_status_string(int(status)).decode()
+
+
+# ---- convenience wrapper over torch-owned device memory ---------------------
+@dataclass
+class Window:
+    centre: tuple
+    r_in: float
+    r_out: float
+
+    def to_c(self) -> lbm_sc_window:
+        c = list(self.centre) + [0.0] * (3 - len(self.centre))
+        return lbm_sc_window(float(c[0]), float(c[1]), float(c[2]), float(self.r_in), float(self.r_out))
+
+
+class Lattice:
+    """A lattice whose workspace is a torch uint8 tensor on ``device``.
+
+    ``shape`` is numpy order: (ny, nx) for D2Q9, (nz, ny, nx) for D3Q19.
+    """
+
+    def __init__(self, lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
+                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B)
+        self.shape = tuple(int(s) for s in shape)
+        self.lattice = int(lattice)
+        self.D = 2 if self.lattice == LBM_D2Q9 else 3
+        self.N = int(np.prod(self.shape))
+        self.cdtype = torch.float64 if self.params.precision == LBM_F64 else torch.float32
+        nbytes = lbm_sc_workspace_bytes(self.params)
+        if nbytes == 0:
+            raise LbmError(LBM_ERR_INVALID_ARG, "lbm_sc_workspace_bytes")
+        self.device = torch.device(device)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = lbm_sc_create(self.params, aligned, nbytes, self.stream.cuda_stream)
+        self.workspace_bytes = nbytes
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_sc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a):
+        t = self.torch
+        if isinstance(a, np.ndarray):
+            a = t.from_numpy(np.ascontiguousarray(a))
+        return a.to(device=self.device, dtype=self.cdtype).contiguous()
+
+    def init(self, rhoA, rhoB, u=None):
+        """rhoA, rhoB of ``shape``; u of shape + (D,) (component last) or None."""
+        self._keep = [self._dev(rhoA).reshape(-1), self._dev(rhoB).reshape(-1)]
+        du = None
+        if u is not None:
+            uu = self._dev(u).reshape(-1, self.D).t().contiguous()
+            self._keep.append(uu)
+            du = uu.data_ptr()
+        lbm_sc_init_fields(self.handle, self._keep[0].data_ptr(), self._keep[1].data_ptr(), du)
+        return self
+
+    def step(self, nsteps: int = 1):
+        lbm_sc_step(self.handle, nsteps)
+        return self
+
+    def moments(self):
+        """(rho_A, rho_B, u (shape + (D,)), p) as device tensors in the compute dtype."""
+        t = self.torch
+        rA = t.empty(self.N, dtype=self.cdtype, device=self.device)
+        rB = t.empty_like(rA)
+        u = t.empty(self.D * self.N, dtype=self.cdtype, device=self.device)
+        p = t.empty_like(rA)
+        lbm_sc_moments(self.handle, rA.data_ptr(), rB.data_ptr(), u.data_ptr(), p.data_ptr())
+        u = u.view(self.D, self.N).t().reshape(self.shape + (self.D,))
+        return rA.view(self.shape), rB.view(self.shape), u, p.view(self.shape)
+
+    def diagnostics(self, window: Optional[Window] = None, check: bool = True):
+        st, d = lbm_sc_diagnostics(self.handle, window.to_c() if window is not None else None, check=check)
+        out = d.as_dict()
+        out["status"] = st
+        return out
+
+    def populations(self):
+        """The current population buffer as a (2, Q, N) tensor view (GPU velocity order)."""
+        t = self.torch
+        eb, q, ptr = lbm_sc_layout(self.handle)
+        dt = {8: t.float64, 4: t.float32}.get(eb)
+        if dt is None:
+            dt = t.bfloat16 if self.params.precision == LBM_F32_STORE_BF16 else t.float16
+        base = self.workspace.data_ptr()
+        off = ptr - base
+        n = 2 * q * self.N
+        return self.workspace[off: off + n * eb].view(dt).view(2, q, self.N)

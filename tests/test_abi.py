@@ -1,0 +1,92 @@
+"""The C-ABI library loads on a machine without a GPU, exports every entry point
+declared in include/lbm_sc.h, and its host-only calls validate arguments."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1112_5547_gb300 import build, lbm_sc
+    build.build()
+    return lbm_sc
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_sc_\w+)\s*\(", src))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 12
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(so, name), name
+    assert declared == set(lib.EXPORTS) | (declared - set(lib.EXPORTS))
+    assert set(lib.EXPORTS) <= declared
+
+
+def test_workspace_sizes(lib):
+    p = lib.make_params(lib.LBM_D3Q19, (10, 12, 14), 1.0, 1.0, 2.0, "f32")
+    n = 10 * 12 * 14
+    ws = lib.lbm_sc_workspace_bytes(p)
+    assert ws >= 2 * 2 * 19 * n * 4
+    p16 = lib.make_params(lib.LBM_D3Q19, (10, 12, 14), 1.0, 1.0, 2.0, "bf16")
+    assert lib.lbm_sc_workspace_bytes(p16) < ws
+    p64 = lib.make_params(lib.LBM_D2Q9, (12, 14), 1.0, 1.0, 2.0, "f64")
+    assert lib.lbm_sc_workspace_bytes(p64) >= 2 * 2 * 9 * 12 * 14 * 8
+    assert lib.lbm_sc_host_staging_bytes(p) >= 6 * n * 4
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau_A=0.5), dict(tau_B=0.3), dict(nx=0), dict(ny=-1), dict(nz=0), dict(lattice=7), dict(precision=9),
+])
+def test_invalid_params_rejected(lib, bad):
+    p = lib.make_params(lib.LBM_D3Q19, (4, 4, 4), 1.0, 1.0, 2.0, "f32")
+    for k, v in bad.items():
+        setattr(p, k, v)
+    assert lib.lbm_sc_workspace_bytes(p) == 0
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_sc_create(p, 1 << 20, 1 << 30, 0)
+    assert e.value.status == lib.LBM_ERR_INVALID_ARG
+
+
+def test_d2q9_requires_nz_1_and_size_limit(lib):
+    p = lib.make_params(lib.LBM_D2Q9, (4, 4), 1.0, 1.0, 2.0, "f32")
+    p.nz = 2
+    assert lib.lbm_sc_workspace_bytes(p) == 0
+    big = lib.make_params(lib.LBM_D3Q19, (2048, 1024, 1024), 1.0, 1.0, 2.0, "f32")
+    assert lib.lbm_sc_workspace_bytes(big) == 0  # N >= 2^31
+
+
+def test_create_checks_workspace_without_touching_the_gpu(lib):
+    p = lib.make_params(lib.LBM_D2Q9, (8, 8), 1.0, 1.0, 2.0, "f32")
+    need = lib.lbm_sc_workspace_bytes(p)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_sc_create(p, 256 * 1024, need - 1, 0)
+    assert e.value.status == lib.LBM_ERR_OUT_OF_MEMORY
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_sc_create(p, 256 * 1024 + 8, need, 0)  # misaligned
+    assert e.value.status == lib.LBM_ERR_INVALID_ARG
+    h = lib.lbm_sc_create(p, 256 * 1024, need, 0)  # a fake address: create does not dereference it
+    eb, q, ptr = lib.lbm_sc_layout(h)
+    assert (eb, q, ptr) == (4, 9, 256 * 1024)
+    with pytest.raises(lib.LbmError):
+        lib.lbm_sc_step(h, -1)
+    lib.lbm_sc_destroy(h)
+
+
+def test_status_strings(lib):
+    for s in range(6):
+        assert lib.lbm_sc_status_string(s).startswith("LBM_")
+    assert "unknown" in lib.lbm_sc_status_string(99)
