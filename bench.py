@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--tile", type=int, default=-1, help="force a step tile (skips the autotuner)")
+    ap.add_argument("--zchunk", type=int, default=0)
     return ap.parse_args()
 
 
@@ -205,6 +207,15 @@ def main():
     with torch.cuda.stream(stream):
         lat.init(rA, rB)
     stream.synchronize()
+    # launch shape: autotuned on this lattice (state restored), or forced
+    if args.tile >= 0:
+        lat.set_tuning(args.tile, args.zchunk)
+        tune_info = {"tile": list(lbm_sc.TILES[args.tile]), "zchunk": lat.tuning()[1], "source": "forced"}
+    else:
+        from paper_1112_5547_gb300 import autotune
+        (tile, zc), table = autotune.autotune(lat)
+        tune_info = {"tile": list(lbm_sc.TILES[tile]), "zchunk": zc, "source": "autotuned",
+                     "candidates": len(table)}
 
     # warm-up
     lat.step(args.warmup)
@@ -297,7 +308,7 @@ def main():
         "config": {"workload": "D3Q19 %d^3 two-component SC drop R=L/4, tau=1, G*rho_tot=2.4, seed 2" % L,
                    "lattice": "D3Q19", "L": L, "nodes": N, "storage": prec,
                    "l2": "inputs larger than L2 (%.1f GB per population buffer)" % (N * 38 * BYTES_PER_VALUE[prec] / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "step_launch": tune_info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_lu": bytes_per_lu,

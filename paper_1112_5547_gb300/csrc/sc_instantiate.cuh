@@ -1,7 +1,10 @@
 // Typed launch helpers shared by the per-lattice translation units.
 #pragma once
 
+#include "sc_async.cuh"
 #include "sc_kernels.cuh"
+#include "sc_pipe.cuh"
+#include "sc_regpipe.cuh"
 #include "sc_launch.cuh"
 
 namespace lbmsc {
@@ -26,18 +29,129 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     return a;
 }
 
-// Minimum CTAs per SM requested from the register allocator: two 256-thread
-// CTAs for 32-bit compute, one for FP64 (whose 76 live doubles would spill).
-template <class S> struct MinBlocks { static constexpr int value = 2; };
-template <> struct MinBlocks<double> { static constexpr int value = 1; };
+template <class L, class S, int TX, int TY>
+cudaError_t step_tiled(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+    using C = typename Codec<S>::C;
+    FieldArgs<C> fo{};
+    // register budget: 65536 / (threads * CTAs per SM)
+    constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : (TX * TY <= 256 ? 2 : 1));
+    sc_fused_kernel<L, S, TX, TY, kModeStep, kMin><<<step_grid(p), dim3(TX, TY), 0, st>>>(a, fo);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY, int STAGES>
+cudaError_t step_async(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
+    using T = AsyncTile<TX, TY, STAGES>;
+    auto kern = sc_step_async_kernel<TX, TY, STAGES>;
+    // the attribute is per function and device: set it on every launch (a cheap host call)
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, T::smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int tiles_x = (p.nx + TX - 1) / TX, tiles_y = (p.ny + TY - 1) / TY;
+    const int nchunks = (p.nz + p.step_zchunk - 1) / p.step_zchunk;
+    const long long items = (long long)tiles_x * tiles_y * nchunks;
+    long long grid = (long long)p.sm_count * per_sm;
+    if (grid > items) grid = items;
+    kern<<<(unsigned)grid, dim3(TX, TY), T::smem_bytes, st>>>(a, tiles_x, tiles_y, nchunks);
+    return cudaGetLastError();
+}
+
+template <class L, class S, int TX, int TY, int MINB>
+cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+    using C = typename Codec<S>::C;
+    constexpr int kMin = sizeof(C) == 8 ? (MINB > 2 ? MINB / 2 : 1) : MINB;
+    sc_step_reload_kernel<L, S, TX, TY, kMin><<<step_grid(p), dim3(TX, TY), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class L, class S, int TX, int TY, int MINB> struct RegPipeLaunch {
+    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
+};
+template <class S, int TX, int TY, int MINB> struct RegPipeLaunch<D3Q19, S, TX, TY, MINB> {
+    static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+        if constexpr (sizeof(S) == 8) {
+            return cudaErrorInvalidValue;  // three planes of doubles do not fit in registers
+        } else {
+            sc_step_regpipe_kernel<S, TX, TY, MINB><<<step_grid(p), dim3(TX, TY), 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
+};
+
+template <class S, int TX, int TY>
+cudaError_t step_pipe(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+    using T = PipeTile<S, TX, TY>;
+    using C = typename Codec<S>::C;
+    constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 3 : 2);
+    auto kern = sc_step_pipe_kernel<S, TX, TY, kMin>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((p.nx + TX - 1) / TX), (unsigned)((p.ny + TY - 1) / TY),
+                    (unsigned)((p.nz + p.step_zchunk - 1) / p.step_zchunk));
+    kern<<<grid, dim3(TX, TY), T::smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class L, class S> struct PipeDispatch {
+    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
+};
+template <class S> struct PipeDispatch<D3Q19, S> {
+    static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+        switch (p.step_tile) {
+            case 8: return step_pipe<S, 32, 8>(p, a, st);
+            case 9: return step_pipe<S, 64, 4>(p, a, st);
+            case 10: return step_pipe<S, 32, 4>(p, a, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+};
+
+template <class L, class S> struct AsyncDispatch {
+    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
+};
+template <> struct AsyncDispatch<D3Q19, float> {
+    static cudaError_t run(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
+        switch (p.step_tile) {
+            case 5: return step_async<32, 8, 3>(p, a, st);
+            case 6: return step_async<32, 8, 4>(p, a, st);
+            case 7: return step_async<64, 4, 3>(p, a, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+};
 
 template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fin, void* fout, cudaStream_t st) {
-    using C = typename Codec<S>::C;
-    const LatticeArgs<S> a = make_args<S>(p, fin, fout);
-    FieldArgs<C> fo{};
-    sc_fused_kernel<L, S, kTX, kTY, kModeStep, MinBlocks<S>::value>
-        <<<fused_grid(p), dim3(kTX, kTY), 0, st>>>(a, fo);
-    return cudaGetLastError();
+    LatticeArgs<S> a = make_args<S>(p, fin, fout);
+    a.zchunk = p.step_zchunk;
+    static_assert(kTiles[0].tx == 32 && kTiles[0].ty == 8 && kTiles[1].ty == 16 && kTiles[2].tx == 64 &&
+                      kTiles[3].ty == 4 && kTiles[4].tx == 64 && kTiles[5].stages == 3 && kTiles[6].stages == 4 &&
+                      kTiles[7].tx == 64 && kTiles[8].kind == 2 && kTiles[9].tx == 64 && kTiles[10].ty == 4 &&
+                      kTiles[11].stages == 6 && kTiles[12].ty == 8 && kTiles[13].tx == 64 && kTiles[14].stages == 4 &&
+                      kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kNumTiles == 18,
+                  "tile table and dispatch disagree");
+    switch (p.step_tile) {
+        case 0: return step_tiled<L, S, 32, 8>(p, a, st);
+        case 1: return step_tiled<L, S, 32, 16>(p, a, st);
+        case 2: return step_tiled<L, S, 64, 8>(p, a, st);
+        case 3: return step_tiled<L, S, 32, 4>(p, a, st);
+        case 4: return step_tiled<L, S, 64, 4>(p, a, st);
+        case 5:
+        case 6:
+        case 7: return AsyncDispatch<L, S>::run(p, a, st);
+        case 8:
+        case 9:
+        case 10: return PipeDispatch<L, S>::run(p, a, st);
+        case 11: return step_reload<L, S, 32, 4, 6>(p, a, st);
+        case 12: return step_reload<L, S, 32, 8, 3>(p, a, st);
+        case 13: return step_reload<L, S, 64, 4, 3>(p, a, st);
+        case 14: return step_reload<L, S, 32, 4, 4>(p, a, st);
+        case 15: return RegPipeLaunch<L, S, 32, 4, 3>::run(p, a, st);
+        case 16: return RegPipeLaunch<L, S, 32, 8, 1>::run(p, a, st);
+        case 17: return RegPipeLaunch<L, S, 16, 8, 3>::run(p, a, st);
+    }
 }
 
 template <class L, class S>

@@ -1,9 +1,11 @@
-// Fused two-component Shan-Chen step on sm_103a.
+// Fused two-component Shan-Chen step on sm_103a: register-pipelined kernel,
+// moments / diagnostics kernel, initialisation and the diagnostics fold.
 //
 // One kernel performs a whole time step of Eq. eq:be with the force of
 // Eq. FORCE (paper Sec. 2.1): pull-streaming of both species' populations,
 // densities and momenta, the neighbour-density force, the common velocity u',
-// the velocity-shifted equilibrium and BGK relaxation, and the store.
+// the velocity-shifted equilibrium and BGK relaxation, and the store.  The
+// per-node arithmetic is in sc_node.cuh.
 //
 // Storage: structure of arrays, plane (s*Q + i) holds f_is for all N nodes,
 // node index x + nx*(y + ny*z).  The buffer holds post-collision values at the
@@ -12,8 +14,8 @@
 //
 // Tiling: a CTA owns a TX x TY tile of (x, y) columns and marches along z over
 // a chunk of planes.  The force at plane z needs the densities of planes z-1,
-// z, z+1 on the tile plus a one-node ring; they live in a three-plane ring of
-// shared memory.  Each iteration pulls the populations of plane z+1 (kept in
+// z, z+1 on the tile plus a one-node ring; they live in a ring of shared
+// memory.  Each iteration pulls the populations of plane z+1 (kept in
 // registers for the next iteration), writes their densities to the ring,
 // computes the densities of the ring's halo nodes (extra pulls served mostly
 // by L2, since neighbouring tiles read the same lines at about the same time),
@@ -21,12 +23,13 @@
 // TX*TY nodes of a plane, in x and y only: marching removes the z halo.
 #pragma once
 
-#include "sc_common.cuh"
+#include "sc_node.cuh"
 
 namespace lbmsc {
 
 enum KernelMode { kModeStep = 0, kModeMoments = 1 };
 
+// Pulled populations of node (x, y, z): f_is = f*_is(x - c_i).
 template <class L, class S>
 __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y, int z,
                                           typename Codec<S>::C (&f)[2][L::Q]) {
@@ -42,7 +45,7 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         const int sx = xs[L::c(i, 0) + 1], sy = ys[L::c(i, 1) + 1], sz = zs[L::c(i, 2) + 1];
-        const long long node = (long long)sx + (long long)nx * ((long long)sy + (long long)ny * sz);
+        const size_t node = (size_t)sx + (size_t)nx * ((size_t)sy + (size_t)ny * sz);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
@@ -51,54 +54,24 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
     }
 }
 
-template <int Q, class C>
-__device__ __forceinline__ C sum_q(const C (&f)[Q]) {
-    C r = f[0];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) r += f[i];
-    return r;
-}
-
-// BGK relaxation of one species towards f^eq(rho, u) (second-order truncated
-// Maxwellian with cs2 = 1/3): f += omega (f^eq - f).
-template <class L, class C>
-__device__ __forceinline__ void relax(C (&f)[L::Q], C rho, const C (&u)[3], C omega) {
-    C uu = u[0] * u[0] + u[1] * u[1];
-    if (L::D == 3) uu += u[2] * u[2];
-    const C base = (C)1 - (C)1.5 * uu;
+template <class L, class S>
+__device__ __forceinline__ void store_node(const LatticeArgs<S>& a, size_t node,
+                                           const typename Codec<S>::C (&f)[2][L::Q]) {
+    using C = typename Codec<S>::C;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        C cu = (C)0;
 #pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            if (L::c(i, d) == 1) cu += u[d];
-            if (L::c(i, d) == -1) cu -= u[d];
+        for (int s = 0; s < 2; ++s) {
+            const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+            Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.N + node, f[s][i], off);
         }
-        const C feq = (C)L::w(i) * rho * (base + cu * ((C)3 + (C)4.5 * cu));
-        f[i] += omega * (feq - f[i]);
     }
 }
 
-template <class L, class S, int TX, int TY, int MODE, int MINB>
-__global__ void __launch_bounds__(TX* TY, MINB)
-    sc_fused_kernel(const LatticeArgs<S> a, const FieldArgs<typename Codec<S>::C> fo) {
-    using C = typename Codec<S>::C;
-    constexpr int Q = L::Q;
+// Halo ring cell of thread tid (frame coordinates; frame (1, 1) = tile (0, 0)):
+// the top row, the bottom row, the left column, the right column.
+template <int TX, int TY> __device__ __forceinline__ void halo_cell(int tid, int& hfx, int& hfy) {
     constexpr int FX = TX + 2, FY = TY + 2;
-    constexpr int NPL = L::D == 3 ? 3 : 1;
-    constexpr int H = 2 * FX + 2 * TY;
-    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
-    __shared__ C srho[NPL][2][FY][FX];
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
-    const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
-
-    // Halo ring cell handled by this thread (frame coordinates; frame (1,1) = tile (0,0)).
-    const bool halo = tid < H;
-    int hfx = 0, hfy = 0;
     if (tid < FX) {
         hfx = tid;
         hfy = 0;
@@ -112,10 +85,35 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         hfx = FX - 1;
         hfy = tid - 2 * FX - TY + 1;
     }
+}
+
+__device__ __forceinline__ double diag_fold(int k, double a, double b) {
+    return (k == kMaxSpeed) ? fmax(a, b) : (k == kMinRhoA || k == kMinRhoB) ? fmin(a, b) : a + b;
+}
+
+template <class L, class S, int TX, int TY, int MODE, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    sc_fused_kernel(const LatticeArgs<S> a, const FieldArgs<typename Codec<S>::C> fo) {
+    using C = typename Codec<S>::C;
+    using A = Ar<C>;
+    constexpr int Q = L::Q;
+    constexpr int FX = TX + 2, FY = TY + 2;
+    constexpr int NPL = L::D == 3 ? 3 : 1;
+    constexpr int H = 2 * FX + 2 * TY;
+    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
+    __shared__ C srho[NPL][2][FY][FX];
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
+    const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+    const bool halo = tid < H;
+    int hfx, hfy;
+    halo_cell<TX, TY>(tid, hfx, hfy);
     const int hgx = (x0 - 1 + hfx + nx) % nx;
     const int hgy = (y0 - 1 + hfy + ny) % ny;
 
-    // Diagnostics accumulators (moments mode).
     double acc[kNumDiag];
     if (MODE == kModeMoments) {
 #pragma unroll
@@ -124,80 +122,46 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         acc[kMinRhoB] = 1e300;
     }
 
-    auto density_plane = [&](int slot, int z, C (&f)[2][Q], bool keep_own) {
-        // own column: pull (kept in f), densities to the ring
+    auto density_plane = [&](int slot, int z, C (&f)[2][Q]) {
         pull_node<L, S>(a, gx, gy, z, f);
-        srho[slot][0][ty + 1][tx + 1] = sum_q<Q>(f[0]);
-        srho[slot][1][ty + 1][tx + 1] = sum_q<Q>(f[1]);
-        (void)keep_own;
+        srho[slot][0][ty + 1][tx + 1] = node_density<L, C>(f[0]);
+        srho[slot][1][ty + 1][tx + 1] = node_density<L, C>(f[1]);
         if (halo) {
             C h[2][Q];
             pull_node<L, S>(a, hgx, hgy, z, h);
-            srho[slot][0][hfy][hfx] = sum_q<Q>(h[0]);
-            srho[slot][1][hfy][hfx] = sum_q<Q>(h[1]);
+            srho[slot][0][hfy][hfx] = node_density<L, C>(h[0]);
+            srho[slot][1][hfy][hfx] = node_density<L, C>(h[1]);
         }
     };
 
     auto process = [&](C (&f)[2][Q], int sm, int sc, int sp, int z) {
         const C rA = srho[sc][0][ty + 1][tx + 1];
         const C rB = srho[sc][1][ty + 1][tx + 1];
-        C jA[3] = {0, 0, 0}, jB[3] = {0, 0, 0};
-        C gA[3] = {0, 0, 0}, gB[3] = {0, 0, 0};  // sum_i w_i rho_s'(x + c_i) c_i
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-#pragma unroll
-            for (int d = 0; d < L::D; ++d) {
-                if (L::c(i, d) == 1) { jA[d] += f[0][i]; jB[d] += f[1][i]; }
-                if (L::c(i, d) == -1) { jA[d] -= f[0][i]; jB[d] -= f[1][i]; }
-            }
+        auto nbr = [&](int s, int i) -> C {
             const int slot = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
-            const C wA = (C)L::w(i) * srho[slot][0][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
-            const C wB = (C)L::w(i) * srho[slot][1][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
-#pragma unroll
-            for (int d = 0; d < L::D; ++d) {
-                if (L::c(i, d) == 1) { gA[d] += wB; gB[d] += wA; }
-                if (L::c(i, d) == -1) { gA[d] -= wB; gB[d] -= wA; }
-            }
-        }
-        // F_s / rho_s = -G sum_i w_i rho_s'(x + c_i) c_i   (Eq. FORCE)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            gA[d] *= -a.G;
-            gB[d] *= -a.G;
-        }
+            return srho[slot][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+        };
+        C gA[3], gB[3];
+        node_force<L, C>(nbr, a.G, gA, gB);
+        const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
-            // common velocity u' = sum_s j_s / tau_s / sum_s rho_s / tau_s, shifted by tau_s F_s / rho_s
-            const C inv_den = (C)1 / (rA * a.omega_A + rB * a.omega_B);
-            C uA[3], uB[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const C up = (jA[d] * a.omega_A + jB[d] * a.omega_B) * inv_den;
-                uA[d] = up + a.tau_A * gA[d];
-                uB[d] = up + a.tau_B * gB[d];
-            }
-            relax<L, C>(f[0], rA, uA, a.omega_A);
-            relax<L, C>(f[1], rB, uB, a.omega_B);
-            if (owner) {
-                const long long node = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * z);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-                        Codec<S>::store(a.fout + (size_t)(s * Q + i) * (size_t)a.N + node, f[s][i], off);
-                    }
-                }
-            }
+            node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            if (owner) store_node<L, S>(a, node, f);
         } else {
             // physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2 shift, Sec. 2.3)
-            const C rho = rA + rB;
+            C jA[3], jB[3];
+            node_momentum<L, C>(f[0], jA);
+            node_momentum<L, C>(f[1], jB);
+            const C rho = A::add(rA, rB);
+            const C inv_rho = A::rcp(rho);
             C u[3];
 #pragma unroll
-            for (int d = 0; d < 3; ++d)
-                u[d] = (jA[d] + jB[d] + (C)0.5 * (rA * gA[d] + rB * gB[d])) / rho;
-            const C p = (rho + a.G * rA * rB) * (C)(1.0 / 3.0);
+            for (int d = 0; d < 3; ++d) {
+                const C half_force = A::mul((C)0.5, A::fma(rA, gA[d], A::mul(rB, gB[d])));
+                u[d] = A::mul(A::add(A::add(jA[d], jB[d]), half_force), inv_rho);
+            }
+            const C p = A::mul(A::fma(A::mul(a.G, rA), rB, rho), (C)(1.0 / 3.0));
             if (owner) {
-                const long long node = (long long)gx + (long long)nx * ((long long)gy + (long long)ny * z);
                 if (fo.rhoA) fo.rhoA[node] = rA;
                 if (fo.rhoB) fo.rhoB[node] = rB;
                 if (fo.u)
@@ -206,19 +170,16 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 if (fo.p) fo.p[node] = p;
                 if (fo.partials) {
                     const double dA = (double)rA, dB = (double)rB, drho = dA + dB;
-                    double m[3], uu = 0.0;
+                    double uu = 0.0;
 #pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        m[d] = (double)u[d] * drho;
-                        uu += (double)u[d] * (double)u[d];
-                    }
+                    for (int d = 0; d < 3; ++d) uu += (double)u[d] * (double)u[d];
                     const bool finite = isfinite(dA) && isfinite(dB) && isfinite(uu) && isfinite((double)p);
                     if (finite) {
                         acc[kMassA] += dA;
                         acc[kMassB] += dB;
-                        acc[kMomX] += m[0];
-                        acc[kMomY] += m[1];
-                        acc[kMomZ] += m[2];
+                        acc[kMomX] += (double)u[0] * drho;
+                        acc[kMomY] += (double)u[1] * drho;
+                        acc[kMomZ] += (double)u[2] * drho;
                         acc[kKE] += 0.5 * drho * uu;
                         acc[kMaxSpeed] = fmax(acc[kMaxSpeed], sqrt(uu));
                         acc[kMinRhoA] = fmin(acc[kMinRhoA], dA);
@@ -251,7 +212,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 
     C cur[2][Q];
     if (L::D == 2) {
-        density_plane(0, 0, cur, true);
+        density_plane(0, 0, cur);
         __syncthreads();
         process(cur, 0, 0, 0, 0);
     } else {
@@ -259,13 +220,13 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         const int z1 = min(z0 + a.zchunk, nz);
         {
             C tmp[2][Q];
-            density_plane(0, z0 == 0 ? nz - 1 : z0 - 1, tmp, false);
+            density_plane(0, z0 == 0 ? nz - 1 : z0 - 1, tmp);
         }
-        density_plane(1, z0, cur, true);
+        density_plane(1, z0, cur);
         int sm = 0, sc = 1, sp = 2;
         for (int z = z0; z < z1; ++z) {
             C nxt[2][Q];
-            density_plane(sp, z + 1 == nz ? 0 : z + 1, nxt, true);
+            density_plane(sp, z + 1 == nz ? 0 : z + 1, nxt);
             __syncthreads();
             process(cur, sm, sc, sp, z);
 #pragma unroll
@@ -289,22 +250,90 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         for (int k = 0; k < kNumDiag; ++k) {
             double v = acc[k];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const double w = __shfl_xor_sync(0xffffffffu, v, o);
-                v = (k == kMaxSpeed) ? fmax(v, w) : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, w) : v + w;
-            }
+            for (int o = 16; o > 0; o >>= 1) v = diag_fold(k, v, __shfl_xor_sync(0xffffffffu, v, o));
             if (lane == 0) red[warp][k] = v;
         }
         __syncthreads();
         if (tid < kNumDiag) {
             const int k = tid;
             double v = red[0][k];
-            for (int w = 1; w < NW; ++w)
-                v = (k == kMaxSpeed) ? fmax(v, red[w][k])
-                    : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, red[w][k]) : v + red[w][k];
+            for (int w = 1; w < NW; ++w) v = diag_fold(k, v, red[w][k]);
             const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
             fo.partials[b * kNumDiag + k] = v;
         }
+    }
+}
+
+// Low-register variant of the step: the populations of plane z are not kept
+// in registers while plane z+1 is reduced to densities; they are pulled a
+// second time for the collision, one iteration after their first load, when
+// they are normally still in L1.  Holding only one plane of pulls lets more
+// CTAs share an SM (more loads in flight), and the four-slot density ring
+// needs one __syncthreads per plane.  Arithmetic and order as sc_fused_kernel.
+template <class L, class S, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const LatticeArgs<S> a) {
+    using C = typename Codec<S>::C;
+    constexpr int Q = L::Q;
+    constexpr int FX = TX + 2, FY = TY + 2;
+    constexpr int NPL = L::D == 3 ? 4 : 1;
+    constexpr int H = 2 * FX + 2 * TY;
+    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
+    __shared__ C ring[NPL][2][FY][FX];
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
+    const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+    const bool halo = tid < H;
+    int hfx, hfy;
+    halo_cell<TX, TY>(tid, hfx, hfy);
+    const int hgx = (x0 - 1 + hfx + nx) % nx;
+    const int hgy = (y0 - 1 + hfy + ny) % ny;
+
+    auto density_plane = [&](int slot, int z) {
+        C f[2][Q];
+        pull_node<L, S>(a, gx, gy, z, f);
+        ring[slot][0][ty + 1][tx + 1] = node_density<L, C>(f[0]);
+        ring[slot][1][ty + 1][tx + 1] = node_density<L, C>(f[1]);
+        if (halo) {
+            pull_node<L, S>(a, hgx, hgy, z, f);
+            ring[slot][0][hfy][hfx] = node_density<L, C>(f[0]);
+            ring[slot][1][hfy][hfx] = node_density<L, C>(f[1]);
+        }
+    };
+    auto collide = [&](int sm, int sc, int sp, int z) {
+        C f[2][Q];
+        pull_node<L, S>(a, gx, gy, z, f);
+        const C rA = ring[sc][0][ty + 1][tx + 1];
+        const C rB = ring[sc][1][ty + 1][tx + 1];
+        auto nbr = [&](int s, int i) -> C {
+            const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
+            return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+        };
+        C gA[3], gB[3];
+        node_force<L, C>(nbr, a.G, gA, gB);
+        node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        if (owner) store_node<L, S>(a, (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z), f);
+    };
+
+    if (L::D == 2) {
+        density_plane(0, 0);
+        __syncthreads();
+        collide(0, 0, 0, 0);
+        return;
+    }
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, nz);
+    // ring slot of plane z is (z - z0 + 1) & 3
+    density_plane(0, z0 == 0 ? nz - 1 : z0 - 1);
+    density_plane(1, z0);
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        const int k = z - z0 + 1;
+        density_plane((k + 1) & 3, z + 1 == nz ? 0 : z + 1);
+        __syncthreads();
+        collide((k - 1) & 3, k & 3, (k + 1) & 3, z);
     }
 }
 
@@ -321,29 +350,20 @@ __global__ void __launch_bounds__(NT) sc_diag_finish_kernel(const double* __rest
     acc[kMinRhoB] = 1e300;
     for (long long b = tid; b < nparts; b += NT) {
 #pragma unroll
-        for (int k = 0; k < kNumDiag; ++k) {
-            const double v = partials[b * kNumDiag + k];
-            acc[k] = (k == kMaxSpeed) ? fmax(acc[k], v)
-                     : (k == kMinRhoA || k == kMinRhoB) ? fmin(acc[k], v) : acc[k] + v;
-        }
+        for (int k = 0; k < kNumDiag; ++k) acc[k] = diag_fold(k, acc[k], partials[b * kNumDiag + k]);
     }
 #pragma unroll
     for (int k = 0; k < kNumDiag; ++k) {
         double v = acc[k];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_xor_sync(0xffffffffu, v, o);
-            v = (k == kMaxSpeed) ? fmax(v, w) : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, w) : v + w;
-        }
+        for (int o = 16; o > 0; o >>= 1) v = diag_fold(k, v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
     if (tid < kNumDiag) {
         const int k = tid;
         double v = red[0][k];
-        for (int w = 1; w < NT / 32; ++w)
-            v = (k == kMaxSpeed) ? fmax(v, red[w][k])
-                : (k == kMinRhoA || k == kMinRhoB) ? fmin(v, red[w][k]) : v + red[w][k];
+        for (int w = 1; w < NT / 32; ++w) v = diag_fold(k, v, red[w][k]);
         out[k] = v;
     }
 }
@@ -367,7 +387,7 @@ __global__ void __launch_bounds__(256)
             const int sx = (x + L::c(i, 0) + nx) % nx;
             const int sy = (y + L::c(i, 1) + ny) % ny;
             const int sz = L::D == 3 ? (z + L::c(i, 2) + nz) % nz : 0;
-            const long long m = (long long)sx + (long long)nx * ((long long)sy + (long long)ny * sz);
+            const size_t m = (size_t)sx + (size_t)nx * ((size_t)sy + (size_t)ny * sz);
             C uv[3] = {0, 0, 0};
             if (u)
                 for (int d = 0; d < L::D; ++d) uv[d] = u[(size_t)d * (size_t)a.N + m];

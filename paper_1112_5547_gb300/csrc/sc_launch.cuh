@@ -14,13 +14,44 @@ struct Plan {
     int precision;  // lbm_precision
     int nx, ny, nz;
     long long N;
-    int zchunk;     // planes per CTA along z (D3Q19)
+    int zchunk;     // planes per CTA along z for the moments kernel (D3Q19)
+    int step_tile;  // index into kTiles for the step kernel
+    int step_zchunk;
+    int sm_count;   // multiprocessors of the device (persistent grids)
     double tau_A, tau_B, G, ref_A, ref_B;
 };
 
-// Tile of one CTA (threads = TX * TY, one (x, y) column each).
+// Tile of one CTA (threads = TX * TY, one (x, y) column each) for the moments
+// kernel, and the tiles the step kernel can be launched with (autotuned).
 constexpr int kTX = 32;
 constexpr int kTY = 8;
+// kind 0: register-pipelined kernel (every lattice and precision);
+// kind 1: persistent cp.async kernel with `stages` shared-memory stages
+//         (D3Q19 with FP32 storage only);
+// kind 2: software-pipelined kernel, loads two planes ahead (D3Q19 only);
+// kind 3: low-register kernel that re-pulls a plane for its collision, with
+//         `stages` = CTAs per SM requested from the register allocator;
+// kind 4: register-pipelined kernel with three planes of pulls in registers
+//         (D3Q19, 32-bit and 16-bit storage), `stages` = CTAs per SM.
+struct TileShape { int tx, ty, kind, stages; };
+constexpr int kNumTiles = 18;
+constexpr TileShape kTiles[kNumTiles] = {{32, 8, 0, 0}, {32, 16, 0, 0}, {64, 8, 0, 0}, {32, 4, 0, 0},
+                                         {64, 4, 0, 0}, {32, 8, 1, 3},  {32, 8, 1, 4},  {64, 4, 1, 3},
+                                         {32, 8, 2, 0}, {64, 4, 2, 0},  {32, 4, 2, 0},  {32, 4, 3, 6},
+                                         {32, 8, 3, 3}, {64, 4, 3, 3},  {32, 4, 3, 4},  {32, 4, 4, 3},
+                                         {32, 8, 4, 1}, {16, 8, 4, 3}};
+
+inline bool tile_supported(int tile, int lattice, int precision) {
+    if (tile < 0 || tile >= kNumTiles) return false;
+    switch (kTiles[tile].kind) {
+        case 0: return true;
+        case 1: return lattice == 1 && precision == 1;
+        case 2: return lattice == 1;
+        case 3: return true;
+        case 4: return lattice == 1 && precision != 0;
+    }
+    return false;
+}
 
 struct MomentsOut {
     void* rhoA;
@@ -34,6 +65,12 @@ struct MomentsOut {
 inline dim3 fused_grid(const Plan& p) {
     return dim3((unsigned)((p.nx + kTX - 1) / kTX), (unsigned)((p.ny + kTY - 1) / kTY),
                 (unsigned)(p.lattice == 1 ? (p.nz + p.zchunk - 1) / p.zchunk : 1));
+}
+
+inline dim3 step_grid(const Plan& p) {
+    const TileShape t = kTiles[p.step_tile];
+    return dim3((unsigned)((p.nx + t.tx - 1) / t.tx), (unsigned)((p.ny + t.ty - 1) / t.ty),
+                (unsigned)(p.lattice == 1 ? (p.nz + p.step_zchunk - 1) / p.step_zchunk : 1));
 }
 
 inline long long fused_blocks(const Plan& p) {

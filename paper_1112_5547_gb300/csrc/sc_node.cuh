@@ -1,0 +1,135 @@
+// Per-node arithmetic of the two-component Shan-Chen step (paper Sec. 2.1),
+// shared by every kernel so that all launch shapes give bit-identical results.
+//
+// For one node with pulled populations f_is (post-streaming, pre-collision):
+//   rho_s = sum_i f_is,  j_s = sum_i f_is c_i                      (Sec. 2.1 moments)
+//   g_s = F_s / rho_s = -G sum_i w_i rho_s'(x + c_i) c_i           (Eq. FORCE)
+//   u' = (j_A / tau_A + j_B / tau_B) / (rho_A / tau_A + rho_B / tau_B)
+//   f_is += (1 / tau_s) (f^eq_i(rho_s, u' + tau_s g_s) - f_is)      (Eq. eq:be)
+// with f^eq_i(rho, u) = w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u].
+//
+// All operations go through Ar<C> (explicitly rounded intrinsics) in a fixed
+// order.  The force is taken per unit density, so a vanishing rho_s is never
+// divided by.  Momentum and force are summed over opposite-direction pairs
+// (the GPU velocity order keeps c_{i+1} = -c_i for odd i): the pair difference
+// f_i - f_{i+1}, resp. rho(x + c_i) - rho(x - c_i), is formed first, so both
+// vanish exactly in a uniform region and their rounding is antisymmetric.
+// Accumulating single terms instead (rho(x + c_i) with an FMA, then
+// rho(x - c_i)) leaves a force of about one ulp in uniform regions; in FP32
+// that random-walks the total momentum and lets a drop drift by about 1e-5
+// lattice units per 1000 steps.  The rest population of the equilibrium is closed as
+// f^eq_0 = rho - sum_{i>0} f^eq_i: equal to w_0 rho (...) in exact arithmetic,
+// it keeps FP32 mass conservation at rounding noise (the rounded weights
+// float(1/9), float(4/9), float(1/36) all err upwards and would otherwise
+// create about 7e-9 of mass per step at tau = 1).
+#pragma once
+
+#include "sc_common.cuh"
+
+namespace lbmsc {
+
+template <class L, class C> __device__ __forceinline__ C node_density(const C (&f)[L::Q]) {
+    C r = f[0];
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) r = Ar<C>::add(r, f[i]);
+    return r;
+}
+
+template <class L> __host__ __device__ constexpr bool opposite_pairs() {
+    for (int i = 1; i + 1 < L::Q; i += 2)
+        for (int d = 0; d < 3; ++d)
+            if (L::c(i + 1, d) != -L::c(i, d)) return false;
+    return L::Q % 2 == 1;
+}
+
+template <class L, class C> __device__ __forceinline__ void node_momentum(const C (&f)[L::Q], C (&j)[3]) {
+    static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
+    j[0] = j[1] = j[2] = (C)0;
+#pragma unroll
+    for (int i = 1; i < L::Q; i += 2) {
+        const C dlt = Ar<C>::sub(f[i], f[i + 1]);
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) j[d] = Ar<C>::add(j[d], dlt);
+            if (L::c(i, d) == -1) j[d] = Ar<C>::sub(j[d], dlt);
+        }
+    }
+}
+
+// g_s = -G sum_i w_i rho_s'(x + c_i) c_i for both species; nbr(s, i) returns
+// rho_s(x + c_i).
+template <class L, class C, class Nbr>
+__device__ __forceinline__ void node_force(const Nbr& nbr, C G, C (&gA)[3], C (&gB)[3]) {
+    using A = Ar<C>;
+    static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
+    gA[0] = gA[1] = gA[2] = gB[0] = gB[1] = gB[2] = (C)0;
+#pragma unroll
+    for (int i = 1; i < L::Q; i += 2) {
+        const C w = (C)L::w(i);
+        const C dA = A::sub(nbr(0, i), nbr(0, i + 1));  // rho_A(x + c_i) - rho_A(x - c_i)
+        const C dB = A::sub(nbr(1, i), nbr(1, i + 1));
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) {
+                gA[d] = A::fma(w, dB, gA[d]);
+                gB[d] = A::fma(w, dA, gB[d]);
+            }
+            if (L::c(i, d) == -1) {
+                gA[d] = A::fma(-w, dB, gA[d]);
+                gB[d] = A::fma(-w, dA, gB[d]);
+            }
+        }
+    }
+    const C mG = -G;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        gA[d] = A::mul(gA[d], mG);
+        gB[d] = A::mul(gB[d], mG);
+    }
+}
+
+// BGK relaxation of one species towards f^eq(rho, u).
+template <class L, class C> __device__ __forceinline__ void node_relax(C (&f)[L::Q], C rho, const C (&u)[3], C omega) {
+    using A = Ar<C>;
+    C uu = L::D == 3 ? A::fma(u[0], u[0], A::fma(u[1], u[1], A::mul(u[2], u[2]))) : A::fma(u[0], u[0], A::mul(u[1], u[1]));
+    const C base = A::fma((C)-1.5, uu, (C)1);
+    C feq[L::Q];
+    C moved = (C)0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        C cu = (C)0;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) cu = A::add(cu, u[d]);
+            if (L::c(i, d) == -1) cu = A::sub(cu, u[d]);
+        }
+        const C wr = A::mul((C)L::w(i), rho);
+        feq[i] = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
+        moved = A::add(moved, feq[i]);
+    }
+    feq[0] = A::sub(rho, moved);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = A::fma(omega, A::sub(feq[i], f[i]), f[i]);
+}
+
+// Collision of both species of one node: common velocity shifted by tau_s g_s.
+template <class L, class C>
+__device__ __forceinline__ void node_collide(C (&f)[2][L::Q], C rA, C rB, const C (&gA)[3], const C (&gB)[3],
+                                             C omega_A, C omega_B, C tau_A, C tau_B) {
+    using A = Ar<C>;
+    C jA[3], jB[3];
+    node_momentum<L, C>(f[0], jA);
+    node_momentum<L, C>(f[1], jB);
+    const C inv_den = A::rcp(A::fma(rA, omega_A, A::mul(rB, omega_B)));
+    C uA[3], uB[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const C up = A::mul(A::fma(jA[d], omega_A, A::mul(jB[d], omega_B)), inv_den);
+        uA[d] = A::fma(tau_A, gA[d], up);
+        uB[d] = A::fma(tau_B, gB[d], up);
+    }
+    node_relax<L, C>(f[0], rA, uA, omega_A);
+    node_relax<L, C>(f[1], rB, uB, omega_B);
+}
+
+}  // namespace lbmsc

@@ -40,8 +40,32 @@ PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_F32_STORE_BF16, "f16":
 EXPORTS = (
     "lbm_sc_workspace_bytes", "lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step",
     "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
-    "lbm_sc_destroy", "lbm_sc_status_string",
+    "lbm_sc_destroy", "lbm_sc_status_string", "lbm_sc_set_tuning", "lbm_sc_get_tuning",
 )
+
+# CTA tiles (x columns by y columns) the step kernel can be launched with, and
+# the shared-memory stages of the persistent cp.async kernel (0: register kernel).
+# kind 0: register-pipelined kernel; 1: persistent cp.async kernel; 2: software-pipelined kernel;
+# 3: low-register re-pull kernel (stages = CTAs per SM asked of the register allocator).
+# 4: register-pipelined kernel, three planes of pulls in registers (D3Q19, 32- and 16-bit storage).
+TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
+         (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8))
+TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4)
+TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3)
+
+
+def tile_supported(tile: int, lattice: int, precision: int) -> bool:
+    """Mirror of the library's rule: kind 1 needs D3Q19 with FP32 storage, kind 2 D3Q19."""
+    if not 0 <= tile < len(TILES):
+        return False
+    kind = TILE_KIND[tile]
+    if kind in (0, 3):
+        return True
+    if kind == 1:
+        return lattice == LBM_D3Q19 and precision == LBM_F32
+    if kind == 4:
+        return lattice == LBM_D3Q19 and precision != LBM_F64
+    return lattice == LBM_D3Q19
 
 
 class lbm_sc_params(ctypes.Structure):
@@ -67,6 +91,10 @@ class lbm_sc_diag(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "momentum"}
         d["momentum"] = tuple(self.momentum)
         return d
+
+
+class lbm_sc_tuning(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("zchunk", ctypes.c_int32)]
 
 
 class LbmError(RuntimeError):
@@ -102,6 +130,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_sc_run_host.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
     lib.lbm_sc_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(vp)]
+    lib.lbm_sc_set_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
+    lib.lbm_sc_get_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
     lib.lbm_sc_destroy.argtypes = [vp]
     lib.lbm_sc_destroy.restype = None
     lib.lbm_sc_status_string.argtypes = [ctypes.c_int]
@@ -109,7 +139,8 @@ def load(path: str = LIB_PATH):
     for name in EXPORTS:
         getattr(lib, name)
     for name in ("lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step", "lbm_sc_moments",
-                 "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout"):
+                 "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout", "lbm_sc_set_tuning",
+                 "lbm_sc_get_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -192,6 +223,17 @@ def lbm_sc_layout(h: int):
     return eb.value, q.value, ptr.value
 
 
+def lbm_sc_set_tuning(h: int, tile: int, zchunk: int = 0) -> None:
+    t = lbm_sc_tuning(int(tile), int(zchunk))
+    _check(load().lbm_sc_set_tuning(ctypes.c_void_p(h), ctypes.byref(t)), "lbm_sc_set_tuning")
+
+
+def lbm_sc_get_tuning(h: int):
+    t = lbm_sc_tuning()
+    _check(load().lbm_sc_get_tuning(ctypes.c_void_p(h), ctypes.byref(t)), "lbm_sc_get_tuning")
+    return t.tile, t.zchunk
+
+
 def lbm_sc_destroy(h: int) -> None:
     load().lbm_sc_destroy(ctypes.c_void_p(h))
 
@@ -271,6 +313,13 @@ class Lattice:
     def step(self, nsteps: int = 1):
         lbm_sc_step(self.handle, nsteps)
         return self
+
+    def set_tuning(self, tile: int, zchunk: int = 0):
+        lbm_sc_set_tuning(self.handle, tile, zchunk)
+        return self
+
+    def tuning(self):
+        return lbm_sc_get_tuning(self.handle)
 
     def moments(self):
         """(rho_A, rho_B, u (shape + (D,)), p) as device tensors in the compute dtype."""

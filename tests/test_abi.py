@@ -86,6 +86,40 @@ def test_create_checks_workspace_without_touching_the_gpu(lib):
     lib.lbm_sc_destroy(h)
 
 
+def test_tuning_validation(lib):
+    p = lib.make_params(lib.LBM_D3Q19, (40, 8, 8), 1.0, 1.0, 2.0, "f32")
+    h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+    try:
+        for t in range(len(lib.TILES)):
+            lib.lbm_sc_set_tuning(h, t, 0)
+            assert lib.lbm_sc_get_tuning(h)[0] == t
+        lib.lbm_sc_set_tuning(h, 1, 500)
+        assert lib.lbm_sc_get_tuning(h) == (1, 40)  # clamped to nz
+        for bad in ((-1, 0), (len(lib.TILES), 0), (0, -3)):
+            with pytest.raises(lib.LbmError):
+                lib.lbm_sc_set_tuning(h, *bad)
+    finally:
+        lib.lbm_sc_destroy(h)
+    # the cp.async tiles exist only for D3Q19 with FP32 storage, the pipelined ones for D3Q19
+    for lat, shape, prec in ((lib.LBM_D2Q9, (8, 8), "f32"), (lib.LBM_D3Q19, (8, 8, 8), "f64"),
+                             (lib.LBM_D3Q19, (8, 8, 8), "bf16")):
+        p = lib.make_params(lat, shape, 1.0, 1.0, 2.0, prec)
+        h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+        try:
+            for t in range(len(lib.TILES)):
+                ok = lib.tile_supported(t, lat, p.precision)
+                kind = lib.TILE_KIND[t]
+                assert ok == (kind in (0, 3) or (kind == 2 and lat == lib.LBM_D3Q19)
+                              or (kind == 4 and lat == lib.LBM_D3Q19 and prec != "f64"))
+                if ok:
+                    lib.lbm_sc_set_tuning(h, t, 0)
+                else:
+                    with pytest.raises(lib.LbmError):
+                        lib.lbm_sc_set_tuning(h, t, 0)
+        finally:
+            lib.lbm_sc_destroy(h)
+
+
 def test_status_strings(lib):
     for s in range(6):
         assert lib.lbm_sc_status_string(s).startswith("LBM_")

@@ -1,8 +1,10 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerances (relative error per field = max|gpu - oracle| / max|oracle|; the
-velocity is compared in the max norm relative to max|u_oracle|, since a
-pointwise relative error is meaningless near u = 0):
+velocity is compared in the max norm relative to max(max|u_oracle|, 1e-3):
+a pointwise relative error is meaningless near u = 0, and the velocity is a
+difference of O(rho) population sums, so its round-off is absolute, about
+1e-16 lattice units in FP64, whatever the flow speed):
   * FP64 GPU build: 1e-12 per field (after 1000 steps on the 64^2 drop);
   * FP32: 1e-5 on the densities, mass drift < 1e-6 (FP64 diagnostics).
 Inputs are the seeded drop / slab recipes of paper_1112_5547_gb300.inputs.
@@ -27,10 +29,17 @@ def sc():
     return lbm_sc
 
 
-def _rel(a, b):
+def _rel(a, b, floor=1e-300):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() / max(np.abs(b).max(), floor)
+
+
+U_FLOOR = 1e-3
+
+
+def _rel_field(name, a, b):
+    return _rel(a, b, U_FLOOR if name == "u" else 1e-300)
 
 
 def _gpu_fields(lat):
@@ -55,7 +64,7 @@ def test_cfg0_f64_1000_steps(sc, oracle_mod):
     f = inputs.drop((64, 64), 16, centre=(32, 32), seed=0)
     g, o, _ = _run_pair(sc, oracle_mod, 0, (64, 64), 1.0, 1.0, G0, 1000, "f64", f)
     for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
-        assert _rel(a, b) < 1e-12, name
+        assert _rel_field(name, a, b) < 1e-12, name
 
 
 def test_cfg0_f32_1000_steps(sc, oracle_mod):
@@ -76,8 +85,8 @@ def test_d3q19_ragged_tiles(sc, oracle_mod, precision, tol):
     f = inputs.drop(shape, 6, centre=(14.0, 9.5, 8.0), seed=5)
     g, o, _ = _run_pair(sc, oracle_mod, 1, shape, 0.8, 1.2, 2.0, 200, precision, f)
     for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
-        t = tol if name != "u" else (1e-11 if precision == "f64" else 1e-3)
-        assert _rel(a, b) < t, name
+        t = tol if name != "u" else (1e-12 if precision == "f64" else 1e-3)
+        assert _rel_field(name, a, b) < t, name
 
 
 def test_d2q9_ragged_f64(sc, oracle_mod):
@@ -85,7 +94,7 @@ def test_d2q9_ragged_f64(sc, oracle_mod):
     f = inputs.drop(shape, 15, centre=(40.0, 30.0), seed=6)
     g, o, _ = _run_pair(sc, oracle_mod, 0, shape, 1.3, 0.7, 2.2, 300, "f64", f)
     for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
-        assert _rel(a, b) < 1e-12, name
+        assert _rel_field(name, a, b) < 1e-12, name
 
 
 @pytest.mark.parametrize("lattice,shape", [(0, (4, 4)), (0, (1, 5)), (1, (7, 3, 5)), (1, (1, 4, 6)), (1, (3, 1, 1))])
@@ -96,7 +105,7 @@ def test_tiny_and_degenerate_lattices(sc, oracle_mod, lattice, shape):
     rB = 0.5 + 0.3 * rng.random(shape)
     g, o, _ = _run_pair(sc, oracle_mod, lattice, shape, 0.9, 1.1, 1.5, 30, "f64", (rA, rB))
     for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
-        assert _rel(a, b) < 1e-12, name
+        assert _rel_field(name, a, b) < 1e-12, name
 
 
 def test_moving_start_and_unequal_tau(sc, oracle_mod):
@@ -106,18 +115,18 @@ def test_moving_start_and_unequal_tau(sc, oracle_mod):
     u = rng.uniform(-0.03, 0.03, size=shape + (3,))
     g, o, _ = _run_pair(sc, oracle_mod, 1, shape, 0.6, 1.5, 1.7, 100, "f64", f, u=u)
     for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
-        assert _rel(a, b) < 1e-12, name
+        assert _rel_field(name, a, b) < 1e-12, name
 
 
 def test_zero_coupling_and_zero_steps(sc, oracle_mod):
     shape = (9, 33)
     f = inputs.drop(shape, 3, seed=1)
     g, o, _ = _run_pair(sc, oracle_mod, 0, shape, 1.0, 1.0, 0.0, 50, "f64", f)
-    for a, b in zip(g, o):
-        assert _rel(a, b) < 1e-12
+    for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
+        assert _rel_field(name, a, b) < 1e-12, name
     g, o, _ = _run_pair(sc, oracle_mod, 0, shape, 1.0, 1.0, 1.0, 0, "f64", f)
-    for a, b in zip(g, o):
-        assert _rel(a, b) < 1e-13
+    for name, a, b in zip(("rhoA", "rhoB", "u", "p"), g, o):
+        assert _rel_field(name, a, b) < 1e-13, name
 
 
 def test_translation_equivariance_bitwise_gpu(sc):
@@ -200,3 +209,36 @@ def test_unstable_state_reported(sc):
     lat = sc.Lattice(0, shape, 1.0, 1.0, 1.0, "f32").init(rA, np.full(shape, 0.5))
     d = lat.diagnostics(check=False)
     assert d["status"] == sc.LBM_ERR_UNSTABLE and d["nonfinite"] >= 1
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16", "f64"])
+def test_every_launch_shape_is_bit_identical(sc, precision):
+    """The step kernel's tile, kernel kind and z-chunk change only speed: all shapes agree bitwise."""
+    shape = (40, 27, 70)
+    f = inputs.drop(shape, 8, seed=12)
+    prec = sc.PRECISIONS[precision]
+    ref = None
+    for tile in range(len(sc.TILES)):
+        if not sc.tile_supported(tile, sc.LBM_D3Q19, prec):
+            continue
+        for z in (0, 7, 40):
+            lat = sc.Lattice(1, shape, 0.9, 1.1, G0, precision, 0.5, 0.5).init(*f).set_tuning(tile, z).step(6)
+            got = _gpu_fields(lat)
+            if ref is None:
+                ref = got
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), (tile, z)
+
+
+def test_autotuner_restores_state(sc):
+    from paper_1112_5547_gb300 import autotune
+    shape = (32, 24, 40)
+    f = inputs.drop(shape, 7, seed=13)
+    a = sc.Lattice(1, shape, 1.0, 1.0, G0, "f32").init(*f).step(3)
+    before = _gpu_fields(a)
+    best, table = autotune.autotune(a, trial_steps=2, warmup_steps=2)
+    assert len(table) == len(autotune.candidates(a))
+    after = _gpu_fields(a)
+    for x, y in zip(before, after):
+        assert np.array_equal(x, y)
+    assert a.tuning() == (best[0], best[1])
