@@ -177,10 +177,15 @@ LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t 
                            const void* h_rhoA, const void* h_rhoB, const void* h_u, int nsteps,
                            void* h_rhoA_out, void* h_rhoB_out, void* h_u_out, void* h_p_out);
 
-/* Bytes and population storage layout (for tools): element size of one stored
- * population value, number of velocities Q, and the current population buffer
- * (2 x Q planes of N values, index (s*Q + i)*N + node, GPU velocity order). */
-LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, const void** d_populations);
+/* Population storage layout (for tools such as checkpointing): bytes of one
+ * stored value, number of velocities Q, and the geometry of the current
+ * population buffer.  It holds 2 x Q planes (index s*Q + i, GPU velocity order)
+ * of pitch_x * pitch_y * nz values each; node (x, y, z) sits at
+ * (x + ghost_x) + pitch_x * ((y + ghost_y) + pitch_y * z).  The columns
+ * x = -2, -1, nx, nx + 1 and rows y = -2, -1, ny, ny + 1 hold periodic images;
+ * other padding is unused.  Any output pointer may be NULL. */
+LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y,
+                                    int* ghost_x, int* ghost_y, const void** d_populations);
 
 /* Release the host handle.  The workspace stays the caller's. */
 LBM_SC_API void lbm_sc_destroy(lbm_sc_handle* h);

@@ -15,8 +15,7 @@ from . import lbm_sc
 
 def candidates(lattice: "lbm_sc.Lattice") -> List[Tuple[int, int]]:
     """(tile, zchunk) pairs worth timing for this lattice (zchunk 0 = automatic)."""
-    tiles = [t for t in range(len(lbm_sc.TILES))
-             if lbm_sc.tile_supported(t, lattice.lattice, lattice.params.precision)]
+    tiles = [t for t in range(len(lbm_sc.TILES)) if lattice.tile_fits(t)]
     if lattice.lattice == lbm_sc.LBM_D2Q9:
         return [(t, 0) for t in tiles]
     nz = lattice.shape[0]
@@ -60,8 +59,10 @@ def autotune(lattice: "lbm_sc.Lattice", trial_steps: int = 4, warmup_steps: int 
 
 
 def format_table(table: Sequence) -> str:
-    rows = ["tile      zchunk  ms/step"]
+    rows = ["id tile  kind stages cluster  zchunk  ms/step"]
     for (tile, _), zc, ms in sorted(table, key=lambda r: r[2]):
         tx, ty = lbm_sc.TILES[tile]
-        rows.append("%2dx%-2d k%d s%d  %6d  %.4f" % (tx, ty, lbm_sc.TILE_KIND[tile], lbm_sc.TILE_STAGES[tile], zc, ms))
+        cx, cy = lbm_sc.TILE_CLUSTER[tile]
+        rows.append("%2d %2dx%-2d k%d s%d c%dx%d  %6d  %.4f" % (tile, tx, ty, lbm_sc.TILE_KIND[tile],
+                                                            lbm_sc.TILE_STAGES[tile], cx, cy, zc, ms))
     return "\n".join(rows)

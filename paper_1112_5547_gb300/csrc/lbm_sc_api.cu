@@ -89,11 +89,17 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.G = p->G;
     pl.ref_A = p->rho_ref_A;
     pl.ref_B = p->rho_ref_B;
+    lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo,
+                            pl.Np);
     return pl;
 }
 
+// One population buffer: 2 species x Q ghost-padded planes.
 size_t population_bytes(const lbm_sc_params* p) {
-    return (size_t)2 * q_of(p->lattice) * (size_t)p->nx * p->ny * p->nz * store_bytes(p->precision);
+    int px, py, gxo, gyo;
+    long long Np;
+    lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), px, py, gxo, gyo, Np);
+    return (size_t)2 * q_of(p->lattice) * (size_t)Np * store_bytes(p->precision);
 }
 
 size_t partial_bytes(const Plan& pl) {
@@ -125,7 +131,7 @@ size_t lbm_sc_workspace_bytes(const lbm_sc_params* p) {
     // each population buffer is followed by at least kAlign bytes of padding, so a
     // 4-byte-word read around the last 16-bit value stays inside the buffer's span
     return 2 * align_up(population_bytes(p) + kAlign) + align_up(partial_bytes(pl)) +
-           align_up(lbmsc::kNumDiag * sizeof(double));
+           align_up(lbmsc::kNumDiag * sizeof(double)) + kAlign /* error word */;
 }
 
 lbm_status lbm_sc_create(const lbm_sc_params* p, void* d_workspace, size_t workspace_bytes, void* cuda_stream,
@@ -148,6 +154,8 @@ lbm_status lbm_sc_create(const lbm_sc_params* p, void* d_workspace, size_t works
     h->buf[1] = h->ws + pb;
     h->partials = reinterpret_cast<double*>(h->ws + 2 * pb);
     h->result = reinterpret_cast<double*>(h->ws + 2 * pb + align_up(partial_bytes(h->plan)));
+    h->plan.err = reinterpret_cast<int*>(h->ws + 2 * pb + align_up(partial_bytes(h->plan)) +
+                                         align_up(lbmsc::kNumDiag * sizeof(double)));
     h->cur = 0;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     {
@@ -166,7 +174,7 @@ lbm_status lbm_sc_create(const lbm_sc_params* p, void* d_workspace, size_t works
 
 lbm_status lbm_sc_set_tuning(lbm_sc_handle* h, const lbm_sc_tuning* t) {
     if (!h || !t || t->zchunk < 0) return LBM_ERR_INVALID_ARG;
-    if (!lbmsc::tile_supported(t->tile, h->params.lattice, h->params.precision)) return LBM_ERR_INVALID_ARG;
+    if (!lbmsc::tile_fits(t->tile, h->plan)) return LBM_ERR_INVALID_ARG;
     const lbmsc::TileShape ts = lbmsc::kTiles[t->tile];
     h->plan.step_tile = t->tile;
     // persistent kernels: ~8 items per SM, chunks of at least 32 planes
@@ -194,6 +202,7 @@ lbm_status lbm_sc_set_stream(lbm_sc_handle* h, void* cuda_stream) {
 lbm_status lbm_sc_init_fields(lbm_sc_handle* h, const void* d_rhoA, const void* d_rhoB, const void* d_u) {
     if (!h || !d_rhoA || !d_rhoB) return LBM_ERR_INVALID_ARG;
     h->cur = 0;
+    if (cudaMemsetAsync(h->plan.err, 0, sizeof(int), h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     return cuda_status(launch_init(h->plan, d_rhoA, d_rhoB, d_u, h->buf[0], h->stream));
 }
 
@@ -243,7 +252,10 @@ lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm
     e = lbmsc::diag_finish(h->partials, lbmsc::fused_blocks(h->plan), h->result, h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     double r[lbmsc::kNumDiag];
+    int err_word = 0;
     e = cudaMemcpyAsync(r, h->result, sizeof(r), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    e = cudaMemcpyAsync(&err_word, h->plan.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
@@ -263,6 +275,7 @@ lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm
     host_out->out_count = r[lbmsc::kOutCount];
     host_out->out_rho_A = r[lbmsc::kOutRhoA];
     host_out->out_p = r[lbmsc::kOutP];
+    if (err_word != 0) return LBM_ERR_TIMEOUT;
     if (host_out->nonfinite > 0 || !(host_out->min_rho_A > 0) || !(host_out->min_rho_B > 0))
         return LBM_ERR_UNSTABLE;
     return LBM_OK;
@@ -306,10 +319,15 @@ lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_byt
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
 
-lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, const void** d_populations) {
+lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y, int* ghost_x,
+                         int* ghost_y, const void** d_populations) {
     if (!h) return LBM_ERR_INVALID_ARG;
     if (elem_bytes) *elem_bytes = (int)store_bytes(h->params.precision);
     if (q) *q = q_of(h->params.lattice);
+    if (pitch_x) *pitch_x = h->plan.px;
+    if (pitch_y) *pitch_y = h->plan.py;
+    if (ghost_x) *ghost_x = h->plan.gxo;
+    if (ghost_y) *ghost_y = h->plan.gyo;
     if (d_populations) *d_populations = h->buf[h->cur];
     return LBM_OK;
 }

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(TX* TY, 1)
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const size_t N = (size_t)a.N;
+    const size_t Np = (size_t)a.Np;
 
     const bool halo = tid < H;
     int hfx, hfy;
@@ -83,11 +83,6 @@ __global__ void __launch_bounds__(TX* TY, 1)
         const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
         const int hgx = (x0 - 1 + hfx + nx) % nx;
         const int hgy = (y0 - 1 + hfy + ny) % ny;
-        // source columns of the pulls (x - c_x, y - c_y) for c = -1, 0, +1
-        const int oxs[3] = {wrap_inc(gx, nx), gx, wrap_dec(gx, nx)};
-        const int oys[3] = {wrap_inc(gy, ny), gy, wrap_dec(gy, ny)};
-        const int hxs[3] = {wrap_inc(hgx, nx), hgx, wrap_dec(hgx, nx)};
-        const int hys[3] = {wrap_inc(hgy, ny), hgy, wrap_dec(hgy, ny)};
 
         // Copies of plane q (z = z0 - 1 + q) into stage q % STAGES; always commits a
         // group (empty past the last plane) so the wait counts stay uniform.
@@ -99,18 +94,16 @@ __global__ void __launch_bounds__(TX* TY, 1)
                 C* st = stage + (size_t)(q % STAGES) * T::stage_floats;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const size_t zoff = (size_t)zs[L::c(i, 2) + 1] * ny;
-                    const size_t on = (size_t)oxs[L::c(i, 0) + 1] + (size_t)nx * (oys[L::c(i, 1) + 1] + zoff);
-                    cp_async4(st + (size_t)i * NODES + tid, a.fin + (size_t)i * N + on);
-                    cp_async4(st + (size_t)(Q + i) * NODES + tid, a.fin + (size_t)(Q + i) * N + on);
+                    const size_t on = cell(a, gx - L::c(i, 0), gy - L::c(i, 1), zs[L::c(i, 2) + 1]);
+                    cp_async4(st + (size_t)i * NODES + tid, a.fin + (size_t)i * Np + on);
+                    cp_async4(st + (size_t)(Q + i) * NODES + tid, a.fin + (size_t)(Q + i) * Np + on);
                 }
                 if (halo) {
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
-                        const size_t zoff = (size_t)zs[L::c(i, 2) + 1] * ny;
-                        const size_t hn = (size_t)hxs[L::c(i, 0) + 1] + (size_t)nx * (hys[L::c(i, 1) + 1] + zoff);
-                        cp_async4(st + (size_t)i * NODES + OWN + tid, a.fin + (size_t)i * N + hn);
-                        cp_async4(st + (size_t)(Q + i) * NODES + OWN + tid, a.fin + (size_t)(Q + i) * N + hn);
+                        const size_t hn = cell(a, hgx - L::c(i, 0), hgy - L::c(i, 1), zs[L::c(i, 2) + 1]);
+                        cp_async4(st + (size_t)i * NODES + OWN + tid, a.fin + (size_t)i * Np + hn);
+                        cp_async4(st + (size_t)(Q + i) * NODES + OWN + tid, a.fin + (size_t)(Q + i) * Np + hn);
                     }
                 }
             }
@@ -157,15 +150,7 @@ __global__ void __launch_bounds__(TX* TY, 1)
             C gA[3], gB[3];
             node_force<L, C>(nbr, a.G, gA, gB);
             node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-            if (owner) {
-                const int z = z0 - 1 + q;
-                const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    __stcs(a.fout + (size_t)i * N + node, f[0][i]);
-                    __stcs(a.fout + (size_t)(Q + i) * N + node, f[1][i]);
-                }
-            }
+            if (owner) store_node<L, float>(a, gx, gy, z0 - 1 + q, f);
         };
 
 #pragma unroll 1

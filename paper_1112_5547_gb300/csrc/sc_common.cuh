@@ -92,6 +92,12 @@ template <class S> struct LatticeArgs {
     int nx, ny, nz;
     int zchunk;         // planes per CTA along z (D3Q19)
     long long N;        // nx * ny * nz
+    // Population storage is ghost-padded: each z plane of a population is
+    // py rows of px values, node (x, y) at column x + gxo, row y + gyo.  The
+    // columns x = -1, nx and rows y = -1, ny hold the periodic images of the
+    // opposite edge (written by every store), so pulls never wrap in x or y.
+    int px, py, gxo, gyo;
+    long long Np;       // values per population plane: px * py * nz
     C omega_A, omega_B; // 1 / tau_s
     C tau_A, tau_B;
     C G;
@@ -134,6 +140,11 @@ template <> struct Ar<double> {
     __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
 };
+
+// Storage index of cell (x, y, z), x in [-gxo, px - gxo), y in [-gyo, py - gyo).
+template <class Args> __device__ __forceinline__ size_t cell(const Args& a, int x, int y, int z) {
+    return (size_t)(x + a.gxo) + (size_t)a.px * ((size_t)(y + a.gyo) + (size_t)a.py * (size_t)z);
+}
 
 __device__ __forceinline__ int wrap_dec(int x, int n) { return x == 0 ? n - 1 : x - 1; }
 __device__ __forceinline__ int wrap_inc(int x, int n) { return x == n - 1 ? 0 : x + 1; }

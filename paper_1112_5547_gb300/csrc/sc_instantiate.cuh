@@ -1,7 +1,10 @@
 // Typed launch helpers shared by the per-lattice translation units.
 #pragma once
 
+#include <cudaTypedefs.h>
+
 #include "sc_async.cuh"
+#include "sc_tma.cuh"
 #include "sc_kernels.cuh"
 #include "sc_pipe.cuh"
 #include "sc_regpipe.cuh"
@@ -19,6 +22,11 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     a.nz = p.nz;
     a.zchunk = p.zchunk;
     a.N = p.N;
+    a.px = p.px;
+    a.py = p.py;
+    a.gxo = p.gxo;
+    a.gyo = p.gyo;
+    a.Np = p.Np;
     a.omega_A = (C)(1.0 / p.tau_A);
     a.omega_B = (C)(1.0 / p.tau_B);
     a.tau_A = (C)p.tau_A;
@@ -66,6 +74,66 @@ cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st)
     sc_step_reload_kernel<L, S, TX, TY, kMin><<<step_grid(p), dim3(TX, TY), 0, st>>>(a);
     return cudaGetLastError();
 }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+template <class L, class S, int TX, int TY, int ST> struct TmaLaunch {
+    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
+};
+template <int TX, int TY, int ST> struct TmaLaunch<D3Q19, float, TX, TY, ST> {
+    static cudaError_t run(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
+        const TileShape& ts = kTiles[p.step_tile];
+        using T = TmaTile<TX, TY, ST>;
+        // box x start (x0 + gxo - 4) must be 16-byte aligned for every 32-node tile
+        if (p.gxo < 4 || p.gxo % 4 != 0 || (p.px * 4) % 16 != 0 || p.nx < TX || p.ny < TY)
+            return cudaErrorInvalidValue;
+        auto enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        // 4-D view of one population buffer: x, y (ghost-padded), z, plane (s*Q + i)
+        CUtensorMap map;
+        const cuuint64_t dims[4] = {(cuuint64_t)p.px, (cuuint64_t)p.py, (cuuint64_t)p.nz, (cuuint64_t)T::Q2};
+        const cuuint64_t strides[3] = {(cuuint64_t)p.px * 4, (cuuint64_t)p.px * p.py * 4, (cuuint64_t)p.Np * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)T::BX, (cuuint32_t)T::BY, 1, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(a.fin), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        auto kern = sc_step_tma_kernel<TX, TY, ST>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        if (ts.cx == 1 && ts.cy == 1) {
+            kern<<<step_grid(p), dim3(TX, TY), T::smem_bytes, st>>>(map, a, p.err);
+            return cudaGetLastError();
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = step_grid(p);
+        cfg.blockDim = dim3(TX, TY);
+        cfg.dynamicSmemBytes = T::smem_bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = ts.cx;
+        attr[0].val.clusterDim.y = ts.cy;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, map, a, p.err);
+    }
+};
 
 template <class L, class S, int TX, int TY, int MINB> struct RegPipeLaunch {
     static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
@@ -130,7 +198,9 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[3].ty == 4 && kTiles[4].tx == 64 && kTiles[5].stages == 3 && kTiles[6].stages == 4 &&
                       kTiles[7].tx == 64 && kTiles[8].kind == 2 && kTiles[9].tx == 64 && kTiles[10].ty == 4 &&
                       kTiles[11].stages == 6 && kTiles[12].ty == 8 && kTiles[13].tx == 64 && kTiles[14].stages == 4 &&
-                      kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kNumTiles == 18,
+                      kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kTiles[18].kind == 5 &&
+                      kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
+                      kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kNumTiles == 26,
                   "tile table and dispatch disagree");
     switch (p.step_tile) {
         case 0: return step_tiled<L, S, 32, 8>(p, a, st);
@@ -151,6 +221,14 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
         case 15: return RegPipeLaunch<L, S, 32, 4, 3>::run(p, a, st);
         case 16: return RegPipeLaunch<L, S, 32, 8, 1>::run(p, a, st);
         case 17: return RegPipeLaunch<L, S, 16, 8, 3>::run(p, a, st);
+        case 18: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+        case 19: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+        case 20: return TmaLaunch<L, S, 32, 4, 4>::run(p, a, st);
+        case 21: return TmaLaunch<L, S, 32, 4, 2>::run(p, a, st);
+        case 22:
+        case 23:
+        case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+        case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
     }
 }
 

@@ -34,28 +34,26 @@ template <class L, class S>
 __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y, int z,
                                           typename Codec<S>::C (&f)[2][L::Q]) {
     using C = typename Codec<S>::C;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int xs[3] = {wrap_inc(x, nx), x, wrap_dec(x, nx)};  // source x for c_x = -1, 0, +1
-    const int ys[3] = {wrap_inc(y, ny), y, wrap_dec(y, ny)};
-    int zs[3] = {z, z, z};
+    const int nz = a.nz;
+    int zs[3] = {z, z, z};  // source plane for c_z = -1, 0, +1
     if (L::D == 3) {
         zs[0] = wrap_inc(z, nz);
         zs[2] = wrap_dec(z, nz);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const int sx = xs[L::c(i, 0) + 1], sy = ys[L::c(i, 1) + 1], sz = zs[L::c(i, 2) + 1];
-        const size_t node = (size_t)sx + (size_t)nx * ((size_t)sy + (size_t)ny * sz);
+        // x - c_x and y - c_y lie in [-1, n]: the ghost images make them valid
+        const size_t node = cell(a, x - L::c(i, 0), y - L::c(i, 1), zs[L::c(i, 2) + 1]);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-            f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.N + node, off);
+            f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.Np + node, off);
         }
     }
 }
 
 template <class L, class S>
-__device__ __forceinline__ void store_node(const LatticeArgs<S>& a, size_t node,
+__device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
                                            const typename Codec<S>::C (&f)[2][L::Q]) {
     using C = typename Codec<S>::C;
 #pragma unroll
@@ -63,7 +61,31 @@ __device__ __forceinline__ void store_node(const LatticeArgs<S>& a, size_t node,
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-            Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.N + node, f[s][i], off);
+            Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], off);
+        }
+    }
+}
+
+// Post-collision populations of node (x, y, z), x in [0, nx), y in [0, ny), and
+// of its periodic images in the ghost columns x in {-2, -1, nx, nx + 1} and
+// rows y in {-2, -1, ny, ny + 1}.  Two ghost layers let a node of the halo
+// ring itself (x = -1 .. nx) pull without wrapping.
+template <class L, class S>
+__device__ __forceinline__ void store_node(const LatticeArgs<S>& a, int x, int y, int z,
+                                           const typename Codec<S>::C (&f)[2][L::Q]) {
+    store_cell<L, S>(a, cell(a, x, y, z), f);
+    const int nx = a.nx, ny = a.ny;
+    if (x < 2 || x >= nx - 2 || y < 2 || y >= ny - 2) {
+#pragma unroll 1
+        for (int ix = -2; ix <= 2; ++ix) {
+            const int xi = x + ix * nx;
+            if (xi < -2 || xi > nx + 1) continue;
+#pragma unroll 1
+            for (int iy = -2; iy <= 2; ++iy) {
+                const int yi = y + iy * ny;
+                if ((ix | iy) == 0 || yi < -2 || yi > ny + 1) continue;
+                store_cell<L, S>(a, cell(a, xi, yi, z), f);
+            }
         }
     }
 }
@@ -146,7 +168,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
             node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-            if (owner) store_node<L, S>(a, node, f);
+            if (owner) store_node<L, S>(a, gx, gy, z, f);
         } else {
             // physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2 shift, Sec. 2.3)
             C jA[3], jB[3];
@@ -314,7 +336,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const Latt
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-        if (owner) store_node<L, S>(a, (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z), f);
+        if (owner) store_node<L, S>(a, gx, gy, z, f);
     };
 
     if (L::D == 2) {
@@ -370,18 +392,23 @@ __global__ void __launch_bounds__(NT) sc_diag_finish_kernel(const double* __rest
 
 // Populations of the rest / moving equilibrium: the buffer slot of direction i
 // at node x holds f^eq_i(rho_s(x + c_i), u(x + c_i)), so pulling it at x + c_i
-// gives f_i(x + c_i, 0) = f^eq_i of that node.
+// gives f_i(x + c_i, 0) = f^eq_i of that node.  The ghost columns and rows get
+// the values of their periodic images.
 template <class L, class S>
 __global__ void __launch_bounds__(256)
     sc_init_kernel(const LatticeArgs<S> a, const typename Codec<S>::C* __restrict__ rhoA,
                    const typename Codec<S>::C* __restrict__ rhoB, const typename Codec<S>::C* __restrict__ u) {
     using C = typename Codec<S>::C;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(n % nx);
-        const int y = (int)((n / nx) % ny);
-        const int z = (int)(n / ((long long)nx * ny));
+    const int ex = nx + 4, ey = ny + 4;  // cells x in [-2, nx + 1], y in [-2, ny + 1]
+    const long long ncells = (long long)ex * ey * nz;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int cx = (int)(k % ex) - 2;
+        const int cy = (int)((k / ex) % ey) - 2;
+        const int z = (int)(k / ((long long)ex * ey));
+        const size_t n = cell(a, cx, cy, z);
+        const int x = ((cx % nx) + nx) % nx, y = ((cy % ny) + ny) % ny;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = (x + L::c(i, 0) + nx) % nx;
@@ -400,7 +427,7 @@ __global__ void __launch_bounds__(256)
                 const C rho = s == 0 ? rhoA[m] : rhoB[m];
                 const C f = (C)L::w(i) * rho * shape;
                 const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.N + n, f, off);
+                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + n, f, off);
             }
         }
     }

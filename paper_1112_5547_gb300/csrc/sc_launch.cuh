@@ -19,7 +19,29 @@ struct Plan {
     int step_zchunk;
     int sm_count;   // multiprocessors of the device (persistent grids)
     double tau_A, tau_B, G, ref_A, ref_B;
+    int px, py, gxo, gyo;  // ghost-padded storage geometry (see LatticeArgs)
+    long long Np;          // values per population plane
+    int* err;              // device error word (set by a kernel whose bounded wait expired)
 };
+
+// Ghost-padded storage geometry for a lattice.  Node x = 0 sits 128 bytes into
+// each row and the row pitch is a multiple of 128 bytes, so every warp's row
+// segment of a tile starting at a multiple of 32 nodes is whole cache lines
+// (a misaligned store would leave partial sectors shared with the next CTA's
+// tile).  The ghost columns x = -2, -1, nx, nx+1 and rows y = -2, -1, ny, ny+1
+// hold periodic images; the columns up to 16 bytes beyond them exist so that
+// 16-byte-aligned TMA boxes of x0 - 16 bytes .. x0 + TX + 16 bytes stay inside
+// the row.
+inline void storage_geometry(int nx, int ny, int nz, int elem_bytes, int& px, int& py, int& gxo, int& gyo,
+                             long long& Np) {
+    const int line = 128 / elem_bytes;  // values per 128 bytes
+    const int box_pad = 16 / elem_bytes;
+    gxo = line;
+    gyo = 2;
+    px = (nx + gxo + box_pad + line - 1) / line * line;
+    py = ny + 2 * gyo;
+    Np = (long long)px * py * nz;
+}
 
 // Tile of one CTA (threads = TX * TY, one (x, y) column each) for the moments
 // kernel, and the tiles the step kernel can be launched with (autotuned).
@@ -32,14 +54,20 @@ constexpr int kTY = 8;
 // kind 3: low-register kernel that re-pulls a plane for its collision, with
 //         `stages` = CTAs per SM requested from the register allocator;
 // kind 4: register-pipelined kernel with three planes of pulls in registers
-//         (D3Q19, 32-bit and 16-bit storage), `stages` = CTAs per SM.
-struct TileShape { int tx, ty, kind, stages; };
-constexpr int kNumTiles = 18;
-constexpr TileShape kTiles[kNumTiles] = {{32, 8, 0, 0}, {32, 16, 0, 0}, {64, 8, 0, 0}, {32, 4, 0, 0},
-                                         {64, 4, 0, 0}, {32, 8, 1, 3},  {32, 8, 1, 4},  {64, 4, 1, 3},
-                                         {32, 8, 2, 0}, {64, 4, 2, 0},  {32, 4, 2, 0},  {32, 4, 3, 6},
-                                         {32, 8, 3, 3}, {64, 4, 3, 3},  {32, 4, 3, 4},  {32, 4, 4, 3},
-                                         {32, 8, 4, 1}, {16, 8, 4, 3}};
+//         (D3Q19, 32-bit and 16-bit storage), `stages` = CTAs per SM;
+// kind 5: TMA-fed kernel with `stages` shared-memory stages (D3Q19, FP32
+//         storage, lattices at least one tile wide in x and y), launched as
+//         clusters of cx x cy neighbouring tiles (co-scheduled on one GPC, so
+//         the halo lines the tiles share are fetched into one die's L2).
+struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1; };
+constexpr int kNumTiles = 26;
+constexpr TileShape kTiles[kNumTiles] = {
+    {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
+    {32, 8, 1, 3},       {32, 8, 1, 4},       {64, 4, 1, 3},       {32, 8, 2, 0},       {64, 4, 2, 0},
+    {32, 4, 2, 0},       {32, 4, 3, 6},       {32, 8, 3, 3},       {64, 4, 3, 3},       {32, 4, 3, 4},
+    {32, 4, 4, 3},       {32, 8, 4, 1},       {16, 8, 4, 3},       {32, 8, 5, 3},       {64, 4, 5, 3},
+    {32, 4, 5, 4},       {32, 4, 5, 2},       {64, 4, 5, 3, 1, 2}, {64, 4, 5, 3, 1, 4}, {64, 4, 5, 3, 2, 2},
+    {32, 8, 5, 3, 2, 2}};
 
 inline bool tile_supported(int tile, int lattice, int precision) {
     if (tile < 0 || tile >= kNumTiles) return false;
@@ -49,8 +77,21 @@ inline bool tile_supported(int tile, int lattice, int precision) {
         case 2: return lattice == 1;
         case 3: return true;
         case 4: return lattice == 1 && precision != 0;
+        case 5: return lattice == 1 && precision == 1;
     }
     return false;
+}
+
+// Size rules beyond the lattice kind and precision: the TMA boxes need the
+// lattice to span at least one tile in x and y.
+inline bool tile_fits(int tile, const Plan& p) {
+    if (!tile_supported(tile, p.lattice, p.precision)) return false;
+    const TileShape& t = kTiles[tile];
+    if (t.kind == 5) {
+        const int tiles_x = (p.nx + t.tx - 1) / t.tx, tiles_y = (p.ny + t.ty - 1) / t.ty;
+        return p.nx >= t.tx && p.ny >= t.ty && tiles_x % t.cx == 0 && tiles_y % t.cy == 0;
+    }
+    return true;
 }
 
 struct MomentsOut {

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_pipe_kernel(const Lattic
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const size_t N = (size_t)a.N;
+    const size_t Np = (size_t)a.Np;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
@@ -66,8 +66,6 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_pipe_kernel(const Lattic
     halo_cell<TX, TY>(tid, hfx, hfy);
     const int hgx = (x0 - 1 + hfx + nx) % nx;
     const int hgy = (y0 - 1 + hfy + ny) % ny;
-    const int hxs[3] = {wrap_inc(hgx, nx), hgx, wrap_dec(hgx, nx)};
-    const int hys[3] = {wrap_inc(hgy, ny), hgy, wrap_dec(hgy, ny)};
 
     auto zof = [&](int q) {
         const int z = z0 - 1 + q;
@@ -92,10 +90,9 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_pipe_kernel(const Lattic
                 const int zs[3] = {wrap_inc(z, nz), z, wrap_dec(z, nz)};
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const size_t hn = (size_t)hxs[L::c(i, 0) + 1] +
-                                      (size_t)nx * ((size_t)hys[L::c(i, 1) + 1] + (size_t)ny * zs[L::c(i, 2) + 1]);
-                    cp_async_bytes<sizeof(S)>(hst + (size_t)i * H + tid, a.fin + (size_t)i * N + hn);
-                    cp_async_bytes<sizeof(S)>(hst + (size_t)(Q + i) * H + tid, a.fin + (size_t)(Q + i) * N + hn);
+                    const size_t hn = cell(a, hgx - L::c(i, 0), hgy - L::c(i, 1), zs[L::c(i, 2) + 1]);
+                    cp_async_bytes<sizeof(S)>(hst + (size_t)i * H + tid, a.fin + (size_t)i * Np + hn);
+                    cp_async_bytes<sizeof(S)>(hst + (size_t)(Q + i) * H + tid, a.fin + (size_t)(Q + i) * Np + hn);
                 }
             }
             cp_async_commit();
@@ -139,7 +136,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_pipe_kernel(const Lattic
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-        if (owner) store_node<L, S>(a, (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * zof(q)), f);
+        if (owner) store_node<L, S>(a, gx, gy, zof(q), f);
     };
 
     C R[2][Q];

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const size_t N = (size_t)a.N;
+    const size_t Np = (size_t)a.Np;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
@@ -58,8 +58,6 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
     halo_cell<TX, TY>(tid, hfx, hfy);
     const int hgx = (x0 - 1 + hfx + nx) % nx;
     const int hgy = (y0 - 1 + hfy + ny) % ny;
-    const int hxs[3] = {wrap_inc(hgx, nx), hgx, wrap_dec(hgx, nx)};
-    const int hys[3] = {wrap_inc(hgy, ny), hgy, wrap_dec(hgy, ny)};
 
     auto zof = [&](int q) {
         const int z = z0 - 1 + q;
@@ -74,12 +72,11 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
             const int zs[3] = {wrap_inc(z, nz), z, wrap_dec(z, nz)};
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const size_t hn = (size_t)hxs[L::c(i, 0) + 1] +
-                                  (size_t)nx * ((size_t)hys[L::c(i, 1) + 1] + (size_t)ny * zs[L::c(i, 2) + 1]);
+                const size_t hn = cell(a, hgx - L::c(i, 0), hgy - L::c(i, 1), zs[L::c(i, 2) + 1]);
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const int j = s * Q + i;
-                    const S* src = a.fin + (size_t)j * N + hn;
+                    const S* src = a.fin + (size_t)j * Np + hn;
                     if constexpr (sizeof(S) >= 4) {
                         cp_async_bytes<sizeof(S)>(&hst[j][tid], src);
                     } else {
@@ -138,7 +135,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-        if (owner) store_node<L, S>(a, (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * zof(q)), X);
+        if (owner) store_node<L, S>(a, gx, gy, zof(q), X);
     };
     // one plane of the steady state; false once the chunk is done
     auto body = [&](int q, C (&Xq)[2][Q], C (&Xq1)[2][Q], C (&Xq2)[2][Q]) -> bool {

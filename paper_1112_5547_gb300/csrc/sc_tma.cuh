@@ -1,0 +1,206 @@
+// TMA-fed D3Q19 step for FP32 storage.
+//
+// Same per-node arithmetic and order as the other step kernels (sc_node.cuh:
+// Eq. eq:be with the force of Eq. FORCE, paper Sec. 2.1), so results are
+// bit-identical; only the data movement differs.  Per z plane of the CTA's
+// chunk one elected thread issues 38 tensor copies (cp.async.bulk.tensor, one
+// per species and direction, completing on an mbarrier), each a box of
+// (TX + 8) x (TY + 2) values of the ghost-padded population plane that the
+// direction is pulled from:
+//     x from x0 - 4 (16-byte aligned, as TMA requires) to x0 + TX + 4,
+//     y from y0 - 1 - c_y to y0 + TY - c_y,  z = plane - c_z (periodic).
+// The pulled value of frame node (fx, fy) (frame (1, 1) = tile (0, 0)) is then
+// box[fy][fx + 3 - c_x]: every pull, for the tile and for its one-node halo
+// ring, is a shared-memory load at a constant offset.  S stages keep S - 1
+// planes of copies in flight.
+//
+// Per plane q: wait for its copies; read the own node's 38 pulls into
+// registers and write own and halo densities to the four-slot ring;
+// one barrier (ring complete, stage q free); the elected thread refills the
+// stage with plane q + S; collide plane q - 1 from registers and store.
+// Every mbarrier wait is bounded: on expiry the CTA raises the error word and
+// leaves (the host reports LBM_ERR_TIMEOUT).
+#pragma once
+
+#include <cuda.h>
+
+#include "sc_kernels.cuh"
+
+namespace lbmsc {
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Iterations of mbarrier.try_wait before a wait is declared lost (each try
+// waits up to a hardware time slice; this bound is seconds, far beyond any
+// plane's copies).
+constexpr int kMbarSpinLimit = 1 << 24;
+
+template <int TX, int TY, int S> struct TmaTile {
+    static constexpr int BX = TX + 8, BY = TY + 2;
+    static constexpr int FX = TX + 2, FY = TY + 2;
+    static constexpr int H = 2 * FX + 2 * TY;
+    static constexpr int Q2 = 2 * D3Q19::Q;
+    static constexpr unsigned box_bytes = BX * BY * 4;
+    static constexpr unsigned box_stride = (box_bytes + 127) / 128 * 128;  // TMA destinations 128-byte aligned
+    static constexpr unsigned stage_bytes = Q2 * box_stride;
+    static constexpr size_t ring_bytes = (size_t)4 * 2 * FY * FX * 4;
+    static constexpr size_t smem_bytes = 128 + (size_t)S * stage_bytes + ring_bytes + (size_t)S * 8;
+};
+
+template <int TX, int TY, int S>
+__global__ void __launch_bounds__(TX* TY, 1)
+    sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const LatticeArgs<float> a, int* __restrict__ err) {
+    using L = D3Q19;
+    using T = TmaTile<TX, TY, S>;
+    using C = float;
+    constexpr int Q = L::Q, Q2 = T::Q2, BX = T::BX, FX = T::FX, FY = T::FY, H = T::H;
+    constexpr unsigned BS = T::box_stride / 4;  // floats between boxes
+    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
+    static_assert(BX * 4 % 16 == 0, "TMA box rows are whole 16-byte units");
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+    C* const stage = reinterpret_cast<C*>(base);
+    C(*const ring)[2][FY][FX] = reinterpret_cast<C(*)[2][FY][FX]>(base + (size_t)S * T::stage_bytes);
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(base + (size_t)S * T::stage_bytes + T::ring_bytes);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, nz);
+    const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
+    const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
+    const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+    const bool halo = tid < H;
+    int hfx, hfy;
+    halo_cell<TX, TY>(tid, hfx, hfy);
+
+    auto zof = [&](int q) {
+        const int z = z0 - 1 + q;
+        return z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    };
+    // elected thread: the 38 boxes of plane q into stage q % S
+    auto issue = [&](int q) {
+        const int z = zof(q);
+        const int st = q % S;
+        mbar_arrive_expect_tx(&bars[st], Q2 * T::box_bytes);
+        C* sb = stage + (size_t)st * (T::stage_bytes / 4);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            int zs = z - L::c(i, 2);
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+            const int cy = y0 + a.gyo - 1 - L::c(i, 1);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int j = s * Q + i;
+                tma_load_4d(sb + (size_t)j * BS, &tmap, &bars[st], x0 + a.gxo - 4, cy, zs, j);
+            }
+        }
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < S && q < nplanes; ++q) issue(q);
+
+    bool lost = false;
+    auto wait_plane = [&](int q) {
+        const int st = q % S;
+        const unsigned parity = (unsigned)((q / S) & 1);
+        int n = 0;
+        while (!mbar_try_wait(&bars[st], parity)) {
+            if (++n >= kMbarSpinLimit) {
+                lost = true;
+                break;
+            }
+        }
+    };
+    // own pulls of plane q into X; own and halo densities into ring slot q % 4
+    auto take_plane = [&](int q, C (&X)[2][Q]) {
+        const C* sb = stage + (size_t)(q % S) * (T::stage_bytes / 4);
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+#pragma unroll
+            for (int s = 0; s < 2; ++s) X[s][i] = sb[(size_t)(s * Q + i) * BS + (ty + 1) * BX + tx + 4 - L::c(i, 0)];
+        ring[q & 3][0][ty + 1][tx + 1] = node_density<L, C>(X[0]);
+        ring[q & 3][1][ty + 1][tx + 1] = node_density<L, C>(X[1]);
+        if (halo) {
+            C h[2][Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i)
+#pragma unroll
+                for (int s = 0; s < 2; ++s) h[s][i] = sb[(size_t)(s * Q + i) * BS + hfy * BX + hfx + 3 - L::c(i, 0)];
+            ring[q & 3][0][hfy][hfx] = node_density<L, C>(h[0]);
+            ring[q & 3][1][hfy][hfx] = node_density<L, C>(h[1]);
+        }
+    };
+    auto collide = [&](int q, C (&X)[2][Q]) {
+        const int sm = (q - 1) & 3, sc = q & 3, sp = (q + 1) & 3;
+        const C rA = ring[sc][0][ty + 1][tx + 1];
+        const C rB = ring[sc][1][ty + 1][tx + 1];
+        auto nbr = [&](int s, int i) -> C {
+            const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
+            return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+        };
+        C gA[3], gB[3];
+        node_force<L, C>(nbr, a.G, gA, gB);
+        node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        if (owner) store_node<L, float>(a, gx, gy, zof(q), X);
+    };
+    // plane q arrives; plane q - 1 collides.  false when the chunk is done or a wait was lost.
+    auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> bool {
+        if (q >= nplanes) return false;
+        wait_plane(q);
+        take_plane(q, Xc);
+        if (__syncthreads_or(lost)) {
+            if (tid == 0) atomicExch(err, 1);
+            return false;
+        }
+        if (tid == 0 && q + S < nplanes) {
+            fence_proxy_async_smem();  // the stage's generic reads precede the async refill
+            issue(q + S);
+        }
+        if (q >= 2) collide(q - 1, Xp);
+        return true;
+    };
+
+    C R0[2][Q], R1[2][Q];
+#pragma unroll 1
+    for (int q = 0;; q += 2) {
+        if (!body(q, R0, R1)) break;
+        if (!body(q + 1, R1, R0)) break;
+    }
+}
+
+}  // namespace lbmsc

@@ -48,10 +48,14 @@ EXPORTS = (
 # kind 0: register-pipelined kernel; 1: persistent cp.async kernel; 2: software-pipelined kernel;
 # 3: low-register re-pull kernel (stages = CTAs per SM asked of the register allocator).
 # 4: register-pipelined kernel, three planes of pulls in registers (D3Q19, 32- and 16-bit storage).
+# 5: TMA-fed kernel (D3Q19, FP32 storage, lattices at least one tile wide), stages = smem stages.
 TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
-         (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8))
-TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4)
-TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3)
+         (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
+         (64, 4), (64, 4), (64, 4), (32, 8))
+TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5)
+TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3)
+# thread-block cluster of the TMA tiles (tiles in x, tiles in y)
+TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2))
 
 
 def tile_supported(tile: int, lattice: int, precision: int) -> bool:
@@ -61,7 +65,7 @@ def tile_supported(tile: int, lattice: int, precision: int) -> bool:
     kind = TILE_KIND[tile]
     if kind in (0, 3):
         return True
-    if kind == 1:
+    if kind in (1, 5):
         return lattice == LBM_D3Q19 and precision == LBM_F32
     if kind == 4:
         return lattice == LBM_D3Q19 and precision != LBM_F64
@@ -128,8 +132,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_sc_host_staging_bytes.argtypes = [P]
     lib.lbm_sc_host_staging_bytes.restype = ctypes.c_size_t
     lib.lbm_sc_run_host.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
-    lib.lbm_sc_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                  ctypes.POINTER(vp)]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.lbm_sc_layout.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(vp)]
     lib.lbm_sc_set_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
     lib.lbm_sc_get_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
     lib.lbm_sc_destroy.argtypes = [vp]
@@ -217,10 +221,12 @@ def lbm_sc_run_host(h: int, d_staging: int, staging_bytes: int, h_rhoA: int, h_r
 
 
 def lbm_sc_layout(h: int):
-    eb, q, ptr = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
-    _check(load().lbm_sc_layout(ctypes.c_void_p(h), ctypes.byref(eb), ctypes.byref(q), ctypes.byref(ptr)),
+    """(elem_bytes, Q, pitch_x, pitch_y, ghost_x, ghost_y, device pointer of the current populations)."""
+    vals = [ctypes.c_int() for _ in range(6)]
+    ptr = ctypes.c_void_p()
+    _check(load().lbm_sc_layout(ctypes.c_void_p(h), *(ctypes.byref(v) for v in vals), ctypes.byref(ptr)),
            "lbm_sc_layout")
-    return eb.value, q.value, ptr.value
+    return tuple(v.value for v in vals) + (ptr.value,)
 
 
 def lbm_sc_set_tuning(h: int, tile: int, zchunk: int = 0) -> None:
@@ -318,6 +324,16 @@ class Lattice:
         lbm_sc_set_tuning(self.handle, tile, zchunk)
         return self
 
+    def tile_fits(self, tile: int) -> bool:
+        """Whether the library accepts this tile for this lattice (kind, precision, size)."""
+        old = self.tuning()
+        try:
+            lbm_sc_set_tuning(self.handle, tile, 0)
+        except LbmError:
+            return False
+        lbm_sc_set_tuning(self.handle, old[0], old[1])
+        return True
+
     def tuning(self):
         return lbm_sc_get_tuning(self.handle)
 
@@ -339,13 +355,15 @@ class Lattice:
         return out
 
     def populations(self):
-        """The current population buffer as a (2, Q, N) tensor view (GPU velocity order)."""
+        """The current population buffer as a (2, Q, nz, pitch_y, pitch_x) tensor view
+        (GPU velocity order, ghost-padded; see lbm_sc_layout)."""
         t = self.torch
-        eb, q, ptr = lbm_sc_layout(self.handle)
+        eb, q, px, py, gx, gy, ptr = lbm_sc_layout(self.handle)
         dt = {8: t.float64, 4: t.float32}.get(eb)
         if dt is None:
             dt = t.bfloat16 if self.params.precision == LBM_F32_STORE_BF16 else t.float16
+        nz = self.params.nz
         base = self.workspace.data_ptr()
         off = ptr - base
-        n = 2 * q * self.N
-        return self.workspace[off: off + n * eb].view(dt).view(2, q, self.N)
+        n = 2 * q * nz * py * px
+        return self.workspace[off: off + n * eb].view(dt).view(2, q, nz, py, px)

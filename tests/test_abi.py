@@ -41,8 +41,18 @@ def test_workspace_sizes(lib):
     n = 10 * 12 * 14
     ws = lib.lbm_sc_workspace_bytes(p)
     assert ws >= 2 * 2 * 19 * n * 4
-    p16 = lib.make_params(lib.LBM_D3Q19, (10, 12, 14), 1.0, 1.0, 2.0, "bf16")
-    assert lib.lbm_sc_workspace_bytes(p16) < ws
+    p32 = lib.make_params(lib.LBM_D3Q19, (10, 12, 200), 1.0, 1.0, 2.0, "f32")
+    p16 = lib.make_params(lib.LBM_D3Q19, (10, 12, 200), 1.0, 1.0, 2.0, "bf16")
+    assert lib.lbm_sc_workspace_bytes(p16) < 0.7 * lib.lbm_sc_workspace_bytes(p32)
+    # ghost-padded planes: pitch multiple of 16 bytes, one-node images on every side
+    for prec, eb in (("f64", 8), ("f32", 4), ("bf16", 2)):
+        pp = lib.make_params(lib.LBM_D3Q19, (10, 12, 14), 1.0, 1.0, 2.0, prec)
+        h = lib.lbm_sc_create(pp, 256 * 1024, lib.lbm_sc_workspace_bytes(pp), 0)
+        e, q, px, py, gx, gy, _ = lib.lbm_sc_layout(h)
+        lib.lbm_sc_destroy(h)
+        assert e == eb and q == 19 and gx * eb == 128 and gy == 2
+        assert (px * eb) % 128 == 0 and px >= 14 + gx + 16 // eb and py == 12 + 4
+        assert lib.lbm_sc_workspace_bytes(pp) >= 2 * 2 * 19 * px * py * 10 * eb
     p64 = lib.make_params(lib.LBM_D2Q9, (12, 14), 1.0, 1.0, 2.0, "f64")
     assert lib.lbm_sc_workspace_bytes(p64) >= 2 * 2 * 9 * 12 * 14 * 8
     assert lib.lbm_sc_host_staging_bytes(p) >= 6 * n * 4
@@ -79,18 +89,26 @@ def test_create_checks_workspace_without_touching_the_gpu(lib):
         lib.lbm_sc_create(p, 256 * 1024 + 8, need, 0)  # misaligned
     assert e.value.status == lib.LBM_ERR_INVALID_ARG
     h = lib.lbm_sc_create(p, 256 * 1024, need, 0)  # a fake address: create does not dereference it
-    eb, q, ptr = lib.lbm_sc_layout(h)
+    eb, q, px, py, gx, gy, ptr = lib.lbm_sc_layout(h)
     assert (eb, q, ptr) == (4, 9, 256 * 1024)
+    assert gx == 32 and gy == 2 and py == 8 + 2 * gy and px >= 8 + gx + 4 and (px * eb) % 128 == 0
     with pytest.raises(lib.LbmError):
         lib.lbm_sc_step(h, -1)
     lib.lbm_sc_destroy(h)
 
 
 def test_tuning_validation(lib):
-    p = lib.make_params(lib.LBM_D3Q19, (40, 8, 8), 1.0, 1.0, 2.0, "f32")
+    p = lib.make_params(lib.LBM_D3Q19, (40, 8, 64), 1.0, 1.0, 2.0, "f32")
     h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
     try:
         for t in range(len(lib.TILES)):
+            tx, ty = lib.TILES[t]
+            cx, cy = lib.TILE_CLUSTER[t]
+            fits = lib.TILE_KIND[t] != 5 or (64 >= tx and 8 >= ty and (64 // tx) % cx == 0 and (8 // ty) % cy == 0)
+            if not fits:
+                with pytest.raises(lib.LbmError):
+                    lib.lbm_sc_set_tuning(h, t, 0)
+                continue
             lib.lbm_sc_set_tuning(h, t, 0)
             assert lib.lbm_sc_get_tuning(h)[0] == t
         lib.lbm_sc_set_tuning(h, 1, 500)
@@ -111,6 +129,8 @@ def test_tuning_validation(lib):
                 kind = lib.TILE_KIND[t]
                 assert ok == (kind in (0, 3) or (kind == 2 and lat == lib.LBM_D3Q19)
                               or (kind == 4 and lat == lib.LBM_D3Q19 and prec != "f64"))
+                if kind == 5:  # TMA kernel also needs one full tile in x and y
+                    ok = False
                 if ok:
                     lib.lbm_sc_set_tuning(h, t, 0)
                 else:
