@@ -210,12 +210,14 @@ def main():
     # launch shape: autotuned on this lattice (state restored), or forced
     if args.tile >= 0:
         lat.set_tuning(args.tile, args.zchunk)
-        tune_info = {"tile": list(lbm_sc.TILES[args.tile]), "zchunk": lat.tuning()[1], "source": "forced"}
+        tune_info = {"tile_id": args.tile, "tile": list(lbm_sc.TILES[args.tile]), "kind": lbm_sc.TILE_KIND[args.tile],
+                     "cluster": list(lbm_sc.TILE_CLUSTER[args.tile]), "zchunk": lat.tuning()[1], "source": "forced"}
     else:
         from paper_1112_5547_gb300 import autotune
-        (tile, zc), table = autotune.autotune(lat)
-        tune_info = {"tile": list(lbm_sc.TILES[tile]), "zchunk": zc, "source": "autotuned",
-                     "candidates": len(table)}
+        (tile, zc), source = autotune.tuned(lat, store=(rank == 0))
+        tune_info = {"tile_id": tile, "tile": list(lbm_sc.TILES[tile]), "kind": lbm_sc.TILE_KIND[tile],
+                     "cluster": list(lbm_sc.TILE_CLUSTER[tile]), "zchunk": zc,
+                     "source": source if source == "autotuned" else "tuning cache (autotuned on GB300)"}
 
     # warm-up
     lat.step(args.warmup)
@@ -312,7 +314,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_lu": bytes_per_lu,
-                     "kernel": "sc_fused_kernel<D3Q19,%s> step" % prec},
+                     "kernel": "D3Q19 %s step, tile %s kind %d" % (prec, lbm_sc.TILES[lat.tuning()[0]],
+                                                                  lbm_sc.TILE_KIND[lat.tuning()[0]])},
         "gpu_launches": K,
         "clocks": clk,
         "diag": {"mass_A": d["mass_A"], "max_speed": d["max_speed"], "status": d["status"]},

@@ -66,3 +66,40 @@ def format_table(table: Sequence) -> str:
         rows.append("%2d %2dx%-2d k%d s%d c%dx%d  %6d  %.4f" % (tile, tx, ty, lbm_sc.TILE_KIND[tile],
                                                             lbm_sc.TILE_STAGES[tile], cx, cy, zc, ms))
     return "\n".join(rows)
+
+
+# ---- tuning cache --------------------------------------------------------------
+CACHE_PATH = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
+                                        "tuning_cache.json")
+
+
+def cache_key(lattice: "lbm_sc.Lattice") -> str:
+    prec = {v: k for k, v in lbm_sc.PRECISIONS.items()}[lattice.params.precision]
+    kind = "D2Q9" if lattice.lattice == lbm_sc.LBM_D2Q9 else "D3Q19"
+    return "%s/%s/%s" % (kind, prec, "x".join(str(s) for s in reversed(lattice.shape)))
+
+
+def tuned(lattice: "lbm_sc.Lattice", path: str = CACHE_PATH, store: bool = True, **kw):
+    """Apply the cached launch shape for this lattice kind, precision and size, or
+    autotune (state restored) and remember the winner.  Returns ((tile, zchunk), source)."""
+    import json
+    import os
+    key = cache_key(lattice)
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        tile, zc = cache[key]["tile"], cache[key]["zchunk"]
+        if lattice.tile_fits(tile):
+            lattice.set_tuning(tile, zc)
+            return (tile, lattice.tuning()[1]), "cache"
+    best, table = autotune(lattice, **kw)
+    if store:
+        cache[key] = {"tile": best[0], "zchunk": best[1], "ms_per_step": min(r[2] for r in table),
+                      "candidates": len(table)}
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(cache, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return best, "autotuned"
