@@ -165,6 +165,34 @@ LBM_SC_API lbm_status lbm_sc_moments(lbm_sc_handle* h, void* d_rhoA, void* d_rho
  * a density is <= 0. */
 LBM_SC_API lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm_sc_diag* host_out);
 
+/* The diagnostics of lbm_sc_diagnostics for a caller that cannot allocate
+ * device memory -- for example code running inside someone else's CUDA graph
+ * capture or custom allocator, or a plugin that is handed device buffers but
+ * may not call cudaMalloc itself.  It needs no handle and no workspace: the
+ * per-CTA partial sums go to a fixed 2 MiB array in the library's static
+ * device memory (allocated when the library is loaded, on every GPU that
+ * loads it, and kept until the process exits).  The paper has no counterpart;
+ * this is an interface convenience.
+ *   params        the lattice (same rules as lbm_sc_workspace_bytes)
+ *   d_populations device pointer to one population buffer in the layout of
+ *                 lbm_sc_layout (for example the pointer it returns)
+ *   window        as for lbm_sc_diagnostics, or NULL
+ *   d_out         device pointer to one lbm_sc_diag that receives the result
+ *   cuda_stream   stream the work is enqueued on; the call does not synchronise
+ * Returns LBM_ERR_INVALID_ARG for invalid parameters or pointers, and also when
+ * the lattice needs more than 16384 partial-sum slots (one per 32 x 8 column
+ * tile: more than about 4.2 million nodes per z plane), which the static array
+ * cannot hold.  Unlike lbm_sc_diagnostics it does not check stability or
+ * timeouts: read nonfinite and the minima from d_out.  The first call on each
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  Every call reuses the same array (its contents are left
+ * from the last call; each slot read is first written by the same call), so
+ * calls whose execution overlaps on the GPU -- on different streams, or from
+ * several threads -- race and must be serialised by the caller. */
+LBM_SC_API lbm_status lbm_sc_diagnostics_noalloc(const lbm_sc_params* params, const void* d_populations,
+                                                 const lbm_sc_window* window, lbm_sc_diag* d_out,
+                                                 void* cuda_stream);
+
 /* Bytes of device staging lbm_sc_run_host needs for its field copies. */
 LBM_SC_API size_t lbm_sc_host_staging_bytes(const lbm_sc_params* params);
 

@@ -41,6 +41,7 @@ EXPORTS = (
     "lbm_sc_workspace_bytes", "lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step",
     "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
     "lbm_sc_destroy", "lbm_sc_status_string", "lbm_sc_set_tuning", "lbm_sc_get_tuning",
+    "lbm_sc_diagnostics_noalloc",
 )
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
@@ -136,6 +137,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_sc_layout.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(vp)]
     lib.lbm_sc_set_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
     lib.lbm_sc_get_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
+    lib.lbm_sc_diagnostics_noalloc.argtypes = [P, vp, ctypes.POINTER(lbm_sc_window), vp, vp]
+    lib.lbm_sc_diagnostics_noalloc.restype = ctypes.c_int
     lib.lbm_sc_destroy.argtypes = [vp]
     lib.lbm_sc_destroy.restype = None
     lib.lbm_sc_status_string.argtypes = [ctypes.c_int]
@@ -171,6 +174,15 @@ def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, preci
 # ---- one Python function per C entry point ----------------------------------
 def lbm_sc_workspace_bytes(params: lbm_sc_params) -> int:
     return int(load().lbm_sc_workspace_bytes(ctypes.byref(params)))
+
+
+def lbm_sc_diagnostics_noalloc(params: lbm_sc_params, d_populations: int, window: Optional[lbm_sc_window],
+                               d_out: int, stream: int = 0) -> None:
+    """Diagnostics into a device lbm_sc_diag at d_out, scratch in the library's static memory."""
+    _check(load().lbm_sc_diagnostics_noalloc(ctypes.byref(params), ctypes.c_void_p(d_populations),
+                                             ctypes.byref(window) if window is not None else None,
+                                             ctypes.c_void_p(d_out), ctypes.c_void_p(stream)),
+           "lbm_sc_diagnostics_noalloc")
 
 
 def lbm_sc_host_staging_bytes(params: lbm_sc_params) -> int:
