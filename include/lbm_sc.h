@@ -113,7 +113,12 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * kernel that pulls a plane a second time for its collision, every lattice and
  * precision; 11 and 14 differ in the register budget); 15 = 32x4, 16 = 32x8,
  * 17 = 16x8 (register-pipelined kernel holding three planes of pulls, D3Q19
- * with 32- or 16-bit storage).  zchunk is the number
+ * with 32- or 16-bit storage); 18 = 32x8 with 3 stages, 19 = 64x4 with 3
+ * stages, 20 = 32x4 with 4 stages, 21 = 32x4 with 2 stages, and the cluster
+ * launches 22 = 64x4 in clusters of 1x2 tiles, 23 = 64x4 in 1x4, 24 = 64x4 in
+ * 2x2, 25 = 32x8 in 2x2 (TMA-fed kernel, D3Q19 with LBM_F32 only, lattices
+ * at least one tile wide in x and y whose tile counts divide by the cluster
+ * shape).  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {
@@ -214,6 +219,51 @@ LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t 
  * other padding is unused.  Any output pointer may be NULL. */
 LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y,
                                     int* ghost_x, int* ghost_y, const void** d_populations);
+
+/* ---- Ragged batch ---------------------------------------------------------
+ * Many independent lattices of different sizes and parameters advanced
+ * together, one kernel launch per time step for the whole batch.  Each step
+ * is Eq. eq:be with Eq. FORCE on every lattice of the batch, exactly as
+ * lbm_sc_step computes it: the results are bit-identical to stepping each
+ * lattice alone.  The paper runs one lattice at a time; batching is a
+ * throughput device for many small lattices, which alone cannot fill the GPU.
+ *
+ * The launch walks a work list of (lattice, x tile, y tile, z chunk) items,
+ * longest first, with a persistent grid of CTAs; per-lattice arguments come
+ * from a descriptor array.  Both live in the batch workspace (device memory
+ * owned by the caller).  When graph_steps > 0 and the stream is not the legacy
+ * default stream, whole chunks of graph_steps steps are replayed from a CUDA
+ * graph captured on the first use (one per starting parity); the remaining
+ * steps are direct launches.
+ *
+ * All handles of a batch must share the lattice kind and the precision
+ * (LBM_ERR_INVALID_ARG otherwise); each must have been initialised
+ * (lbm_sc_init_fields) before the first lbm_sc_batch_step.  While the batch
+ * exists, advance its lattices only through it: lbm_sc_batch_step reports
+ * LBM_ERR_INVALID_ARG if a handle was stepped on its own in between.
+ * lbm_sc_moments and lbm_sc_diagnostics on a handle read the state the batch
+ * left (enqueue them on the batch's stream, or synchronise it first).
+ *   tile    0 = 32x8, 1 = 32x4, 2 = 64x4 columns per CTA
+ *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
+ *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
+typedef struct lbm_sc_batch lbm_sc_batch;
+
+/* Bytes of batch workspace for these handles and shape (0 if invalid). */
+LBM_SC_API size_t lbm_sc_batch_workspace_bytes(lbm_sc_handle* const* handles, int n, int tile, int zchunk);
+
+/* Build a batch over n handles (the array is copied; the handles must outlive
+ * the batch).  d_workspace: >= lbm_sc_batch_workspace_bytes, 256-byte aligned.
+ * Uploads the descriptors and the work list and synchronises cuda_stream once. */
+LBM_SC_API lbm_status lbm_sc_batch_create(lbm_sc_handle* const* handles, int n, int tile, int zchunk,
+                                          int graph_steps, void* d_workspace, size_t workspace_bytes,
+                                          void* cuda_stream, lbm_sc_batch** out);
+
+/* Advance every lattice of the batch by nsteps (>= 0) on the batch's stream;
+ * asynchronous like lbm_sc_step. */
+LBM_SC_API lbm_status lbm_sc_batch_step(lbm_sc_batch* b, int nsteps);
+
+/* Release the batch (and its graphs).  The handles and workspace stay the caller's. */
+LBM_SC_API void lbm_sc_batch_destroy(lbm_sc_batch* b);
 
 /* Release the host handle.  The workspace stays the caller's. */
 LBM_SC_API void lbm_sc_destroy(lbm_sc_handle* h);

@@ -68,6 +68,49 @@ def format_table(table: Sequence) -> str:
     return "\n".join(rows)
 
 
+# ---- ragged batch ---------------------------------------------------------------
+def batch_candidates(lattices, zchunks=(0, 16, 32, 64), graph_steps=(0, 8, 32)):
+    """(tile, zchunk, graph_steps) triples for a batch (zchunk only for D3Q19)."""
+    zs = zchunks if lattices[0].lattice == lbm_sc.LBM_D3Q19 else (0,)
+    tiles = [t for t in range(len(lbm_sc.BATCH_TILES)) if all(lbm_sc.batch_tile_fits(t, lat) for lat in lattices)]
+    return [(t, z, g) for t in tiles for z in zs for g in graph_steps]
+
+
+def tune_batch(lattices, trial_steps: int = 8, warmup_steps: int = 2, cands=None, stream=None,
+               restore: bool = True):
+    """Time whole batched steps for each (tile, zchunk, graph_steps) candidate on
+    the caller's lattices (states saved and restored; even step counts) and
+    return (best, table) with table rows ((tile, zchunk, graph_steps), ms_per_step).
+    Graph chunks only take effect on a non-default stream."""
+    import torch
+    if (trial_steps + warmup_steps) % 2:
+        trial_steps += 1
+    stream = stream if stream is not None else lattices[0].stream
+    saved = [lat.populations().clone() for lat in lattices] if restore else None
+    table = []
+    for tile, z, g in (cands if cands is not None else batch_candidates(lattices)):
+        if g and trial_steps % g:
+            continue
+        b = lbm_sc.Batch(lattices, tile=tile, zchunk=z, graph_steps=g, stream=stream)
+        b.step(max(warmup_steps, g))  # the first chunk captures the graph
+        if max(warmup_steps, g) % 2:
+            b.step(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(trial_steps)
+        e1.record(stream)
+        e1.synchronize()
+        b.close()
+        table.append(((tile, z, g), e0.elapsed_time(e1) / trial_steps))
+    best = min(table, key=lambda r: r[1])
+    if saved is not None:
+        for lat, sv in zip(lattices, saved):
+            lat.populations().copy_(sv)
+        stream.synchronize()
+    return best[0], table
+
+
 # ---- tuning cache --------------------------------------------------------------
 CACHE_PATH = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.abspath(__file__)),
                                         "tuning_cache.json")

@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <new>
+
 #include "../../include/lbm_sc.h"
 #include "sc_launch.cuh"
 
@@ -344,6 +346,186 @@ const char* lbm_sc_status_string(lbm_status s) {
         case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT: bounded device wait expired";
     }
     return "unknown lbm_status";
+}
+
+}  // extern "C"
+
+// ---- ragged batch -------------------------------------------------------------
+#include <algorithm>
+#include <vector>
+
+#include "sc_batch_launch.h"
+
+struct lbm_sc_batch {
+    std::vector<lbm_sc_handle*> h;
+    std::vector<int> cur0;
+    int lattice, precision, tile, zchunk, graph_steps;
+    void* d_lats;
+    lbmsc::BatchItem* d_items;
+    int nitems;
+    int parity;
+    int sm_count;
+    cudaStream_t stream;
+    cudaGraphExec_t graph[2];  // graph_steps launches starting at parity 0 / 1
+};
+
+namespace {
+
+bool batch_valid(lbm_sc_handle* const* handles, int n, int tile, int zchunk) {
+    if (!handles || n < 1 || tile < 0 || tile >= lbmsc::kNumBatchTiles || zchunk < 0) return false;
+    for (int k = 0; k < n; ++k) {
+        if (!handles[k]) return false;
+        if (handles[k]->params.lattice != handles[0]->params.lattice ||
+            handles[k]->params.precision != handles[0]->params.precision)
+            return false;
+        if (!lbmsc::batch_tile_fits(tile, handles[k]->plan)) return false;
+    }
+    return true;
+}
+
+int batch_zchunk(const lbm_sc_handle* h, int zchunk) {
+    if (h->params.lattice == LBM_D2Q9) return 1;
+    const int zc = zchunk == 0 ? 32 : zchunk;
+    return zc > h->params.nz ? h->params.nz : zc;
+}
+
+std::vector<lbmsc::BatchItem> batch_items(lbm_sc_handle* const* handles, int n, int tile, int zchunk) {
+    std::vector<lbmsc::BatchItem> items;
+    std::vector<int> len;
+    const int tx = lbmsc::kBatchTileX[tile], ty = lbmsc::kBatchTileY[tile];
+    for (int k = 0; k < n; ++k) {
+        const lbm_sc_params& p = handles[k]->params;
+        const int zc = batch_zchunk(handles[k], zchunk);
+        for (int z0 = 0; z0 < p.nz; z0 += zc)
+            for (int y0 = 0; y0 < p.ny; y0 += ty)
+                for (int x0 = 0; x0 < p.nx; x0 += tx) {
+                    items.push_back({k, x0, y0, z0});
+                    len.push_back(std::min(zc, p.nz - z0));
+                }
+    }
+    // longest items first, so the grid-stride walk ends with the short ones
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return len[a] > len[b]; });
+    std::vector<lbmsc::BatchItem> sorted;
+    sorted.reserve(items.size());
+    for (size_t i : order) sorted.push_back(items[i]);
+    return sorted;
+}
+
+cudaError_t batch_launch_steps(lbm_sc_batch* b, int nsteps) {
+    for (int t = 0; t < nsteps; ++t) {
+        const cudaError_t e = lbmsc::batch_step(b->lattice, b->precision, b->tile, b->d_lats, b->d_items, b->nitems,
+                                                b->parity, b->sm_count, b->stream);
+        if (e != cudaSuccess) return e;
+        b->parity ^= 1;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_sc_batch_workspace_bytes(lbm_sc_handle* const* handles, int n, int tile, int zchunk) {
+    if (!batch_valid(handles, n, tile, zchunk)) return 0;
+    const size_t items = batch_items(handles, n, tile, zchunk).size();
+    return align_up(lbmsc::batch_lattice_bytes(handles[0]->params.precision, tile) * (size_t)n) +
+           align_up(items * sizeof(lbmsc::BatchItem));
+}
+
+lbm_status lbm_sc_batch_create(lbm_sc_handle* const* handles, int n, int tile, int zchunk, int graph_steps,
+                               void* d_workspace, size_t workspace_bytes, void* cuda_stream, lbm_sc_batch** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!batch_valid(handles, n, tile, zchunk) || !d_workspace || graph_steps < 0 || graph_steps % 2 != 0)
+        return LBM_ERR_INVALID_ARG;
+    if (((uintptr_t)d_workspace) % kAlign != 0) return LBM_ERR_INVALID_ARG;
+    if (workspace_bytes < lbm_sc_batch_workspace_bytes(handles, n, tile, zchunk)) return LBM_ERR_OUT_OF_MEMORY;
+    lbm_sc_batch* b = new (std::nothrow) lbm_sc_batch();
+    if (!b) return LBM_ERR_OUT_OF_MEMORY;
+    b->h.assign(handles, handles + n);
+    b->lattice = handles[0]->params.lattice;
+    b->precision = handles[0]->params.precision;
+    b->tile = tile;
+    b->zchunk = zchunk;
+    b->graph_steps = graph_steps;
+    b->parity = 0;
+    b->sm_count = handles[0]->plan.sm_count;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->graph[0] = b->graph[1] = nullptr;
+    const size_t lb = lbmsc::batch_lattice_bytes(b->precision, tile);
+    std::vector<unsigned char> lats(lb * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        b->cur0.push_back(handles[k]->cur);
+        if (lbmsc::batch_lattice_fill(handles[k]->plan, handles[k]->buf[0], handles[k]->buf[1], handles[k]->cur,
+                                      batch_zchunk(handles[k], zchunk), tile, lats.data() + lb * k) != cudaSuccess) {
+            delete b;
+            return LBM_ERR_INVALID_ARG;
+        }
+    }
+    const std::vector<lbmsc::BatchItem> items = batch_items(handles, n, tile, zchunk);
+    b->nitems = (int)items.size();
+    char* ws = static_cast<char*>(d_workspace);
+    b->d_lats = ws;
+    b->d_items = reinterpret_cast<lbmsc::BatchItem*>(ws + align_up(lb * (size_t)n));
+    cudaError_t e = cudaMemcpyAsync(b->d_lats, lats.data(), lats.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(lbmsc::BatchItem),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host staging goes out of scope
+    // kernel attributes and occupancy are set up now, outside any later stream capture
+    if (e == cudaSuccess) e = lbmsc::batch_step(b->lattice, b->precision, tile, b->d_lats, b->d_items, 0, 0, b->sm_count,
+                                                b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return LBM_ERR_CUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_batch_step(lbm_sc_batch* b, int nsteps) {
+    if (!b || nsteps < 0) return LBM_ERR_INVALID_ARG;
+    for (size_t k = 0; k < b->h.size(); ++k)
+        if (b->h[k]->cur != (b->cur0[k] ^ b->parity)) return LBM_ERR_INVALID_ARG;  // stepped outside the batch
+    int left = nsteps;
+    if (b->graph_steps > 0 && b->stream != nullptr) {
+        while (left >= b->graph_steps) {
+            const int p = b->parity;
+            if (!b->graph[p]) {
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return LBM_ERR_CUDA;
+                const cudaError_t le = batch_launch_steps(b, b->graph_steps);
+                const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+                b->parity = p;  // capturing did not advance the lattices
+                if (le != cudaSuccess || ce != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    return LBM_ERR_CUDA;
+                }
+                const cudaError_t ie = cudaGraphInstantiate(&b->graph[p], g, 0);
+                cudaGraphDestroy(g);
+                if (ie != cudaSuccess) {
+                    b->graph[p] = nullptr;
+                    return LBM_ERR_CUDA;
+                }
+            }
+            if (cudaGraphLaunch(b->graph[p], b->stream) != cudaSuccess) return LBM_ERR_CUDA;
+            // graph_steps is even: the parity is back where it started
+            left -= b->graph_steps;
+        }
+    }
+    if (batch_launch_steps(b, left) != cudaSuccess) return LBM_ERR_CUDA;
+    for (size_t k = 0; k < b->h.size(); ++k) b->h[k]->cur = b->cur0[k] ^ b->parity;
+    return LBM_OK;
+}
+
+void lbm_sc_batch_destroy(lbm_sc_batch* b) {
+    if (!b) return;
+    for (int p = 0; p < 2; ++p)
+        if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+    delete b;
 }
 
 }  // extern "C"

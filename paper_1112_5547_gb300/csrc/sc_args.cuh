@@ -1,0 +1,72 @@
+// Kernel arguments of one lattice from its host-side plan.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include "sc_common.cuh"
+#include "sc_launch.cuh"
+
+namespace lbmsc {
+
+template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void* fout) {
+    using C = typename Codec<S>::C;
+    LatticeArgs<S> a;
+    a.fin = static_cast<const S*>(fin);
+    a.fout = static_cast<S*>(fout);
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.nz = p.nz;
+    a.zchunk = p.zchunk;
+    a.N = p.N;
+    a.px = p.px;
+    a.py = p.py;
+    a.gxo = p.gxo;
+    a.gyo = p.gyo;
+    a.Np = p.Np;
+    a.omega_A = (C)(1.0 / p.tau_A);
+    a.omega_B = (C)(1.0 / p.tau_B);
+    a.tau_A = (C)p.tau_A;
+    a.tau_B = (C)p.tau_B;
+    a.G = (C)p.G;
+    a.ref_A = Codec<S>::kOffset ? (C)p.ref_A : (C)0;
+    a.ref_B = Codec<S>::kOffset ? (C)p.ref_B : (C)0;
+    return a;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// Tensor map of one FP32 population buffer as a 4-D array: x and y of the
+// ghost-padded plane, z, and the plane index s*Q + i; boxes of bx x by x 1 x 1
+// values.  The box x start of a tile at x0 is x0 + gxo - 4, so gxo must be a
+// multiple of 4 values and the row pitch of 16 bytes for it to be 16-byte
+// aligned, as tensor copies require.
+inline cudaError_t encode_population_map(const Plan& p, const float* fin, int bx, int by, CUtensorMap* map) {
+    if (p.gxo < 4 || p.gxo % 4 != 0 || (p.px * 4) % 16 != 0 || (bx * 4) % 16 != 0) return cudaErrorInvalidValue;
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const int q2 = 2 * (p.lattice == 0 ? 9 : 19);
+    const cuuint64_t dims[4] = {(cuuint64_t)p.px, (cuuint64_t)p.py, (cuuint64_t)p.nz, (cuuint64_t)q2};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.px * 4, (cuuint64_t)p.px * p.py * 4, (cuuint64_t)p.Np * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(fin), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+}  // namespace lbmsc

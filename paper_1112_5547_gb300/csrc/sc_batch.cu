@@ -1,0 +1,137 @@
+// Host launchers of the ragged-batch step (sc_batch.cuh).
+#include <cstring>
+#include <type_traits>
+
+#include "sc_batch.cuh"
+#include "sc_batch_launch.h"
+#include "sc_args.cuh"
+
+namespace lbmsc {
+
+namespace {
+
+template <class L, class S, int TX, int TY>
+cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
+                         cudaStream_t st) {
+    using C = typename Codec<S>::C;
+    constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : 2);
+    auto kern = sc_batch_step_kernel<L, S, TX, TY, kMin>;
+    static int per_sm = -1;  // resident CTAs per SM, asked once per instantiation
+    if (per_sm < 0) {
+        int n = 0;
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0);
+        if (e != cudaSuccess) return e;
+        per_sm = n;
+    }
+    long long grid = (long long)sm_count * (per_sm > 0 ? per_sm : 1);
+    if (grid > nitems) grid = nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, dim3(TX, TY), 0, st>>>(static_cast<const BatchLattice<S>*>(lats), items, nitems, parity);
+    return cudaGetLastError();
+}
+
+template <int TX, int TY, int ST>
+cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
+                             cudaStream_t st) {
+    using T = TmaTile<TX, TY, ST>;
+    auto kern = sc_batch_tma_kernel<TX, TY, ST>;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+    if (attr != cudaSuccess) return attr;
+    long long grid = sm_count;  // one CTA per SM (the stages take most of shared memory)
+    if (grid > nitems) grid = nitems;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, dim3(TX, TY), T::smem_bytes, st>>>(static_cast<const BatchTmaLattice*>(lats), items,
+                                                              nitems, parity);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
+                        cudaStream_t st) {
+    switch (tile) {
+        case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, st);
+        case 1: return launch_batch<L, S, 32, 4>(lats, items, nitems, parity, sm_count, st);
+        case 2: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, st);
+    }
+    if constexpr (std::is_same<L, D3Q19>::value && std::is_same<S, float>::value) {
+        switch (tile) {
+            case 3: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, st);
+            case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, st);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class L>
+cudaError_t batch_lat(int precision, int tile, const void* lats, const BatchItem* items, int nitems, int parity,
+                      int sm_count, cudaStream_t st) {
+    switch (precision) {
+        case 0: return batch_typed<L, double>(tile, lats, items, nitems, parity, sm_count, st);
+        case 1: return batch_typed<L, float>(tile, lats, items, nitems, parity, sm_count, st);
+        case 2: return batch_typed<L, __nv_bfloat16>(tile, lats, items, nitems, parity, sm_count, st);
+        case 3: return batch_typed<L, __half>(tile, lats, items, nitems, parity, sm_count, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S> void fill_typed(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, void* dst) {
+    BatchLattice<S> bl;
+    const void* bufs[2] = {b0, b1};
+    for (int par = 0; par < 2; ++par) {
+        const int src = cur0 ^ par;
+        bl.a[par] = make_args<S>(p, bufs[src], const_cast<void*>(bufs[src ^ 1]));
+        bl.a[par].zchunk = zchunk;
+    }
+    memcpy(dst, &bl, sizeof(bl));
+}
+
+}  // namespace
+
+size_t batch_lattice_bytes(int precision, int tile) {
+    if (tile >= 0 && tile < kNumBatchTiles && kBatchTileTma[tile]) return sizeof(BatchTmaLattice);
+    switch (precision) {
+        case 0: return sizeof(BatchLattice<double>);
+        case 1: return sizeof(BatchLattice<float>);
+        case 2: return sizeof(BatchLattice<__nv_bfloat16>);
+        case 3: return sizeof(BatchLattice<__half>);
+    }
+    return 0;
+}
+
+cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, int tile,
+                               void* dst) {
+    if (!batch_tile_fits(tile, p)) return cudaErrorInvalidValue;
+    if (kBatchTileTma[tile]) {
+        BatchTmaLattice bl;
+        memset(&bl, 0, sizeof(bl));
+        const void* bufs[2] = {b0, b1};
+        for (int par = 0; par < 2; ++par) {
+            const int src = cur0 ^ par;
+            bl.a[par] = make_args<float>(p, bufs[src], const_cast<void*>(bufs[src ^ 1]));
+            bl.a[par].zchunk = zchunk;
+            const cudaError_t e = encode_population_map(p, static_cast<const float*>(bufs[src]), kBatchTileX[tile] + 8,
+                                                        kBatchTileY[tile] + 2, &bl.map[par]);
+            if (e != cudaSuccess) return e;
+        }
+        bl.err = p.err;
+        memcpy(dst, &bl, sizeof(bl));
+        return cudaSuccess;
+    }
+    switch (p.precision) {
+        case 0: fill_typed<double>(p, b0, b1, cur0, zchunk, dst); break;
+        case 1: fill_typed<float>(p, b0, b1, cur0, zchunk, dst); break;
+        case 2: fill_typed<__nv_bfloat16>(p, b0, b1, cur0, zchunk, dst); break;
+        case 3: fill_typed<__half>(p, b0, b1, cur0, zchunk, dst); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t batch_step(int lattice, int precision, int tile, const void* lats, const BatchItem* items, int nitems,
+                       int parity, int sm_count, cudaStream_t st) {
+    return lattice == 0 ? batch_lat<D2Q9>(precision, tile, lats, items, nitems, parity, sm_count, st)
+                        : batch_lat<D3Q19>(precision, tile, lats, items, nitems, parity, sm_count, st);
+}
+
+}  // namespace lbmsc

@@ -1,0 +1,140 @@
+// Ragged batch: one launch advances many independent lattices by one step.
+//
+// The host builds a work list of items (lattice, x tile, y tile, z chunk) for
+// every lattice of the batch, longest items first; persistent CTAs walk it with
+// a grid stride.  Each item runs the z-marching step of sc_fused_kernel on its
+// own lattice's arguments (read from a device descriptor array holding both
+// ping-pong parities), so every lattice gets exactly the arithmetic of a solo
+// step: batched and solo results are bit-identical.
+#pragma once
+
+#include "sc_batch_launch.h"
+#include "sc_kernels.cuh"
+#include "sc_tma.cuh"
+
+namespace lbmsc {
+
+// Both parities of one lattice: a[p] reads buffer cur0 ^ p and writes the other.
+template <class S> struct BatchLattice {
+    LatticeArgs<S> a[2];
+};
+
+template <class L, class S, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    sc_batch_step_kernel(const BatchLattice<S>* __restrict__ lats,
+                         const BatchItem* __restrict__ items, int nitems, int parity) {
+    using C = typename Codec<S>::C;
+    constexpr int Q = L::Q;
+    constexpr int FX = TX + 2, FY = TY + 2;
+    constexpr int NPL = L::D == 3 ? 3 : 1;
+    constexpr int H = 2 * FX + 2 * TY;
+    static_assert(H <= TX * TY, "halo ring must fit in the CTA");
+    __shared__ C srho[NPL][2][FY][FX];
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const bool halo = tid < H;
+    int hfx, hfy;
+    halo_cell<TX, TY>(tid, hfx, hfy);
+
+#pragma unroll 1
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const LatticeArgs<S> a = lats[w.lat].a[parity];
+        const int nx = a.nx, ny = a.ny, nz = a.nz;
+        const int x0 = w.x0, y0 = w.y0;
+        const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
+        const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+        const int hgx = (x0 - 1 + hfx + nx) % nx;
+        const int hgy = (y0 - 1 + hfy + ny) % ny;
+
+        auto density_plane = [&](int slot, int z, C (&f)[2][Q]) {
+            pull_node<L, S>(a, gx, gy, z, f);
+            srho[slot][0][ty + 1][tx + 1] = node_density<L, C>(f[0]);
+            srho[slot][1][ty + 1][tx + 1] = node_density<L, C>(f[1]);
+            if (halo) {
+                C h[2][Q];
+                pull_node<L, S>(a, hgx, hgy, z, h);
+                srho[slot][0][hfy][hfx] = node_density<L, C>(h[0]);
+                srho[slot][1][hfy][hfx] = node_density<L, C>(h[1]);
+            }
+        };
+        auto process = [&](C (&f)[2][Q], int sm, int sc, int sp, int z) {
+            const C rA = srho[sc][0][ty + 1][tx + 1];
+            const C rB = srho[sc][1][ty + 1][tx + 1];
+            auto nbr = [&](int s, int i) -> C {
+                const int slot = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
+                return srho[slot][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
+            };
+            C gA[3], gB[3];
+            node_force<L, C>(nbr, a.G, gA, gB);
+            node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            if (owner) store_node<L, S>(a, gx, gy, z, f);
+        };
+
+        C cur[2][Q];
+        if (L::D == 2) {
+            density_plane(0, 0, cur);
+            __syncthreads();
+            process(cur, 0, 0, 0, 0);
+        } else {
+            const int z0 = w.z0;
+            const int z1 = min(z0 + a.zchunk, nz);
+            {
+                C tmp[2][Q];
+                density_plane(0, z0 == 0 ? nz - 1 : z0 - 1, tmp);
+            }
+            density_plane(1, z0, cur);
+            int sm = 0, sc = 1, sp = 2;
+#pragma unroll 1
+            for (int z = z0; z < z1; ++z) {
+                C nxt[2][Q];
+                density_plane(sp, z + 1 == nz ? 0 : z + 1, nxt);
+                __syncthreads();
+                process(cur, sm, sc, sp, z);
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) cur[s][i] = nxt[s][i];
+                const int t = sm;
+                sm = sc;
+                sc = sp;
+                sp = t;
+                __syncthreads();
+            }
+        }
+        __syncthreads();  // the next item rewrites the density ring
+    }
+}
+
+// Both parities of one FP32 D3Q19 lattice for the TMA-fed batch kernel: the
+// tensor map of the buffer each parity reads, its arguments, and the lattice's
+// error word (raised if a bounded wait expires on one of its items).
+struct alignas(64) BatchTmaLattice {
+    CUtensorMap map[2];
+    LatticeArgs<float> a[2];
+    int* err;
+};
+
+// TMA-fed batch step: persistent CTAs run tma_item (sc_tma.cuh) over the work
+// list, so each item gets the arithmetic and order of the solo TMA kernel.
+template <int TX, int TY, int S>
+__global__ void __launch_bounds__(TX* TY, 1)
+    sc_batch_tma_kernel(const BatchTmaLattice* __restrict__ lats, const BatchItem* __restrict__ items, int nitems,
+                        int parity) {
+    extern __shared__ unsigned char smem_raw[];
+    TmaSmem<TX, TY, S> sm(smem_raw);
+    sm.init_barriers();
+    unsigned qbase = 0;
+#pragma unroll 1
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        const BatchTmaLattice* l = lats + w.lat;
+        const LatticeArgs<float> a = l->a[parity];
+        const int n = tma_item<TX, TY, S>(&l->map[parity], a, w.x0, w.y0, w.z0, qbase, sm, l->err);
+        if (n < 0) return;
+        qbase += (unsigned)n;
+        __syncthreads();  // the next item rewrites the stages and the density ring
+    }
+}
+
+}  // namespace lbmsc

@@ -1,0 +1,38 @@
+// Declarations shared by the batch launcher TU and the C-ABI TU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "sc_launch.cuh"
+
+namespace lbmsc {
+
+// One work item of a batch: lattice index, tile origin, first plane of the z chunk.
+struct BatchItem {
+    int lat, x0, y0, z0;
+};
+
+// Batch tiles (x by y columns per CTA): 0 = 32x8, 1 = 32x4, 2 = 64x4 (z-marching
+// kernel, every lattice and precision); 3 = 32x8, 4 = 64x4 (TMA-fed kernel with
+// 3 stages, D3Q19 with FP32 storage, lattices at least one tile wide in x and y).
+constexpr int kNumBatchTiles = 5;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4};
+constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true};
+
+inline bool batch_tile_fits(int tile, const Plan& p) {
+    if (tile < 0 || tile >= kNumBatchTiles) return false;
+    if (!kBatchTileTma[tile]) return true;
+    return p.lattice == 1 && p.precision == 1 && p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];
+}
+
+// Bytes of one lattice's descriptor, and the descriptor itself (both parities;
+// parity p reads buffer cur0 ^ p).  err: the lattice's device error word.
+size_t batch_lattice_bytes(int precision, int tile);
+cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, int tile,
+                               void* dst);
+cudaError_t batch_step(int lattice, int precision, int tile, const void* lats, const BatchItem* items, int nitems,
+                       int parity, int sm_count, cudaStream_t st);
+
+}  // namespace lbmsc

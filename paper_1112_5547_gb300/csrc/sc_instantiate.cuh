@@ -1,41 +1,15 @@
 // Typed launch helpers shared by the per-lattice translation units.
 #pragma once
 
-#include <cudaTypedefs.h>
-
 #include "sc_async.cuh"
 #include "sc_tma.cuh"
 #include "sc_kernels.cuh"
 #include "sc_pipe.cuh"
 #include "sc_regpipe.cuh"
 #include "sc_launch.cuh"
+#include "sc_args.cuh"
 
 namespace lbmsc {
-
-template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void* fout) {
-    using C = typename Codec<S>::C;
-    LatticeArgs<S> a;
-    a.fin = static_cast<const S*>(fin);
-    a.fout = static_cast<S*>(fout);
-    a.nx = p.nx;
-    a.ny = p.ny;
-    a.nz = p.nz;
-    a.zchunk = p.zchunk;
-    a.N = p.N;
-    a.px = p.px;
-    a.py = p.py;
-    a.gxo = p.gxo;
-    a.gyo = p.gyo;
-    a.Np = p.Np;
-    a.omega_A = (C)(1.0 / p.tau_A);
-    a.omega_B = (C)(1.0 / p.tau_B);
-    a.tau_A = (C)p.tau_A;
-    a.tau_B = (C)p.tau_B;
-    a.G = (C)p.G;
-    a.ref_A = Codec<S>::kOffset ? (C)p.ref_A : (C)0;
-    a.ref_B = Codec<S>::kOffset ? (C)p.ref_B : (C)0;
-    return a;
-}
 
 template <class L, class S, int TX, int TY>
 cudaError_t step_tiled(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
@@ -75,21 +49,6 @@ cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library).
-inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
-    return fn;
-}
-
 template <class L, class S, int TX, int TY, int ST> struct TmaLaunch {
     static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
 };
@@ -97,21 +56,10 @@ template <int TX, int TY, int ST> struct TmaLaunch<D3Q19, float, TX, TY, ST> {
     static cudaError_t run(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
         const TileShape& ts = kTiles[p.step_tile];
         using T = TmaTile<TX, TY, ST>;
-        // box x start (x0 + gxo - 4) must be 16-byte aligned for every 32-node tile
-        if (p.gxo < 4 || p.gxo % 4 != 0 || (p.px * 4) % 16 != 0 || p.nx < TX || p.ny < TY)
-            return cudaErrorInvalidValue;
-        auto enc = tensor_map_encoder();
-        if (!enc) return cudaErrorNotSupported;
-        // 4-D view of one population buffer: x, y (ghost-padded), z, plane (s*Q + i)
+        if (p.nx < TX || p.ny < TY) return cudaErrorInvalidValue;
         CUtensorMap map;
-        const cuuint64_t dims[4] = {(cuuint64_t)p.px, (cuuint64_t)p.py, (cuuint64_t)p.nz, (cuuint64_t)T::Q2};
-        const cuuint64_t strides[3] = {(cuuint64_t)p.px * 4, (cuuint64_t)p.px * p.py * 4, (cuuint64_t)p.Np * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)T::BX, (cuuint32_t)T::BY, 1, 1};
-        const cuuint32_t es[4] = {1, 1, 1, 1};
-        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(a.fin), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
+        const cudaError_t me = encode_population_map(p, a.fin, T::BX, T::BY, &map);
+        if (me != cudaSuccess) return me;
         auto kern = sc_step_tma_kernel<TX, TY, ST>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
         if (e != cudaSuccess) return e;

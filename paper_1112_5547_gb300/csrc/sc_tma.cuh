@@ -18,8 +18,10 @@
 // registers and write own and halo densities to the four-slot ring;
 // one barrier (ring complete, stage q free); the elected thread refills the
 // stage with plane q + S; collide plane q - 1 from registers and store.
-// Every mbarrier wait is bounded: on expiry the CTA raises the error word and
-// leaves (the host reports LBM_ERR_TIMEOUT).
+// Every mbarrier wait is bounded: on expiry the CTA raises the error word,
+// waits (bounded) for its copies still in flight and leaves (the host reports
+// LBM_ERR_TIMEOUT).  tma_item is the per-item pipeline; the solo kernel runs
+// one item per CTA, the batch kernel (sc_batch.cuh) a work list of them.
 #pragma once
 
 #include <cuda.h>
@@ -73,27 +75,52 @@ template <int TX, int TY, int S> struct TmaTile {
     static constexpr size_t smem_bytes = 128 + (size_t)S * stage_bytes + ring_bytes + (size_t)S * 8;
 };
 
+// Shared memory of one CTA: S stages of 38 boxes, the density ring, S mbarriers.
+template <int TX, int TY, int S> struct TmaSmem {
+    using T = TmaTile<TX, TY, S>;
+    float* stage;
+    float (*ring)[2][T::FY][T::FX];
+    uint64_t* bars;
+
+    __device__ __forceinline__ explicit TmaSmem(unsigned char* raw) {
+        unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
+        stage = reinterpret_cast<float*>(base);
+        ring = reinterpret_cast<float(*)[2][T::FY][T::FX]>(base + (size_t)S * T::stage_bytes);
+        bars = reinterpret_cast<uint64_t*>(base + (size_t)S * T::stage_bytes + T::ring_bytes);
+    }
+    __device__ __forceinline__ void init_barriers() {
+        if (threadIdx.x + threadIdx.y * blockDim.x == 0) {
+#pragma unroll
+            for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+};
+
+// One work item through the plane pipeline: the TX x TY tile at (x0, y0),
+// planes z0 .. min(z0 + zchunk, nz) - 1.  qbase counts the planes this CTA
+// pushed through its stages before (the mbarrier phases continue from there).
+// Every thread returns the number of planes the item used, or -1 if a wait
+// was lost (the error word is then raised, and the copies still in flight
+// have been waited for, again with a bound).  The caller must synchronise the
+// CTA between two items.
 template <int TX, int TY, int S>
-__global__ void __launch_bounds__(TX* TY, 1)
-    sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const LatticeArgs<float> a, int* __restrict__ err) {
+__device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeArgs<float>& a, int x0, int y0, int z0,
+                                        unsigned qbase, const TmaSmem<TX, TY, S>& sm, int* __restrict__ err) {
     using L = D3Q19;
     using T = TmaTile<TX, TY, S>;
     using C = float;
-    constexpr int Q = L::Q, Q2 = T::Q2, BX = T::BX, FX = T::FX, FY = T::FY, H = T::H;
+    constexpr int Q = L::Q, Q2 = T::Q2, BX = T::BX, FX = T::FX, H = T::H;
     constexpr unsigned BS = T::box_stride / 4;  // floats between boxes
     static_assert(H <= TX * TY, "halo ring must fit in the CTA");
     static_assert(BX * 4 % 16 == 0, "TMA box rows are whole 16-byte units");
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-    C* const stage = reinterpret_cast<C*>(base);
-    C(*const ring)[2][FY][FX] = reinterpret_cast<C(*)[2][FY][FX]>(base + (size_t)S * T::stage_bytes);
-    uint64_t* const bars = reinterpret_cast<uint64_t*>(base + (size_t)S * T::stage_bytes + T::ring_bytes);
-
+    C* const stage = sm.stage;
+    auto ring = sm.ring;
+    uint64_t* const bars = sm.bars;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, nz);
     const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
     const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
@@ -106,10 +133,10 @@ __global__ void __launch_bounds__(TX* TY, 1)
         const int z = z0 - 1 + q;
         return z < 0 ? z + nz : (z >= nz ? z - nz : z);
     };
-    // elected thread: the 38 boxes of plane q into stage q % S
+    // elected thread: the 38 boxes of plane q into its stage
     auto issue = [&](int q) {
         const int z = zof(q);
-        const int st = q % S;
+        const unsigned st = (qbase + q) % S;
         mbar_arrive_expect_tx(&bars[st], Q2 * T::box_bytes);
         C* sb = stage + (size_t)st * (T::stage_bytes / 4);
 #pragma unroll
@@ -120,35 +147,27 @@ __global__ void __launch_bounds__(TX* TY, 1)
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const int j = s * Q + i;
-                tma_load_4d(sb + (size_t)j * BS, &tmap, &bars[st], x0 + a.gxo - 4, cy, zs, j);
+                tma_load_4d(sb + (size_t)j * BS, tmap, &bars[st], x0 + a.gxo - 4, cy, zs, j);
             }
         }
+    };
+    auto try_plane = [&](int q) {
+        const unsigned g = qbase + q;
+        int n = 0;
+        while (!mbar_try_wait(&bars[g % S], (g / S) & 1))
+            if (++n >= kMbarSpinLimit) return false;
+        return true;
     };
 
     if (tid == 0) {
-#pragma unroll
-        for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0)
+        fence_proxy_async_smem();  // earlier generic reads of the stages precede the refill
         for (int q = 0; q < S && q < nplanes; ++q) issue(q);
+    }
 
     bool lost = false;
-    auto wait_plane = [&](int q) {
-        const int st = q % S;
-        const unsigned parity = (unsigned)((q / S) & 1);
-        int n = 0;
-        while (!mbar_try_wait(&bars[st], parity)) {
-            if (++n >= kMbarSpinLimit) {
-                lost = true;
-                break;
-            }
-        }
-    };
     // own pulls of plane q into X; own and halo densities into ring slot q % 4
     auto take_plane = [&](int q, C (&X)[2][Q]) {
-        const C* sb = stage + (size_t)(q % S) * (T::stage_bytes / 4);
+        const C* sb = stage + (size_t)((qbase + q) % S) * (T::stage_bytes / 4);
 #pragma unroll
         for (int i = 0; i < Q; ++i)
 #pragma unroll
@@ -166,11 +185,11 @@ __global__ void __launch_bounds__(TX* TY, 1)
         }
     };
     auto collide = [&](int q, C (&X)[2][Q]) {
-        const int sm = (q - 1) & 3, sc = q & 3, sp = (q + 1) & 3;
+        const int sm_ = (q - 1) & 3, sc = q & 3, sp = (q + 1) & 3;
         const C rA = ring[sc][0][ty + 1][tx + 1];
         const C rB = ring[sc][1][ty + 1][tx + 1];
         auto nbr = [&](int s, int i) -> C {
-            const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
+            const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm_);
             return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
         };
         C gA[3], gB[3];
@@ -178,29 +197,44 @@ __global__ void __launch_bounds__(TX* TY, 1)
         node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         if (owner) store_node<L, float>(a, gx, gy, zof(q), X);
     };
-    // plane q arrives; plane q - 1 collides.  false when the chunk is done or a wait was lost.
-    auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> bool {
-        if (q >= nplanes) return false;
-        wait_plane(q);
+    // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
+    auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> int {
+        if (q >= nplanes) return 1;
+        if (!try_plane(q)) lost = true;
         take_plane(q, Xc);
         if (__syncthreads_or(lost)) {
-            if (tid == 0) atomicExch(err, 1);
-            return false;
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // drain: wait (bounded) for the planes issued from q on
+                for (int r = q; r < nplanes && r < q + S; ++r) try_plane(r);
+            }
+            return -1;
         }
         if (tid == 0 && q + S < nplanes) {
             fence_proxy_async_smem();  // the stage's generic reads precede the async refill
             issue(q + S);
         }
         if (q >= 2) collide(q - 1, Xp);
-        return true;
+        return 0;
     };
 
     C R0[2][Q], R1[2][Q];
+    int r = 0;
 #pragma unroll 1
     for (int q = 0;; q += 2) {
-        if (!body(q, R0, R1)) break;
-        if (!body(q + 1, R1, R0)) break;
+        if ((r = body(q, R0, R1)) != 0) break;
+        if ((r = body(q + 1, R1, R0)) != 0) break;
     }
+    return r < 0 ? -1 : nplanes;
+}
+
+template <int TX, int TY, int S>
+__global__ void __launch_bounds__(TX* TY, 1)
+    sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const LatticeArgs<float> a, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    TmaSmem<TX, TY, S> sm(smem_raw);
+    sm.init_barriers();
+    tma_item<TX, TY, S>(&tmap, a, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * a.zchunk, 0u, sm, err);
 }
 
 }  // namespace lbmsc

@@ -117,3 +117,34 @@ def uniform_velocity(shape, U):
     for a, v in enumerate(U):
         u[..., a] = v
     return u
+
+
+RHO_TOT = 1.04  # rho_hi + rho_lo of the drop recipe
+
+
+def ragged_drop_specs(n=64, sizes=(32, 48, 64, 96, 128), dim=3, seed=0):
+    """Specifications of a ragged batch of independent drop lattices.
+
+    Per lattice, drawn from one numpy PCG64 stream: the edge L uniformly from
+    ``sizes`` (a cube, or a square for dim=2), G rho_tot uniformly in
+    [2.2, 2.8], tau_A and tau_B uniformly in [0.6, 1.5], a drop radius
+    uniformly in [L/8, L/3] at a uniformly random centre, and the noise seed.
+    Returns dicts with keys shape, G, tau_A, tau_B, R, centre, seed.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    specs = []
+    for k in range(n):
+        L = int(sizes[int(rng.integers(len(sizes)))])
+        g_rho = float(rng.uniform(2.2, 2.8))
+        tau_A = float(rng.uniform(0.6, 1.5))
+        tau_B = float(rng.uniform(0.6, 1.5))
+        R = float(rng.uniform(L / 8.0, L / 3.0))
+        centre = tuple(float(c) for c in rng.uniform(0.0, L, size=dim))
+        specs.append(dict(shape=(L,) * dim, G=g_rho / RHO_TOT, tau_A=tau_A, tau_B=tau_B, R=R, centre=centre,
+                          seed=int(seed) * 1000003 + k))
+    return specs
+
+
+def spec_fields(spec, dtype=np.float64):
+    """Initial (rho_A, rho_B) of one ragged_drop_specs entry."""
+    return drop(spec["shape"], spec["R"], centre=spec["centre"], seed=spec["seed"], dtype=dtype)

@@ -41,8 +41,25 @@ EXPORTS = (
     "lbm_sc_workspace_bytes", "lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step",
     "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
     "lbm_sc_destroy", "lbm_sc_status_string", "lbm_sc_set_tuning", "lbm_sc_get_tuning",
-    "lbm_sc_diagnostics_noalloc",
+    "lbm_sc_diagnostics_noalloc", "lbm_sc_batch_workspace_bytes", "lbm_sc_batch_create", "lbm_sc_batch_step",
+    "lbm_sc_batch_destroy",
 )
+
+# CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
+# take D3Q19 lattices with FP32 storage at least one tile wide in x and y.
+BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4))
+BATCH_TILE_TMA = (False, False, False, True, True)
+
+
+def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
+    """Mirror of the library's rule for one lattice of a batch."""
+    if not 0 <= tile < len(BATCH_TILES):
+        return False
+    if not BATCH_TILE_TMA[tile]:
+        return True
+    tx, ty = BATCH_TILES[tile]
+    p = lattice.params
+    return p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.nx >= tx and p.ny >= ty
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
 # the shared-memory stages of the persistent cp.async kernel (0: register kernel).
@@ -141,13 +158,21 @@ def load(path: str = LIB_PATH):
     lib.lbm_sc_diagnostics_noalloc.restype = ctypes.c_int
     lib.lbm_sc_destroy.argtypes = [vp]
     lib.lbm_sc_destroy.restype = None
+    HP = ctypes.POINTER(vp)
+    lib.lbm_sc_batch_workspace_bytes.argtypes = [HP, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.lbm_sc_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.lbm_sc_batch_create.argtypes = [HP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                        ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    lib.lbm_sc_batch_step.argtypes = [vp, ctypes.c_int]
+    lib.lbm_sc_batch_destroy.argtypes = [vp]
+    lib.lbm_sc_batch_destroy.restype = None
     lib.lbm_sc_status_string.argtypes = [ctypes.c_int]
     lib.lbm_sc_status_string.restype = ctypes.c_char_p
     for name in EXPORTS:
         getattr(lib, name)
     for name in ("lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step", "lbm_sc_moments",
                  "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout", "lbm_sc_set_tuning",
-                 "lbm_sc_get_tuning"):
+                 "lbm_sc_get_tuning", "lbm_sc_batch_create", "lbm_sc_batch_step"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -254,6 +279,33 @@ def lbm_sc_get_tuning(h: int):
 
 def lbm_sc_destroy(h: int) -> None:
     load().lbm_sc_destroy(ctypes.c_void_p(h))
+
+
+def _handle_array(handles):
+    return (ctypes.c_void_p * len(handles))(*[ctypes.c_void_p(h) for h in handles])
+
+
+def lbm_sc_batch_workspace_bytes(handles, tile: int = 0, zchunk: int = 0) -> int:
+    arr = _handle_array(handles)
+    return int(load().lbm_sc_batch_workspace_bytes(arr, len(handles), int(tile), int(zchunk)))
+
+
+def lbm_sc_batch_create(handles, tile: int, zchunk: int, graph_steps: int, d_workspace: int, workspace_bytes: int,
+                        stream: int = 0) -> int:
+    arr = _handle_array(handles)
+    b = ctypes.c_void_p()
+    _check(load().lbm_sc_batch_create(arr, len(handles), int(tile), int(zchunk), int(graph_steps),
+                                      ctypes.c_void_p(d_workspace), ctypes.c_size_t(workspace_bytes),
+                                      ctypes.c_void_p(stream), ctypes.byref(b)), "lbm_sc_batch_create")
+    return b.value
+
+
+def lbm_sc_batch_step(b: int, nsteps: int) -> None:
+    _check(load().lbm_sc_batch_step(ctypes.c_void_p(b), int(nsteps)), "lbm_sc_batch_step")
+
+
+def lbm_sc_batch_destroy(b: int) -> None:
+    load().lbm_sc_batch_destroy(ctypes.c_void_p(b))
 
 
 def lbm_sc_status_string(status: int) -> str:
@@ -379,3 +431,42 @@ class Lattice:
         off = ptr - base
         n = 2 * q * nz * py * px
         return self.workspace[off: off + n * eb].view(dt).view(2, q, nz, py, px)
+
+
+class Batch:
+    """Lattices (``Lattice`` objects of one lattice kind and precision) advanced
+    together by one launch per step; the batch workspace is a torch uint8 tensor.
+    The lattices must stay alive as long as the batch, and be stepped only
+    through it while it exists."""
+
+    def __init__(self, lattices, tile: int = 0, zchunk: int = 0, graph_steps: int = 0, stream=None):
+        import torch
+
+        if not lattices:
+            raise ValueError("a batch needs at least one lattice")
+        self.lattices = list(lattices)
+        dev = self.lattices[0].device
+        self.stream = stream if stream is not None else self.lattices[0].stream
+        hs = [lat.handle for lat in self.lattices]
+        nbytes = lbm_sc_batch_workspace_bytes(hs, tile, zchunk)
+        if nbytes == 0:
+            raise LbmError(LBM_ERR_INVALID_ARG, "lbm_sc_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        self.handle = lbm_sc_batch_create(hs, tile, zchunk, graph_steps, aligned, nbytes, self.stream.cuda_stream)
+        self.workspace_bytes = nbytes
+
+    def step(self, nsteps: int = 1):
+        lbm_sc_batch_step(self.handle, nsteps)
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lbm_sc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

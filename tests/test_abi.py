@@ -144,3 +144,57 @@ def test_status_strings(lib):
     for s in range(6):
         assert lib.lbm_sc_status_string(s).startswith("LBM_")
     assert "unknown" in lib.lbm_sc_status_string(99)
+
+
+def test_batch_workspace_and_validation(lib):
+    """Batch sizing counts one descriptor per lattice and one 16-byte item per
+    (x tile, y tile, z chunk); mixed lattice kinds or precisions, unknown tiles,
+    odd graph chunks and short or misaligned workspaces are rejected before any
+    device work."""
+    shapes = [(40, 20, 24), (17, 33, 9), (64, 64, 64)]
+    ps = [lib.make_params(lib.LBM_D3Q19, s, 1.0, 0.8, 2.0, "f32") for s in shapes]
+    hs = [lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0) for p in ps]
+    try:
+        for tile, (tx, ty) in enumerate(lib.BATCH_TILES[:3]):
+            for zc in (0, 8, 100):
+                z = 32 if zc == 0 else zc
+                items = sum(-(-nx // tx) * -(-ny // ty) * -(-nz // min(z, nz)) for nz, ny, nx in shapes)
+                ws = lib.lbm_sc_batch_workspace_bytes(hs, tile, zc)
+                assert ws >= items * 16 + len(hs) * 2 * 80
+                assert ws < items * 16 + len(hs) * 2 * 200 + 512
+        assert lib.lbm_sc_batch_workspace_bytes(hs, 5, 0) == 0
+        # TMA-fed tiles need every lattice at least one tile wide (nx = 24 < 32 here)
+        assert lib.lbm_sc_batch_workspace_bytes(hs, 3, 0) == 0
+        assert lib.lbm_sc_batch_workspace_bytes(hs[2:], 3, 0) > 0
+        assert lib.lbm_sc_batch_workspace_bytes(hs[2:], 4, 0) > 0
+        assert lib.lbm_sc_batch_workspace_bytes(hs[1:], 4, 0) == 0  # nx = 9 < 64
+        assert lib.lbm_sc_batch_workspace_bytes(hs, -1, 0) == 0
+        assert lib.lbm_sc_batch_workspace_bytes(hs, 0, -1) == 0
+        assert lib.lbm_sc_batch_workspace_bytes([], 0, 0) == 0
+        p2 = lib.make_params(lib.LBM_D2Q9, (16, 16), 1.0, 1.0, 2.0, "f32")
+        p16 = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.0, "bf16")
+        for other in (p2, p16):
+            h2 = lib.lbm_sc_create(other, 256 * 1024, lib.lbm_sc_workspace_bytes(other), 0)
+            try:
+                assert lib.lbm_sc_batch_workspace_bytes(hs + [h2], 0, 0) == 0
+                with pytest.raises(lib.LbmError):
+                    lib.lbm_sc_batch_create(hs + [h2], 0, 0, 0, 256 * 1024, 1 << 30, 0)
+            finally:
+                lib.lbm_sc_destroy(h2)
+        need = lib.lbm_sc_batch_workspace_bytes(hs, 0, 0)
+        cases = [((0, 0, 3, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),    # odd graph chunk
+                 ((0, 0, -2, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
+                 ((0, 0, 0, 256 * 1024 + 8, need), lib.LBM_ERR_INVALID_ARG),  # misaligned
+                 ((0, 0, 0, 256 * 1024, need - 1), lib.LBM_ERR_OUT_OF_MEMORY),
+                 ((5, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
+                 ((3, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG)]
+        for args, status in cases:
+            with pytest.raises(lib.LbmError) as e:
+                lib.lbm_sc_batch_create(hs, *args, 0)
+            assert e.value.status == status, args
+        with pytest.raises(lib.LbmError):
+            lib.lbm_sc_batch_step(0, 1)
+        lib.lbm_sc_batch_destroy(0)  # a null batch is ignored
+    finally:
+        for h in hs:
+            lib.lbm_sc_destroy(h)
