@@ -31,8 +31,18 @@ sys.path.insert(0, ROOT)
 
 G_RHO = 2.4
 RHO_HI, RHO_LO = 1.0, 0.04
-BYTES_PER_VALUE = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}
-DTYPE_NAME = {"f64": "f64", "f32": "f32", "bf16": "f32 (bf16 storage)", "f16": "f32 (f16 storage)"}
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "bf16": 2, "f16": 2, "bf16_rest": 2, "f16_rest": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "bf16": "f32 (bf16 storage)", "f16": "f32 (f16 storage)",
+              "bf16_rest": "f32 (bf16 rest-offset storage)", "f16_rest": "f32 (f16 rest-offset storage)"}
+
+
+def bytes_per_lu(prec: str, q: int = 19) -> int:
+    """Algorithmic HBM bytes of one lattice update (both species): every population
+    read once and written once, plus the two FP32 densities of the rest-offset storage."""
+    b = 2 * q * 2 * BYTES_PER_VALUE[prec]
+    if prec.endswith("_rest"):
+        b += 2 * 2 * 4
+    return b
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -49,6 +59,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--tile", type=int, default=-1, help="force a step tile (skips the autotuner)")
     ap.add_argument("--zchunk", type=int, default=0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch vs serial comparison")
+    ap.add_argument("--batch-steps", type=int, default=40)
     return ap.parse_args()
 
 
@@ -154,6 +166,64 @@ def cpu_baseline(seconds: float, L: int = 128):
             "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d steps in %.1f s" % (L, n, el)}
 
 
+def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 0):
+    """Ragged batch against one-lattice-at-a-time on the same lattices: n
+    independent D3Q19 FP32 drop lattices, L from {32, 48, 64, 96, 128}, per
+    lattice G rho_tot in [2.2, 2.8], tau_A, tau_B in [0.6, 1.5], R in [L/8, L/3]
+    at a random centre (inputs.ragged_drop_specs).  Serial: every lattice
+    stepped alone with its own autotuned launch shape (tuned once per size),
+    lattice after lattice, `steps` steps each.  Batched: one launch per step for
+    all lattices, launch shape and graph chunk autotuned (tune_batch).  Both
+    timed with CUDA events on one stream; aggregate MLUPS = total nodes x steps
+    / time.  Results are bit-identical between the two (tests/test_gpu_batch.py)."""
+    import torch
+    from paper_1112_5547_gb300 import autotune, inputs, lbm_sc
+
+    st = torch.cuda.Stream()
+    specs = inputs.ragged_drop_specs(n=n, seed=seed)
+    lats = []
+    with torch.cuda.stream(st):
+        for sp in specs:
+            rA, rB = inputs.spec_fields(sp, dtype=np.float32)
+            lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32",
+                                       stream=st).init(rA, rB))
+        st.synchronize()
+        N = sum(lat.N for lat in lats)
+        best = {}
+        for lat in lats:
+            if lat.shape not in best:
+                best[lat.shape] = autotune.autotune(lat)[0]
+            lat.set_tuning(*best[lat.shape])
+
+        def timed(fn, k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn(k)
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1)
+
+        for lat in lats:
+            lat.step(warmup + warmup % 2)
+        ser_ms = timed(lambda k: [lat.step(k) for lat in lats], steps) / steps
+        (tile, zc, gs), table = autotune.tune_batch(lats, stream=st)
+        b = lbm_sc.Batch(lats, tile=tile, zchunk=zc, graph_steps=gs, stream=st)
+        b.step(max(warmup, gs, 2))
+        k = steps if gs == 0 else max(gs, steps // gs * gs)
+        bat_ms = timed(b.step, k) / k
+        b.close()
+    sizes = sorted({lat.shape[0] for lat in lats})
+    out = {"workload": "%d ragged D3Q19 FP32 drop lattices, L in %s, %.1fM nodes, seed %d" % (n, sizes, N / 1e6, seed),
+           "nodes": N, "steps": steps, "batched_mlups": N / bat_ms / 1e3, "serial_mlups": N / ser_ms / 1e3,
+           "batched_ms_per_step": bat_ms, "serial_ms_per_step": ser_ms, "speedup": ser_ms / bat_ms,
+           "batch_launch": {"tile": list(lbm_sc.BATCH_TILES[tile]), "tma": lbm_sc.BATCH_TILE_TMA[tile],
+                            "zchunk": zc, "graph_steps": gs, "candidates": len(table)},
+           "gpu_launches_per_step": {"batched": 1, "serial": n}}
+    del lats
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -250,8 +320,8 @@ def main():
     ms_per_step = total_ms / K
     value = world * N * K / (total_ms / 1e3) / 1e6
     avg_launch_s = statistics.mean(launch_ms) / 1e3
-    bytes_per_lu = 2 * 19 * 2 * BYTES_PER_VALUE[prec]
-    achieved = bytes_per_lu * N / avg_launch_s / 1e9
+    bpl = bytes_per_lu(prec)
+    achieved = bpl * N / avg_launch_s / 1e9
     peak, peak_kind = measured_peak_hbm()
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
@@ -288,7 +358,13 @@ def main():
         e2e = {"value": world * N * K / e2e_s / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": 2 * N * esz / K, "d2h_bytes_per_step": 6 * N * esz / K,
                "note": "one job of %d steps: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p; bytes per step = job bytes / steps" % K}
-        del staging, hA, hB, oA, oB, oP, oU
+        del staging, hA, hB, oA, oB, oP, oU, lat2
+
+    bt = None
+    if not args.no_batch and rank == 0:
+        del lat
+        torch.cuda.empty_cache()
+        bt = batch_compare(args.batch_steps, args.warmup)
 
     if rank != 0:
         if dist is not None:
@@ -313,15 +389,16 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU", "step_launch": tune_info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_lu": bytes_per_lu,
-                     "kernel": "D3Q19 %s step, tile %s kind %d" % (prec, lbm_sc.TILES[lat.tuning()[0]],
-                                                                  lbm_sc.TILE_KIND[lat.tuning()[0]])},
+                     "algorithmic_bytes_per_lu": bpl,
+                     "kernel": "D3Q19 %s step, tile %s kind %d" % (prec, tuple(tune_info["tile"]), tune_info["kind"])},
         "gpu_launches": K,
         "clocks": clk,
         "diag": {"mass_A": d["mass_A"], "max_speed": d["max_speed"], "status": d["status"]},
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if bt is not None:
+        line["batch"] = bt
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -56,14 +56,24 @@ typedef enum {
 
 typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 
-/* Arithmetic is FP64 for LBM_F64 and FP32 otherwise.  The 16-bit precisions
- * store h_is = f_is - w_i rho_ref_s (an offset from the rest equilibrium of
- * a reference density) in bf16 / fp16 and decode to FP32 on load. */
+/* Arithmetic is FP64 for LBM_F64 and FP32 otherwise.  LBM_F32_STORE_BF16 and
+ * LBM_F32_STORE_F16 store h_is = f_is - w_i rho_ref_s (an offset from the rest
+ * equilibrium of a reference density, one per species) in bf16 / fp16 and
+ * decode to FP32 on load.  The _REST variants store h_is(n) = f_is(n) -
+ * w_i rho_s(n), the offset from the rest equilibrium of the density of the
+ * node n the value is stored at, with rho_s(n) itself kept in FP32: 16-bit
+ * populations plus two FP32 density planes per buffer (84 instead of 152 bytes
+ * per D3Q19 node), and an error that no longer grows with |rho_s - rho_ref_s|,
+ * which in a two-phase lattice is large in one of the phases whatever
+ * rho_ref_s is.  The paper computes in double precision throughout; the
+ * 16-bit storage modes are a bandwidth option of this library. */
 typedef enum {
     LBM_F64 = 0,
     LBM_F32 = 1,
     LBM_F32_STORE_BF16 = 2,
-    LBM_F32_STORE_F16 = 3
+    LBM_F32_STORE_F16 = 3,
+    LBM_F32_STORE_BF16_REST = 4,
+    LBM_F32_STORE_F16_REST = 5
 } lbm_precision;
 
 /* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE). */
@@ -109,11 +119,11 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * shared-memory stages, 6 = 32x8 with 4 stages, 7 = 64x4 with 3 stages
  * (persistent cp.async kernel, D3Q19 with LBM_F32 only); 8 = 32x8, 9 = 64x4,
  * 10 = 32x4 (software-pipelined kernel with loads two planes ahead, D3Q19,
- * every precision); 11 = 32x4, 12 = 32x8, 13 = 64x4, 14 = 32x4 (low-register
+ * every precision but the _REST ones); 11 = 32x4, 12 = 32x8, 13 = 64x4, 14 = 32x4 (low-register
  * kernel that pulls a plane a second time for its collision, every lattice and
  * precision; 11 and 14 differ in the register budget); 15 = 32x4, 16 = 32x8,
  * 17 = 16x8 (register-pipelined kernel holding three planes of pulls, D3Q19
- * with 32- or 16-bit storage); 18 = 32x8 with 3 stages, 19 = 64x4 with 3
+ * with 32-bit storage or the reference-offset 16-bit storage); 18 = 32x8 with 3 stages, 19 = 64x4 with 3
  * stages, 20 = 32x4 with 4 stages, 21 = 32x4 with 2 stages, and the cluster
  * launches 22 = 64x4 in clusters of 1x2 tiles, 23 = 64x4 in 1x4, 24 = 64x4 in
  * 2x2, 25 = 32x8 in 2x2 (TMA-fed kernel, D3Q19 with LBM_F32 only, lattices
@@ -180,7 +190,8 @@ LBM_SC_API lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* 
  * this is an interface convenience.
  *   params        the lattice (same rules as lbm_sc_workspace_bytes)
  *   d_populations device pointer to one population buffer in the layout of
- *                 lbm_sc_layout (for example the pointer it returns)
+ *                 lbm_sc_layout (for example the pointer it returns; with
+ *                 its density planes for the _REST precisions)
  *   window        as for lbm_sc_diagnostics, or NULL
  *   d_out         device pointer to one lbm_sc_diag that receives the result
  *   cuda_stream   stream the work is enqueued on; the call does not synchronise
@@ -216,7 +227,9 @@ LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t 
  * of pitch_x * pitch_y * nz values each; node (x, y, z) sits at
  * (x + ghost_x) + pitch_x * ((y + ghost_y) + pitch_y * z).  The columns
  * x = -2, -1, nx, nx + 1 and rows y = -2, -1, ny, ny + 1 hold periodic images;
- * other padding is unused.  Any output pointer may be NULL. */
+ * other padding is unused.  For the _REST precisions the 2 x Q planes are
+ * followed by 2 planes of FP32 densities rho_s (species s at plane s) with the
+ * same pitches, node (x, y, z) at the same index.  Any output pointer may be NULL. */
 LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y,
                                     int* ghost_x, int* ghost_y, const void** d_populations);
 

@@ -43,7 +43,7 @@ def autotune(lattice: "lbm_sc.Lattice", trial_steps: int = 4, warmup_steps: int 
     """
     if (trial_steps + warmup_steps) % 2:
         trial_steps += 1
-    saved = lattice.populations().clone() if restore else None
+    saved = lattice.state().clone() if restore else None
     table = []
     for tile, z in (cands if cands is not None else candidates(lattice)):
         lattice.set_tuning(tile, z)
@@ -53,7 +53,7 @@ def autotune(lattice: "lbm_sc.Lattice", trial_steps: int = 4, warmup_steps: int 
     best = min(table, key=lambda r: r[2])
     lattice.set_tuning(best[0][0], best[1])
     if saved is not None:
-        lattice.populations().copy_(saved)
+        lattice.state().copy_(saved)
         lattice.stream.synchronize()
     return (best[0][0], best[1]), table
 
@@ -86,7 +86,7 @@ def tune_batch(lattices, trial_steps: int = 8, warmup_steps: int = 2, cands=None
     if (trial_steps + warmup_steps) % 2:
         trial_steps += 1
     stream = stream if stream is not None else lattices[0].stream
-    saved = [lat.populations().clone() for lat in lattices] if restore else None
+    saved = [lat.state().clone() for lat in lattices] if restore else None
     table = []
     for tile, z, g in (cands if cands is not None else batch_candidates(lattices)):
         if g and trial_steps % g:
@@ -106,7 +106,7 @@ def tune_batch(lattices, trial_steps: int = 8, warmup_steps: int = 2, cands=None
     best = min(table, key=lambda r: r[1])
     if saved is not None:
         for lat, sv in zip(lattices, saved):
-            lat.populations().copy_(sv)
+            lat.state().copy_(sv)
         stream.synchronize()
     return best[0], table
 

@@ -39,10 +39,14 @@ size_t store_bytes(int precision) {
         case LBM_F64: return 8;
         case LBM_F32: return 4;
         case LBM_F32_STORE_BF16:
-        case LBM_F32_STORE_F16: return 2;
+        case LBM_F32_STORE_F16:
+        case LBM_F32_STORE_BF16_REST:
+        case LBM_F32_STORE_F16_REST: return 2;
     }
     return 0;
 }
+
+bool rest_offsets(int precision) { return precision == LBM_F32_STORE_BF16_REST || precision == LBM_F32_STORE_F16_REST; }
 
 size_t compute_bytes(int precision) { return precision == LBM_F64 ? 8 : 4; }
 
@@ -101,7 +105,9 @@ size_t population_bytes(const lbm_sc_params* p) {
     int px, py, gxo, gyo;
     long long Np;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), px, py, gxo, gyo, Np);
-    return (size_t)2 * q_of(p->lattice) * (size_t)Np * store_bytes(p->precision);
+    // rest-offset storage keeps the two FP32 density planes after the populations
+    return (size_t)2 * q_of(p->lattice) * (size_t)Np * store_bytes(p->precision) +
+           (rest_offsets(p->precision) ? (size_t)2 * (size_t)Np * 4 : 0);
 }
 
 size_t partial_bytes(const Plan& pl) {
@@ -362,6 +368,7 @@ struct lbm_sc_batch {
     int lattice, precision, tile, zchunk, graph_steps;
     void* d_lats;
     lbmsc::BatchItem* d_items;
+    int* d_ctr;  // work-queue counters of the batch kernels
     int nitems;
     int parity;
     int sm_count;
@@ -416,7 +423,7 @@ std::vector<lbmsc::BatchItem> batch_items(lbm_sc_handle* const* handles, int n, 
 cudaError_t batch_launch_steps(lbm_sc_batch* b, int nsteps) {
     for (int t = 0; t < nsteps; ++t) {
         const cudaError_t e = lbmsc::batch_step(b->lattice, b->precision, b->tile, b->d_lats, b->d_items, b->nitems,
-                                                b->parity, b->sm_count, b->stream);
+                                                b->parity, b->sm_count, b->d_ctr, b->stream);
         if (e != cudaSuccess) return e;
         b->parity ^= 1;
     }
@@ -431,7 +438,7 @@ size_t lbm_sc_batch_workspace_bytes(lbm_sc_handle* const* handles, int n, int ti
     if (!batch_valid(handles, n, tile, zchunk)) return 0;
     const size_t items = batch_items(handles, n, tile, zchunk).size();
     return align_up(lbmsc::batch_lattice_bytes(handles[0]->params.precision, tile) * (size_t)n) +
-           align_up(items * sizeof(lbmsc::BatchItem));
+           align_up(items * sizeof(lbmsc::BatchItem)) + kAlign /* queue counters */;
 }
 
 lbm_status lbm_sc_batch_create(lbm_sc_handle* const* handles, int n, int tile, int zchunk, int graph_steps,
@@ -469,14 +476,17 @@ lbm_status lbm_sc_batch_create(lbm_sc_handle* const* handles, int n, int tile, i
     char* ws = static_cast<char*>(d_workspace);
     b->d_lats = ws;
     b->d_items = reinterpret_cast<lbmsc::BatchItem*>(ws + align_up(lb * (size_t)n));
+    b->d_ctr = reinterpret_cast<int*>(ws + align_up(lb * (size_t)n) + align_up(items.size() * sizeof(lbmsc::BatchItem)));
     cudaError_t e = cudaMemcpyAsync(b->d_lats, lats.data(), lats.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(int), b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(lbmsc::BatchItem),
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host staging goes out of scope
     // kernel attributes and occupancy are set up now, outside any later stream capture
-    if (e == cudaSuccess) e = lbmsc::batch_step(b->lattice, b->precision, tile, b->d_lats, b->d_items, 0, 0, b->sm_count,
-                                                b->stream);
+    if (e == cudaSuccess)
+        e = lbmsc::batch_step(b->lattice, b->precision, tile, b->d_lats, b->d_items, 0, 0, b->sm_count, b->d_ctr,
+                              b->stream);
     if (e != cudaSuccess) {
         delete b;
         return LBM_ERR_CUDA;

@@ -11,7 +11,7 @@ namespace lbmsc {
 namespace {
 
 template <class L, class S, int TX, int TY>
-cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
+cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
                          cudaStream_t st) {
     using C = typename Codec<S>::C;
     constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : 2);
@@ -26,12 +26,13 @@ cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, i
     long long grid = (long long)sm_count * (per_sm > 0 ? per_sm : 1);
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
-    kern<<<(unsigned)grid, dim3(TX, TY), 0, st>>>(static_cast<const BatchLattice<S>*>(lats), items, nitems, parity);
+    kern<<<(unsigned)grid, dim3(TX, TY), 0, st>>>(static_cast<const BatchLattice<S>*>(lats), items, nitems, parity,
+                                                  ctr);
     return cudaGetLastError();
 }
 
 template <int TX, int TY, int ST>
-cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
+cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
                              cudaStream_t st) {
     using T = TmaTile<TX, TY, ST>;
     auto kern = sc_batch_tma_kernel<TX, TY, ST>;
@@ -42,22 +43,22 @@ cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitem
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, dim3(TX, TY), T::smem_bytes, st>>>(static_cast<const BatchTmaLattice*>(lats), items,
-                                                              nitems, parity);
+                                                              nitems, parity, ctr);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
-                        cudaStream_t st) {
+                        int* ctr, cudaStream_t st) {
     switch (tile) {
-        case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, st);
-        case 1: return launch_batch<L, S, 32, 4>(lats, items, nitems, parity, sm_count, st);
-        case 2: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, st);
+        case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, st);
+        case 1: return launch_batch<L, S, 32, 4>(lats, items, nitems, parity, sm_count, ctr, st);
+        case 2: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, ctr, st);
     }
     if constexpr (std::is_same<L, D3Q19>::value && std::is_same<S, float>::value) {
         switch (tile) {
-            case 3: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, st);
-            case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, st);
+            case 3: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, ctr, st);
+            case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, st);
         }
     }
     return cudaErrorInvalidValue;
@@ -65,12 +66,14 @@ cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int 
 
 template <class L>
 cudaError_t batch_lat(int precision, int tile, const void* lats, const BatchItem* items, int nitems, int parity,
-                      int sm_count, cudaStream_t st) {
+                      int sm_count, int* ctr, cudaStream_t st) {
     switch (precision) {
-        case 0: return batch_typed<L, double>(tile, lats, items, nitems, parity, sm_count, st);
-        case 1: return batch_typed<L, float>(tile, lats, items, nitems, parity, sm_count, st);
-        case 2: return batch_typed<L, __nv_bfloat16>(tile, lats, items, nitems, parity, sm_count, st);
-        case 3: return batch_typed<L, __half>(tile, lats, items, nitems, parity, sm_count, st);
+        case 0: return batch_typed<L, double>(tile, lats, items, nitems, parity, sm_count, ctr, st);
+        case 1: return batch_typed<L, float>(tile, lats, items, nitems, parity, sm_count, ctr, st);
+        case 2: return batch_typed<L, __nv_bfloat16>(tile, lats, items, nitems, parity, sm_count, ctr, st);
+        case 3: return batch_typed<L, __half>(tile, lats, items, nitems, parity, sm_count, ctr, st);
+        case 4: return batch_typed<L, bf16_rest>(tile, lats, items, nitems, parity, sm_count, ctr, st);
+        case 5: return batch_typed<L, f16_rest>(tile, lats, items, nitems, parity, sm_count, ctr, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -95,6 +98,8 @@ size_t batch_lattice_bytes(int precision, int tile) {
         case 1: return sizeof(BatchLattice<float>);
         case 2: return sizeof(BatchLattice<__nv_bfloat16>);
         case 3: return sizeof(BatchLattice<__half>);
+        case 4: return sizeof(BatchLattice<bf16_rest>);
+        case 5: return sizeof(BatchLattice<f16_rest>);
     }
     return 0;
 }
@@ -123,15 +128,17 @@ cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, in
         case 1: fill_typed<float>(p, b0, b1, cur0, zchunk, dst); break;
         case 2: fill_typed<__nv_bfloat16>(p, b0, b1, cur0, zchunk, dst); break;
         case 3: fill_typed<__half>(p, b0, b1, cur0, zchunk, dst); break;
+        case 4: fill_typed<bf16_rest>(p, b0, b1, cur0, zchunk, dst); break;
+        case 5: fill_typed<f16_rest>(p, b0, b1, cur0, zchunk, dst); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaSuccess;
 }
 
 cudaError_t batch_step(int lattice, int precision, int tile, const void* lats, const BatchItem* items, int nitems,
-                       int parity, int sm_count, cudaStream_t st) {
-    return lattice == 0 ? batch_lat<D2Q9>(precision, tile, lats, items, nitems, parity, sm_count, st)
-                        : batch_lat<D3Q19>(precision, tile, lats, items, nitems, parity, sm_count, st);
+                       int parity, int sm_count, int* ctr, cudaStream_t st) {
+    return lattice == 0 ? batch_lat<D2Q9>(precision, tile, lats, items, nitems, parity, sm_count, ctr, st)
+                        : batch_lat<D3Q19>(precision, tile, lats, items, nitems, parity, sm_count, ctr, st);
 }
 
 }  // namespace lbmsc

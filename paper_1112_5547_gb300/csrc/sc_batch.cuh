@@ -14,6 +14,31 @@
 
 namespace lbmsc {
 
+// Work queue of a batch launch: CTAs take items in list order from an atomic
+// counter (so the items in flight at any moment are neighbours in the list,
+// as with the hardware's own block order, and a CTA that finishes early takes
+// more).  The next index is fetched while the current item runs.  The last
+// CTA to find the queue empty resets both counters for the next launch, so
+// launches need no memset and replay from a CUDA graph.
+struct BatchQueue {
+    int* ctr;  // [0]: next item, [1]: CTAs done
+    int* slot; // shared: the fetched index
+
+    __device__ __forceinline__ void fetch(int tid) {
+        if (tid == 0) *slot = atomicAdd(&ctr[0], 1);
+    }
+    __device__ __forceinline__ void retire(int tid) {
+        if (tid == 0) {
+            __threadfence();
+            if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
+                ctr[0] = 0;
+                ctr[1] = 0;
+                __threadfence();
+            }
+        }
+    }
+};
+
 // Both parities of one lattice: a[p] reads buffer cur0 ^ p and writes the other.
 template <class S> struct BatchLattice {
     LatticeArgs<S> a[2];
@@ -22,7 +47,7 @@ template <class S> struct BatchLattice {
 template <class L, class S, int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX* TY, MINB)
     sc_batch_step_kernel(const BatchLattice<S>* __restrict__ lats,
-                         const BatchItem* __restrict__ items, int nitems, int parity) {
+                         const BatchItem* __restrict__ items, int nitems, int parity, int* __restrict__ ctr) {
     using C = typename Codec<S>::C;
     constexpr int Q = L::Q;
     constexpr int FX = TX + 2, FY = TY + 2;
@@ -30,14 +55,22 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     constexpr int H = 2 * FX + 2 * TY;
     static_assert(H <= TX * TY, "halo ring must fit in the CTA");
     __shared__ C srho[NPL][2][FY][FX];
+    __shared__ int s_next;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const bool halo = tid < H;
     int hfx, hfy;
     halo_cell<TX, TY>(tid, hfx, hfy);
+    BatchQueue queue{ctr, &s_next};
+    queue.fetch(tid);
+    __syncthreads();
 
 #pragma unroll 1
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (;;) {
+        const int it = s_next;
+        if (it >= nitems) break;
+        __syncthreads();  // every thread has read s_next
+        queue.fetch(tid);  // the next index, while this item runs
         const BatchItem w = items[it];
         const LatticeArgs<S> a = lats[w.lat].a[parity];
         const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -102,14 +135,15 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 __syncthreads();
             }
         }
-        __syncthreads();  // the next item rewrites the density ring
+        __syncthreads();  // the next item rewrites the density ring; s_next is visible
     }
+    queue.retire(tid);
 }
 
 // Both parities of one FP32 D3Q19 lattice for the TMA-fed batch kernel: the
 // tensor map of the buffer each parity reads, its arguments, and the lattice's
 // error word (raised if a bounded wait expires on one of its items).
-struct alignas(64) BatchTmaLattice {
+struct BatchTmaLattice {  // CUtensorMap brings its own 128-byte alignment
     CUtensorMap map[2];
     LatticeArgs<float> a[2];
     int* err;
@@ -120,21 +154,54 @@ struct alignas(64) BatchTmaLattice {
 template <int TX, int TY, int S>
 __global__ void __launch_bounds__(TX* TY, 1)
     sc_batch_tma_kernel(const BatchTmaLattice* __restrict__ lats, const BatchItem* __restrict__ items, int nitems,
-                        int parity) {
+                        int parity, int* __restrict__ ctr) {
+    static_assert(S <= 3, "every item has at least 3 planes: all S first planes of the next item are pre-issued");
     extern __shared__ unsigned char smem_raw[];
+    __shared__ int s_next;
     TmaSmem<TX, TY, S> sm(smem_raw);
-    sm.init_barriers();
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    BatchQueue queue{ctr, &s_next};
+    queue.fetch(tid);
+    sm.init_barriers();  // (ends with a CTA barrier)
     unsigned qbase = 0;
+    bool preissued = false;
 #pragma unroll 1
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    for (;;) {
+        const int it = s_next;
+        if (it >= nitems) break;
+        __syncthreads();  // every thread has read s_next
+        queue.fetch(tid);
         const BatchItem w = items[it];
         const BatchTmaLattice* l = lats + w.lat;
         const LatticeArgs<float> a = l->a[parity];
-        const int n = tma_item<TX, TY, S>(&l->map[parity], a, w.x0, w.y0, w.z0, qbase, sm, l->err);
-        if (n < 0) return;
+        TmaNext nxt{nullptr, 0, 0, 0, 0, 0, 0, 0};
+        if (tid == 0) {
+            if (!preissued) tma_prefetch_map(&l->map[parity]);
+            const int nit = s_next;  // written by this thread's fetch
+            if (nit < nitems) {
+                const BatchItem wn = items[nit];
+                const BatchTmaLattice* ln = lats + wn.lat;
+                const LatticeArgs<float>& an = ln->a[parity];
+                nxt.map = &ln->map[parity];
+                tma_prefetch_map(nxt.map);
+                nxt.x0 = wn.x0;
+                nxt.y0 = wn.y0;
+                nxt.z0 = wn.z0;
+                nxt.gxo = an.gxo;
+                nxt.gyo = an.gyo;
+                nxt.nz = an.nz;
+                nxt.nplanes = min(wn.z0 + an.zchunk, an.nz) - wn.z0 + 2;
+            }
+        }
+        const int n = tma_item<TX, TY, S>(&l->map[parity], a, w.x0, w.y0, w.z0, qbase, sm, l->err, preissued, nxt);
+        if (n < 0) break;  // a lost wait: the lattice's error word is raised
         qbase += (unsigned)n;
-        __syncthreads();  // the next item rewrites the stages and the density ring
+        // the next item's first planes went out with this one (the elected
+        // thread decided; every item has at least S planes, so all did)
+        preissued = true;
+        __syncthreads();  // the next item rewrites the density ring; s_next is visible
     }
+    queue.retire(tid);
 }
 
 }  // namespace lbmsc

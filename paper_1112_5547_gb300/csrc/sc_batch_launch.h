@@ -32,7 +32,8 @@ inline bool batch_tile_fits(int tile, const Plan& p) {
 size_t batch_lattice_bytes(int precision, int tile);
 cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, int tile,
                                void* dst);
+// ctr: two device ints, zero before the first launch (each launch leaves them zero).
 cudaError_t batch_step(int lattice, int precision, int tile, const void* lats, const BatchItem* items, int nitems,
-                       int parity, int sm_count, cudaStream_t st);
+                       int parity, int sm_count, int* ctr, cudaStream_t st);
 
 }  // namespace lbmsc

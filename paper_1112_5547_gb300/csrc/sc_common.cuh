@@ -48,11 +48,15 @@ struct D3Q19 {
 
 // Storage codecs: load/store one population value.  16-bit types hold the
 // offset h = f - w_i rho_ref (the caller passes the offset w_i rho_ref).
+// The rest-offset types (kRest) hold h = f - w_i rho_s(n), rho_s(n) the density
+// of the node n the value was stored at, kept in FP32 beside the populations
+// (see rest_rho); the caller passes w_i rho_s(n) as the offset.
 template <class S> struct Codec;
 
 template <> struct Codec<double> {
     using C = double;
     static constexpr bool kOffset = false;
+    static constexpr bool kRest = false;
     __device__ __forceinline__ static C load(const double* p, C) { return __ldg(p); }
     __device__ __forceinline__ static void store(double* p, C v, C) { __stcs(p, v); }
 };
@@ -60,6 +64,7 @@ template <> struct Codec<double> {
 template <> struct Codec<float> {
     using C = float;
     static constexpr bool kOffset = false;
+    static constexpr bool kRest = false;
     __device__ __forceinline__ static C load(const float* p, C) { return __ldg(p); }
     __device__ __forceinline__ static void store(float* p, C v, C) { __stcs(p, v); }
 };
@@ -67,6 +72,7 @@ template <> struct Codec<float> {
 template <> struct Codec<__nv_bfloat16> {
     using C = float;
     static constexpr bool kOffset = true;
+    static constexpr bool kRest = false;
     __device__ __forceinline__ static C decode(__nv_bfloat16 v, C off) { return __bfloat162float(v) + off; }
     __device__ __forceinline__ static C load(const __nv_bfloat16* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__nv_bfloat16* p, C v, C off) {
@@ -77,12 +83,55 @@ template <> struct Codec<__nv_bfloat16> {
 template <> struct Codec<__half> {
     using C = float;
     static constexpr bool kOffset = true;
+    static constexpr bool kRest = false;
     __device__ __forceinline__ static C decode(__half v, C off) { return __half2float(v) + off; }
     __device__ __forceinline__ static C load(const __half* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__half* p, C v, C off) {
         *p = __float2half_rn(v - off);
     }
 };
+
+// 16-bit values offset from the rest equilibrium of their own node.
+struct bf16_rest {
+    __nv_bfloat16 v;
+};
+struct f16_rest {
+    __half v;
+};
+
+template <> struct Codec<bf16_rest> {
+    using C = float;
+    static constexpr bool kOffset = true;
+    static constexpr bool kRest = true;
+    __device__ __forceinline__ static C load(const bf16_rest* p, C off) {
+        return __fadd_rn(__bfloat162float(__ldg(&p->v)), off);
+    }
+    __device__ __forceinline__ static void store(bf16_rest* p, C v, C off) {
+        p->v = __float2bfloat16_rn(__fsub_rn(v, off));
+    }
+};
+
+template <> struct Codec<f16_rest> {
+    using C = float;
+    static constexpr bool kOffset = true;
+    static constexpr bool kRest = true;
+    __device__ __forceinline__ static C load(const f16_rest* p, C off) {
+        return __fadd_rn(__half2float(__ldg(&p->v)), off);
+    }
+    __device__ __forceinline__ static void store(f16_rest* p, C v, C off) {
+        p->v = __float2half_rn(__fsub_rn(v, off));
+    }
+};
+
+// FP32 density planes of a rest-offset population buffer: they follow its
+// 2 Q population planes, species s at plane s, same ghost-padded geometry
+// (node index cell(), values of 4 bytes).
+template <class L, class S> __host__ __device__ __forceinline__ float* rest_rho(S* buf, long long Np) {
+    return reinterpret_cast<float*>(buf + (size_t)2 * L::Q * (size_t)Np);
+}
+template <class L, class S> __host__ __device__ __forceinline__ const float* rest_rho(const S* buf, long long Np) {
+    return reinterpret_cast<const float*>(buf + (size_t)2 * L::Q * (size_t)Np);
+}
 
 // Per-lattice arguments of the step / moments kernels (compute type C).
 template <class S> struct LatticeArgs {

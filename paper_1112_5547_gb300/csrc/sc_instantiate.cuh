@@ -139,6 +139,8 @@ template <> struct AsyncDispatch<D3Q19, float> {
     }
 };
 
+template <class L, class S> cudaError_t step_typed_other(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st);
+
 template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fin, void* fout, cudaStream_t st) {
     LatticeArgs<S> a = make_args<S>(p, fin, fout);
     a.zchunk = p.step_zchunk;
@@ -150,6 +152,26 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
                       kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kNumTiles == 26,
                   "tile table and dispatch disagree");
+    if constexpr (Codec<S>::kRest) {
+        // rest-offset storage: the kernels that pull through pull_node
+        switch (p.step_tile) {
+            case 0: return step_tiled<L, S, 32, 8>(p, a, st);
+            case 1: return step_tiled<L, S, 32, 16>(p, a, st);
+            case 2: return step_tiled<L, S, 64, 8>(p, a, st);
+            case 3: return step_tiled<L, S, 32, 4>(p, a, st);
+            case 4: return step_tiled<L, S, 64, 4>(p, a, st);
+            case 11: return step_reload<L, S, 32, 4, 6>(p, a, st);
+            case 12: return step_reload<L, S, 32, 8, 3>(p, a, st);
+            case 13: return step_reload<L, S, 64, 4, 3>(p, a, st);
+            case 14: return step_reload<L, S, 32, 4, 4>(p, a, st);
+        }
+        return cudaErrorInvalidValue;
+    } else {
+        return step_typed_other<L, S>(p, a, st);
+    }
+}
+
+template <class L, class S> cudaError_t step_typed_other(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
     switch (p.step_tile) {
         case 0: return step_tiled<L, S, 32, 8>(p, a, st);
         case 1: return step_tiled<L, S, 32, 16>(p, a, st);
@@ -178,6 +200,7 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
         case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
         case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
     }
+    return cudaErrorInvalidValue;
 }
 
 template <class L, class S>
@@ -216,6 +239,8 @@ template <class L> cudaError_t step_any(const Plan& p, const void* fin, void* fo
         case 1: return step_typed<L, float>(p, fin, fout, st);
         case 2: return step_typed<L, __nv_bfloat16>(p, fin, fout, st);
         case 3: return step_typed<L, __half>(p, fin, fout, st);
+        case 4: return step_typed<L, bf16_rest>(p, fin, fout, st);
+        case 5: return step_typed<L, f16_rest>(p, fin, fout, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -227,6 +252,8 @@ cudaError_t init_any(const Plan& p, const void* rA, const void* rB, const void* 
         case 1: return init_typed<L, float>(p, rA, rB, u, fout, st);
         case 2: return init_typed<L, __nv_bfloat16>(p, rA, rB, u, fout, st);
         case 3: return init_typed<L, __half>(p, rA, rB, u, fout, st);
+        case 4: return init_typed<L, bf16_rest>(p, rA, rB, u, fout, st);
+        case 5: return init_typed<L, f16_rest>(p, rA, rB, u, fout, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -237,6 +264,8 @@ template <class L> cudaError_t moments_any(const Plan& p, const void* fin, const
         case 1: return moments_typed<L, float>(p, fin, o, st);
         case 2: return moments_typed<L, __nv_bfloat16>(p, fin, o, st);
         case 3: return moments_typed<L, __half>(p, fin, o, st);
+        case 4: return moments_typed<L, bf16_rest>(p, fin, o, st);
+        case 5: return moments_typed<L, f16_rest>(p, fin, o, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -46,7 +46,11 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
         const size_t node = cell(a, x - L::c(i, 0), y - L::c(i, 1), zs[L::c(i, 2) + 1]);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+            C off;
+            if constexpr (Codec<S>::kRest)
+                off = __fmul_rn((C)L::w(i), __ldg(rest_rho<L>(a.fin, a.Np) + (size_t)s * (size_t)a.Np + node));
+            else
+                off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
             f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.Np + node, off);
         }
     }
@@ -56,12 +60,27 @@ template <class L, class S>
 __device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
                                            const typename Codec<S>::C (&f)[2][L::Q]) {
     using C = typename Codec<S>::C;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
+    if constexpr (Codec<S>::kRest) {
+        // the cell's own density (sum of what it stores, in a fixed order) is the
+        // offset base, kept in FP32 for the nodes that pull from this cell
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-            Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], off);
+            C r = f[s][0];
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) r = __fadd_rn(r, f[s][i]);
+            rest_rho<L>(a.fout, a.Np)[(size_t)s * (size_t)a.Np + c] = r;
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i)
+                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], __fmul_rn((C)L::w(i), r));
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], off);
+            }
         }
     }
 }
@@ -409,6 +428,7 @@ __global__ void __launch_bounds__(256)
         const int z = (int)(k / ((long long)ex * ey));
         const size_t n = cell(a, cx, cy, z);
         const int x = ((cx % nx) + nx) % nx, y = ((cy % ny) + ny) % ny;
+        C fr[2][L::Q];  // rest-offset storage: the cell's values, stored together
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const int sx = (x + L::c(i, 0) + nx) % nx;
@@ -426,10 +446,15 @@ __global__ void __launch_bounds__(256)
             for (int s = 0; s < 2; ++s) {
                 const C rho = s == 0 ? rhoA[m] : rhoB[m];
                 const C f = (C)L::w(i) * rho * shape;
-                const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
-                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + n, f, off);
+                if constexpr (Codec<S>::kRest) {
+                    fr[s][i] = f;
+                } else {
+                    const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                    Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + n, f, off);
+                }
             }
         }
+        if constexpr (Codec<S>::kRest) store_cell<L, S>(a, n, fr);
     }
 }
 

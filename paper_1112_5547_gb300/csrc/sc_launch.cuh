@@ -11,7 +11,7 @@ namespace lbmsc {
 // Everything a launcher needs to know about one lattice.
 struct Plan {
     int lattice;    // 0 D2Q9, 1 D3Q19
-    int precision;  // lbm_precision
+    int precision;  // lbm_precision (4, 5: rest-offset 16-bit storage)
     int nx, ny, nz;
     long long N;
     int zchunk;     // planes per CTA along z for the moments kernel (D3Q19)
@@ -74,9 +74,9 @@ inline bool tile_supported(int tile, int lattice, int precision) {
     switch (kTiles[tile].kind) {
         case 0: return true;
         case 1: return lattice == 1 && precision == 1;
-        case 2: return lattice == 1;
+        case 2: return lattice == 1 && precision <= 3;
         case 3: return true;
-        case 4: return lattice == 1 && precision != 0;
+        case 4: return lattice == 1 && precision >= 1 && precision <= 3;
         case 5: return lattice == 1 && precision == 1;
     }
     return false;

@@ -56,6 +56,10 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
         "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
         : "memory");
 }
+// Bring a tensor map held in global memory into the copy engine's descriptor cache.
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Iterations of mbarrier.try_wait before a wait is declared lost (each try
@@ -98,20 +102,57 @@ template <int TX, int TY, int S> struct TmaSmem {
     }
 };
 
+// The copies of plane q of a work item (tile x0, y0; planes z0 - 1 .. z1 of
+// its chunk) into the stage of pipeline slot g: 38 boxes, one per species and
+// direction, completing on the slot's mbarrier.  Elected thread only.
+template <int TX, int TY, int S>
+__device__ __forceinline__ void tma_issue_plane(const CUtensorMap* tmap, int x0, int y0, int z0, int gxo, int gyo,
+                                                int nz, int q, unsigned g, const TmaSmem<TX, TY, S>& sm) {
+    using L = D3Q19;
+    using T = TmaTile<TX, TY, S>;
+    constexpr unsigned BS = T::box_stride / 4;
+    int z = z0 - 1 + q;
+    z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+    const unsigned st = g % S;
+    mbar_arrive_expect_tx(&sm.bars[st], T::Q2 * T::box_bytes);
+    float* sb = sm.stage + (size_t)st * (T::stage_bytes / 4);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        int zs = z - L::c(i, 2);
+        zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+        const int cy = y0 + gyo - 1 - L::c(i, 1);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int j = s * L::Q + i;
+            tma_load_4d(sb + (size_t)j * BS, tmap, &sm.bars[st], x0 + gxo - 4, cy, zs, j);
+        }
+    }
+}
+
+// The item a CTA runs after the current one (batch kernels): the elected
+// thread issues its first S planes into the stages the current item frees,
+// so the pipeline does not drain between items.
+struct TmaNext {
+    const CUtensorMap* map;
+    int x0, y0, z0, gxo, gyo, nz, nplanes;  // nplanes = 0: no next item
+};
+
 // One work item through the plane pipeline: the TX x TY tile at (x0, y0),
 // planes z0 .. min(z0 + zchunk, nz) - 1.  qbase counts the planes this CTA
 // pushed through its stages before (the mbarrier phases continue from there).
-// Every thread returns the number of planes the item used, or -1 if a wait
-// was lost (the error word is then raised, and the copies still in flight
-// have been waited for, again with a bound).  The caller must synchronise the
-// CTA between two items.
+// preissued: the item's first S planes were issued by the previous item (as
+// its TmaNext).  Every thread returns the number of planes the item used, or
+// -1 if a wait was lost (the error word is then raised, and the copies still
+// in flight have been waited for, again with a bound).  The caller must
+// synchronise the CTA between two items.
 template <int TX, int TY, int S>
 __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeArgs<float>& a, int x0, int y0, int z0,
-                                        unsigned qbase, const TmaSmem<TX, TY, S>& sm, int* __restrict__ err) {
+                                        unsigned qbase, const TmaSmem<TX, TY, S>& sm, int* __restrict__ err,
+                                        bool preissued = false, const TmaNext& nxt = TmaNext{nullptr, 0, 0, 0, 0, 0, 0, 0}) {
     using L = D3Q19;
     using T = TmaTile<TX, TY, S>;
     using C = float;
-    constexpr int Q = L::Q, Q2 = T::Q2, BX = T::BX, FX = T::FX, H = T::H;
+    constexpr int Q = L::Q, BX = T::BX, H = T::H;
     constexpr unsigned BS = T::box_stride / 4;  // floats between boxes
     static_assert(H <= TX * TY, "halo ring must fit in the CTA");
     static_assert(BX * 4 % 16 == 0, "TMA box rows are whole 16-byte units");
@@ -135,21 +176,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
     };
     // elected thread: the 38 boxes of plane q into its stage
     auto issue = [&](int q) {
-        const int z = zof(q);
-        const unsigned st = (qbase + q) % S;
-        mbar_arrive_expect_tx(&bars[st], Q2 * T::box_bytes);
-        C* sb = stage + (size_t)st * (T::stage_bytes / 4);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            int zs = z - L::c(i, 2);
-            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-            const int cy = y0 + a.gyo - 1 - L::c(i, 1);
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int j = s * Q + i;
-                tma_load_4d(sb + (size_t)j * BS, tmap, &bars[st], x0 + a.gxo - 4, cy, zs, j);
-            }
-        }
+        tma_issue_plane<TX, TY, S>(tmap, x0, y0, z0, a.gxo, a.gyo, nz, q, qbase + q, sm);
     };
     auto try_plane = [&](int q) {
         const unsigned g = qbase + q;
@@ -159,7 +186,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
         return true;
     };
 
-    if (tid == 0) {
+    if (tid == 0 && !preissued) {
         fence_proxy_async_smem();  // earlier generic reads of the stages precede the refill
         for (int q = 0; q < S && q < nplanes; ++q) issue(q);
     }
@@ -205,14 +232,22 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
         if (__syncthreads_or(lost)) {
             if (tid == 0) {
                 atomicExch(err, 1);
-                // drain: wait (bounded) for the planes issued from q on
-                for (int r = q; r < nplanes && r < q + S; ++r) try_plane(r);
+                // drain: wait (bounded) for the planes issued from q on (the
+                // next item's first planes included)
+                const int last = nxt.nplanes > 0 ? nplanes + min(S, nxt.nplanes) : nplanes;
+                for (int r = q; r < last && r < q + S; ++r) try_plane(r);
             }
             return -1;
         }
-        if (tid == 0 && q + S < nplanes) {
-            fence_proxy_async_smem();  // the stage's generic reads precede the async refill
-            issue(q + S);
+        if (tid == 0) {
+            if (q + S < nplanes) {
+                fence_proxy_async_smem();  // the stage's generic reads precede the async refill
+                issue(q + S);
+            } else if (q + S - nplanes < nxt.nplanes) {
+                fence_proxy_async_smem();
+                tma_issue_plane<TX, TY, S>(nxt.map, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz, q + S - nplanes,
+                                           qbase + q + S, sm);
+            }
         }
         if (q >= 2) collide(q - 1, Xp);
         return 0;

@@ -33,8 +33,12 @@ LBM_F64 = 0
 LBM_F32 = 1
 LBM_F32_STORE_BF16 = 2
 LBM_F32_STORE_F16 = 3
+LBM_F32_STORE_BF16_REST = 4
+LBM_F32_STORE_F16_REST = 5
 
-PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_F32_STORE_BF16, "f16": LBM_F32_STORE_F16}
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_F32_STORE_BF16, "f16": LBM_F32_STORE_F16,
+              "bf16_rest": LBM_F32_STORE_BF16_REST, "f16_rest": LBM_F32_STORE_F16_REST}
+REST_PRECISIONS = (LBM_F32_STORE_BF16_REST, LBM_F32_STORE_F16_REST)
 
 # Every entry point declared in include/lbm_sc.h.
 EXPORTS = (
@@ -77,7 +81,8 @@ TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2))
 
 
 def tile_supported(tile: int, lattice: int, precision: int) -> bool:
-    """Mirror of the library's rule: kind 1 needs D3Q19 with FP32 storage, kind 2 D3Q19."""
+    """Mirror of the library's rule: kinds 1 and 5 need D3Q19 with FP32 storage, kind 2 D3Q19 without
+    rest-offset storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage."""
     if not 0 <= tile < len(TILES):
         return False
     kind = TILE_KIND[tile]
@@ -86,8 +91,8 @@ def tile_supported(tile: int, lattice: int, precision: int) -> bool:
     if kind in (1, 5):
         return lattice == LBM_D3Q19 and precision == LBM_F32
     if kind == 4:
-        return lattice == LBM_D3Q19 and precision != LBM_F64
-    return lattice == LBM_D3Q19
+        return lattice == LBM_D3Q19 and precision in (LBM_F32, LBM_F32_STORE_BF16, LBM_F32_STORE_F16)
+    return lattice == LBM_D3Q19 and precision not in REST_PRECISIONS
 
 
 class lbm_sc_params(ctypes.Structure):
@@ -417,6 +422,16 @@ class Lattice:
         out = d.as_dict()
         out["status"] = st
         return out
+
+    def state(self):
+        """The whole current population buffer as raw bytes (with the FP32 density
+        planes of the rest-offset precisions): save and restore it to rewind."""
+        eb, q, px, py, gx, gy, ptr = lbm_sc_layout(self.handle)
+        n = 2 * q * self.params.nz * py * px * eb
+        if self.params.precision in REST_PRECISIONS:
+            n += 2 * self.params.nz * py * px * 4
+        off = ptr - self.workspace.data_ptr()
+        return self.workspace[off: off + n]
 
     def populations(self):
         """The current population buffer as a (2, Q, nz, pitch_y, pitch_x) tensor view

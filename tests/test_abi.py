@@ -119,16 +119,19 @@ def test_tuning_validation(lib):
     finally:
         lib.lbm_sc_destroy(h)
     # the cp.async tiles exist only for D3Q19 with FP32 storage, the pipelined ones for D3Q19
+    # (rest-offset storage runs only the kernels that pull through the generic node loads)
     for lat, shape, prec in ((lib.LBM_D2Q9, (8, 8), "f32"), (lib.LBM_D3Q19, (8, 8, 8), "f64"),
-                             (lib.LBM_D3Q19, (8, 8, 8), "bf16")):
+                             (lib.LBM_D3Q19, (8, 8, 8), "bf16"), (lib.LBM_D3Q19, (8, 8, 8), "bf16_rest"),
+                             (lib.LBM_D2Q9, (8, 8), "f16_rest")):
         p = lib.make_params(lat, shape, 1.0, 1.0, 2.0, prec)
         h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+        rest = prec.endswith("_rest")
         try:
             for t in range(len(lib.TILES)):
                 ok = lib.tile_supported(t, lat, p.precision)
                 kind = lib.TILE_KIND[t]
-                assert ok == (kind in (0, 3) or (kind == 2 and lat == lib.LBM_D3Q19)
-                              or (kind == 4 and lat == lib.LBM_D3Q19 and prec != "f64"))
+                assert ok == (kind in (0, 3) or (kind == 2 and lat == lib.LBM_D3Q19 and not rest)
+                              or (kind == 4 and lat == lib.LBM_D3Q19 and prec in ("f32", "bf16", "f16")))
                 if kind == 5:  # TMA kernel also needs one full tile in x and y
                     ok = False
                 if ok:
@@ -138,6 +141,36 @@ def test_tuning_validation(lib):
                         lib.lbm_sc_set_tuning(h, t, 0)
         finally:
             lib.lbm_sc_destroy(h)
+
+
+def test_rest_offset_storage_sizes(lib):
+    """Rest-offset 16-bit storage: 2 Q 16-bit planes plus two FP32 density
+    planes per buffer, about 84/152 of the FP32 bytes for D3Q19 (42/72 for D2Q9)."""
+    for lat, shape, q in ((lib.LBM_D3Q19, (64, 64, 64), 19), (lib.LBM_D2Q9, (256, 256), 9),
+                          (lib.LBM_D3Q19, (16, 64, 1024), 19)):
+        ws, px = {}, {}
+        for pr in ("f32", "bf16", "bf16_rest", "f16_rest"):
+            p = lib.make_params(lat, shape, 1.0, 1.0, 2.0, pr)
+            ws[pr] = lib.lbm_sc_workspace_bytes(p)
+            h = lib.lbm_sc_create(p, 256 * 1024, ws[pr], 0)
+            px[pr] = lib.lbm_sc_layout(h)[2]  # row pitch in values: 128-byte ghost margin, 128-byte rows
+            lib.lbm_sc_destroy(h)
+        assert ws["bf16_rest"] == ws["f16_rest"]
+        ratio = (2 * q * 2 + 2 * 4) * px["bf16_rest"] / ((2 * q * 4) * px["f32"])
+        assert abs(ws["bf16_rest"] / ws["f32"] - ratio) < 0.01 * ratio, (lat, ws)
+        assert ws["bf16"] < ws["bf16_rest"] < ws["f32"]
+    assert ratio < 0.61  # wide rows: the padding is a small part
+    p = lib.make_params(lib.LBM_D3Q19, (10, 12, 14), 1.0, 1.0, 2.0, "bf16_rest")
+    h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+    try:
+        eb, q, px, py, gx, gy, ptr = lib.lbm_sc_layout(h)
+        assert (eb, q) == (2, 19)
+        # both buffers hold the populations and the density planes
+        assert lib.lbm_sc_workspace_bytes(p) >= 2 * (2 * 19 * px * py * 10 * 2 + 2 * px * py * 10 * 4)
+    finally:
+        lib.lbm_sc_destroy(h)
+    bad = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.0, 6)
+    assert lib.lbm_sc_workspace_bytes(bad) == 0
 
 
 def test_status_strings(lib):
@@ -161,7 +194,7 @@ def test_batch_workspace_and_validation(lib):
                 items = sum(-(-nx // tx) * -(-ny // ty) * -(-nz // min(z, nz)) for nz, ny, nx in shapes)
                 ws = lib.lbm_sc_batch_workspace_bytes(hs, tile, zc)
                 assert ws >= items * 16 + len(hs) * 2 * 80
-                assert ws < items * 16 + len(hs) * 2 * 200 + 512
+                assert ws < items * 16 + len(hs) * 2 * 200 + 1024
         assert lib.lbm_sc_batch_workspace_bytes(hs, 5, 0) == 0
         # TMA-fed tiles need every lattice at least one tile wide (nx = 24 < 32 here)
         assert lib.lbm_sc_batch_workspace_bytes(hs, 3, 0) == 0

@@ -57,7 +57,8 @@ def _assert_same(a, b, what):
 
 
 @pytest.mark.parametrize("lattice,mix,precision", [(1, MIX3, "f32"), (0, MIX2, "f64"), (1, MIX3, "bf16"),
-                                                   (0, MIX2, "f16"), (1, MIX3_TMA, "f32")])
+                                                   (0, MIX2, "f16"), (1, MIX3_TMA, "f32"),
+                                                   (1, MIX3, "bf16_rest"), (0, MIX2, "f16_rest")])
 def test_batch_equals_solo(sc, lattice, mix, precision):
     steps = 13
     solo = _make(sc, lattice, mix, precision)

@@ -211,7 +211,7 @@ def test_unstable_state_reported(sc):
     assert d["status"] == sc.LBM_ERR_UNSTABLE and d["nonfinite"] >= 1
 
 
-@pytest.mark.parametrize("precision", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("precision", ["f32", "bf16", "f64", "bf16_rest", "f16_rest"])
 def test_every_launch_shape_is_bit_identical(sc, precision):
     """The step kernel's tile, kernel kind and z-chunk change only speed: all shapes agree bitwise."""
     shape = (40, 32, 70)  # 32 rows: the clustered TMA tiles (pairs and quads of y tiles) fit too

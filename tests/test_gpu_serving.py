@@ -1,0 +1,49 @@
+"""Continuous-batching server: every request's result (density field and step
+count) is the same served in a mix as solved alone, requests that arrive while
+others run are admitted as memory frees up, and the HBM budget is respected."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sv():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1112_5547_gb300 import build, serving
+    build.build()
+    return serving
+
+
+def _small_requests(sv, n=8, seed=3):
+    return sv.poisson_requests(n, rate=200.0, seed=seed, sizes2=(64, 96), sizes3=(32, 40))
+
+
+def test_served_equals_alone(sv):
+    reqs = _small_requests(sv)
+    srv = sv.Server(hbm_budget=80e9, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+    res, st = srv.run(reqs)
+    assert len(res) == len(reqs)
+    assert st.max_resident >= 2  # requests overlapped on the device
+    for r in reqs:
+        alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+        got = res[r.rid]
+        assert got.steps == alone.steps and got.converged == alone.converged
+        assert np.array_equal(got.rhoA, alone.rhoA), r.rid
+    assert st.p99_s >= st.p50_s > 0
+
+
+def test_admission_respects_budget(sv):
+    """A budget that holds only two of these lattices: at most two are resident,
+    the rest wait, and every request still finishes with its own result."""
+    reqs = sv.poisson_requests(5, rate=1000.0, seed=5, d3_fraction=1.0, sizes3=(40,))
+    fp = sv.Server.footprint(reqs[0])
+    srv = sv.Server(hbm_budget=2.5 * fp, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
+    res, st = srv.run(reqs)
+    assert st.max_resident == 2
+    assert [r.rid for r in res] == list(range(5))
+    for r in reqs[:2]:
+        alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
+        assert np.array_equal(res[r.rid].rhoA, alone.rhoA)

@@ -1,0 +1,32 @@
+"""Host-side logic of the server: the seeded Poisson request stream and the
+footprint used for admission (no GPU needed)."""
+import numpy as np
+
+
+def test_poisson_stream_is_seeded_and_in_range():
+    from paper_1112_5547_gb300 import inputs, lbm_sc, serving
+    a = serving.poisson_requests(400, rate=50.0, seed=7)
+    b = serving.poisson_requests(400, rate=50.0, seed=7)
+    assert [(r.shape, r.G, r.arrival) for r in a] == [(r.shape, r.G, r.arrival) for r in b]
+    t = np.array([r.arrival for r in a])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 50.0) < 0.25 / 50.0  # mean inter-arrival 1/rate
+    d3 = [r for r in a if r.lattice == lbm_sc.LBM_D3Q19]
+    assert 0.35 < len(d3) / len(a) < 0.65
+    for r in a:
+        L = r.shape[0]
+        assert 2.2 <= r.G * inputs.RHO_TOT <= 2.8
+        assert 0.6 <= r.tau_A <= 1.5 and 0.6 <= r.tau_B <= 1.5
+        assert L / 8 <= r.R <= L / 3
+        assert all(0 <= c < L for c in r.centre)
+        assert len(r.centre) == len(r.shape)
+
+
+def test_footprint_is_the_workspace():
+    from paper_1112_5547_gb300 import lbm_sc, serving
+    r = serving.poisson_requests(1, seed=1, d3_fraction=1.0, sizes3=(192,))[0]
+    p = lbm_sc.make_params(r.lattice, r.shape, r.tau_A, r.tau_B, r.G, "f32")
+    assert serving.Server.footprint(r) == lbm_sc.lbm_sc_workspace_bytes(p)
+    # the largest D3Q19 request: two FP32 buffers of 2 x 19 values per node
+    assert serving.Server.footprint(r) >= 2 * 2 * 19 * 4 * 192 ** 3
