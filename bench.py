@@ -7,11 +7,17 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
 129 MB L2, so no L2 flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--L 512] [--precision f32|bf16|f16|f64] [--no-e2e] [--no-cpu-baseline]
+                    [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
+                    [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
 
-Prints one JSON line (rank 0).  Under torchrun each rank advances its own
+Prints one JSON line (rank 0).  Beside the headline step it carries "batch"
+(64 ragged D3Q19 lattices advanced by one launch per step against the same
+lattices stepped one at a time) and "serving" (a seeded Poisson stream of
+drop-relaxation requests served with continuous batching against serial
+solves, p50/p99 time to result).  Under torchrun each rank advances its own
 lattice (independent replicas, no collective on the data path); the timed
-region is bracketed by barriers and the max over ranks is reported.
+region is bracketed by barriers and the max over ranks is reported; the batch
+and serving comparisons run on rank 0 only.
 """
 from __future__ import annotations
 
@@ -61,6 +67,9 @@ def parse():
     ap.add_argument("--zchunk", type=int, default=0)
     ap.add_argument("--no-batch", action="store_true", help="skip the ragged-batch vs serial comparison")
     ap.add_argument("--batch-steps", type=int, default=40)
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the continuous-batching serving run (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=50.0)
     return ap.parse_args()
 
 
@@ -224,6 +233,26 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 0):
     return out
 
 
+def serve_compare(n: int, rate: float, seed: int = 0):
+    """Continuous batching against serial solves on a seeded Poisson stream of
+    n drop-relaxation requests (mean rate per second): D2Q9 lattices 64^2 ..
+    1024^2 and D3Q19 32^3 .. 192^3, per-request G, tau, R as in the ragged
+    batch; each runs until max|u_phys| changes by < 1% over 500 steps or 10000
+    steps; 80 GB HBM admission budget; FP32.  Time to result = arrival to the
+    result (rho_A) in host memory.  Serial: the same requests one at a time
+    (plain lbm_sc_step, same convergence rule), input generation not timed."""
+    from paper_1112_5547_gb300 import serving
+    reqs = serving.poisson_requests(n, rate, seed)
+    res, st = serving.Server(hbm_budget=80e9).run(reqs)
+    sres, stot, smlups = serving.serial_baseline(reqs)
+    return {"workload": "%d Poisson requests at %.0f/s (seed %d): D2Q9 64^2..1024^2, D3Q19 32^3..192^3, "
+                        "until |d max|u|| < 1%% per 500 steps or 10000 steps, 80 GB budget, FP32" % (n, rate, seed),
+            "served_mlups": st.mlups, "serial_mlups": smlups, "speedup": st.mlups / smlups,
+            "p50_s": st.p50_s, "p99_s": st.p99_s, "mean_s": st.mean_s, "wall_s": st.wall_s, "serial_s": stot,
+            "max_resident": st.max_resident, "converged": sum(r.converged for r in res),
+            "same_steps_as_alone": all(a.steps == b.steps for a, b in zip(res, sres))}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -365,6 +394,9 @@ def main():
         del lat
         torch.cuda.empty_cache()
         bt = batch_compare(args.batch_steps, args.warmup)
+    sv = None
+    if args.serve_requests > 0 and rank == 0:
+        sv = serve_compare(args.serve_requests, args.serve_rate)
 
     if rank != 0:
         if dist is not None:
@@ -399,6 +431,8 @@ def main():
         line["e2e"] = e2e
     if bt is not None:
         line["batch"] = bt
+    if sv is not None:
+        line["serving"] = sv
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -126,9 +126,11 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * with 32-bit storage or the reference-offset 16-bit storage); 18 = 32x8 with 3 stages, 19 = 64x4 with 3
  * stages, 20 = 32x4 with 4 stages, 21 = 32x4 with 2 stages, and the cluster
  * launches 22 = 64x4 in clusters of 1x2 tiles, 23 = 64x4 in 1x4, 24 = 64x4 in
- * 2x2, 25 = 32x8 in 2x2 (TMA-fed kernel, D3Q19 with LBM_F32 only, lattices
- * at least one tile wide in x and y whose tile counts divide by the cluster
- * shape).  zchunk is the number
+ * 2x2, 25 = 32x8 in 2x2, and with the L2 fetch granularity of the tensor
+ * copies changed from 256 bytes: 26 = 64x4 in 1x2 with 128 bytes, 27 = the
+ * same with none, 28 = 32x8 with 128 bytes, 29 = 32x8 with none (TMA-fed
+ * kernel, D3Q19 with LBM_F32 only, lattices at least one tile wide in x and y
+ * whose tile counts divide by the cluster shape).  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {
@@ -256,7 +258,13 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  * LBM_ERR_INVALID_ARG if a handle was stepped on its own in between.
  * lbm_sc_moments and lbm_sc_diagnostics on a handle read the state the batch
  * left (enqueue them on the batch's stream, or synchronise it first).
- *   tile    0 = 32x8, 1 = 32x4, 2 = 64x4 columns per CTA
+ *   tile    CTA tile (x by y columns) and kernel: 0 = 32x8, 1 = 32x4, 2 = 64x4
+ *           (z-marching kernel, every lattice and precision) and 3 = 32x8,
+ *           4 = 64x4 (TMA-fed kernel, D3Q19 with LBM_F32, every lattice at
+ *           least one tile wide in x and y), all as persistent grids that
+ *           take work items from an atomic counter in the batch workspace;
+ *           5 = 32x8, 6 = 64x4 (TMA-fed) and 7 = 32x8, 8 = 64x4 (z-marching)
+ *           launch one CTA per work item instead
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

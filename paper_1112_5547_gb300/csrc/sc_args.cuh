@@ -48,12 +48,17 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+constexpr CUtensorMapL2promotion kPromotion[4] = {CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_64B,
+                                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B};
+
 // Tensor map of one FP32 population buffer as a 4-D array: x and y of the
 // ghost-padded plane, z, and the plane index s*Q + i; boxes of bx x by x 1 x 1
 // values.  The box x start of a tile at x0 is x0 + gxo - 4, so gxo must be a
 // multiple of 4 values and the row pitch of 16 bytes for it to be 16-byte
-// aligned, as tensor copies require.
-inline cudaError_t encode_population_map(const Plan& p, const float* fin, int bx, int by, CUtensorMap* map) {
+// aligned, as tensor copies require.  promo indexes kPromotion (the L2 fetch
+// granularity on a miss).
+inline cudaError_t encode_population_map(const Plan& p, const float* fin, int bx, int by, CUtensorMap* map,
+                                         int promo = 3) {
     if (p.gxo < 4 || p.gxo % 4 != 0 || (p.px * 4) % 16 != 0 || (bx * 4) % 16 != 0) return cudaErrorInvalidValue;
     auto enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
@@ -63,7 +68,7 @@ inline cudaError_t encode_population_map(const Plan& p, const float* fin, int bx
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(fin), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, kPromotion[promo & 3],
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     return cudaSuccess;

@@ -10,9 +10,10 @@ namespace lbmsc {
 
 namespace {
 
+// grid: one CTA per item (ctr unused), else a persistent grid over the counter.
 template <class L, class S, int TX, int TY>
 cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
-                         cudaStream_t st) {
+                         bool grid_mode, cudaStream_t st) {
     using C = typename Codec<S>::C;
     constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : 2);
     auto kern = sc_batch_step_kernel<L, S, TX, TY, kMin>;
@@ -23,42 +24,50 @@ cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, i
         if (e != cudaSuccess) return e;
         per_sm = n;
     }
-    long long grid = (long long)sm_count * (per_sm > 0 ? per_sm : 1);
+    long long grid = grid_mode ? nitems : (long long)sm_count * (per_sm > 0 ? per_sm : 1);
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, dim3(TX, TY), 0, st>>>(static_cast<const BatchLattice<S>*>(lats), items, nitems, parity,
-                                                  ctr);
+                                                  grid_mode ? nullptr : ctr);
     return cudaGetLastError();
 }
 
 template <int TX, int TY, int ST>
 cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
-                             cudaStream_t st) {
+                             bool grid_mode, cudaStream_t st) {
     using T = TmaTile<TX, TY, ST>;
     auto kern = sc_batch_tma_kernel<TX, TY, ST>;
     static const cudaError_t attr =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
     if (attr != cudaSuccess) return attr;
-    long long grid = sm_count;  // one CTA per SM (the stages take most of shared memory)
+    // persistent: one CTA per SM (the stages take most of shared memory)
+    long long grid = grid_mode ? nitems : sm_count;
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, dim3(TX, TY), T::smem_bytes, st>>>(static_cast<const BatchTmaLattice*>(lats), items,
-                                                              nitems, parity, ctr);
+                                                              nitems, parity, grid_mode ? nullptr : ctr);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
                         int* ctr, cudaStream_t st) {
+    static_assert(kNumBatchTiles == 9 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
+                      !kBatchTileTma[7] && kBatchTileY[8] == 4,
+                  "batch tile table and dispatch disagree");
     switch (tile) {
-        case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, st);
-        case 1: return launch_batch<L, S, 32, 4>(lats, items, nitems, parity, sm_count, ctr, st);
-        case 2: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, ctr, st);
+        case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, false, st);
+        case 1: return launch_batch<L, S, 32, 4>(lats, items, nitems, parity, sm_count, ctr, false, st);
+        case 2: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, ctr, false, st);
+        case 7: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, true, st);
+        case 8: return launch_batch<L, S, 64, 4>(lats, items, nitems, parity, sm_count, ctr, true, st);
     }
     if constexpr (std::is_same<L, D3Q19>::value && std::is_same<S, float>::value) {
         switch (tile) {
-            case 3: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, ctr, st);
-            case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, st);
+            case 3: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, ctr, false, st);
+            case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, false, st);
+            case 5: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, ctr, true, st);
+            case 6: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, true, st);
         }
     }
     return cudaErrorInvalidValue;

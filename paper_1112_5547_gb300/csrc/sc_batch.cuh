@@ -14,21 +14,25 @@
 
 namespace lbmsc {
 
-// Work queue of a batch launch: CTAs take items in list order from an atomic
-// counter (so the items in flight at any moment are neighbours in the list,
-// as with the hardware's own block order, and a CTA that finishes early takes
-// more).  The next index is fetched while the current item runs.  The last
-// CTA to find the queue empty resets both counters for the next launch, so
-// launches need no memset and replay from a CUDA graph.
+// Work list order of a batch launch.  With a counter (persistent grids): CTAs
+// take items in list order from an atomic counter, so a CTA that finishes
+// early takes more; the next index is fetched while the current item runs,
+// and the last CTA to find the list empty resets both counters for the next
+// launch (no memset between launches; graph replays work).  Without a counter
+// (one CTA per item, grid = item count): CTA b runs item b, and the hardware's
+// block scheduler starts each item as an earlier one retires, which keeps the
+// items in flight at any moment neighbours in the list.
 struct BatchQueue {
-    int* ctr;  // [0]: next item, [1]: CTAs done
-    int* slot; // shared: the fetched index
+    int* ctr;   // [0]: next item, [1]: CTAs done; null: static order
+    int* slot;  // shared: the fetched index
+    int k;      // fetches so far (static order)
 
     __device__ __forceinline__ void fetch(int tid) {
-        if (tid == 0) *slot = atomicAdd(&ctr[0], 1);
+        if (tid == 0) *slot = ctr ? atomicAdd(&ctr[0], 1) : (int)blockIdx.x + k * (int)gridDim.x;
+        ++k;
     }
     __device__ __forceinline__ void retire(int tid) {
-        if (tid == 0) {
+        if (ctr && tid == 0) {
             __threadfence();
             if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
                 ctr[0] = 0;
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const bool halo = tid < H;
     int hfx, hfy;
     halo_cell<TX, TY>(tid, hfx, hfy);
-    BatchQueue queue{ctr, &s_next};
+    BatchQueue queue{ctr, &s_next, 0};
     queue.fetch(tid);
     __syncthreads();
 
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(TX* TY, 1)
     __shared__ int s_next;
     TmaSmem<TX, TY, S> sm(smem_raw);
     const int tid = threadIdx.y * TX + threadIdx.x;
-    BatchQueue queue{ctr, &s_next};
+    BatchQueue queue{ctr, &s_next, 0};
     queue.fetch(tid);
     sm.init_barriers();  // (ends with a CTA barrier)
     unsigned qbase = 0;

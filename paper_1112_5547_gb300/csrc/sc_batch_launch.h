@@ -15,11 +15,15 @@ struct BatchItem {
 
 // Batch tiles (x by y columns per CTA): 0 = 32x8, 1 = 32x4, 2 = 64x4 (z-marching
 // kernel, every lattice and precision); 3 = 32x8, 4 = 64x4 (TMA-fed kernel with
-// 3 stages, D3Q19 with FP32 storage, lattices at least one tile wide in x and y).
-constexpr int kNumBatchTiles = 5;
-constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64};
-constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4};
-constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true};
+// 3 stages, D3Q19 with FP32 storage, lattices at least one tile wide in x and
+// y).  Tiles 0-4 run persistent grids over an atomic work counter; 5 = 32x8
+// and 6 = 64x4 TMA-fed, 7 = 32x8 and 8 = 64x4 z-marching launch one CTA per
+// work item and leave the order to the hardware's block scheduler.
+constexpr int kNumBatchTiles = 9;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4};
+constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true, false, false};
+constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true, true, true};
 
 inline bool batch_tile_fits(int tile, const Plan& p) {
     if (tile < 0 || tile >= kNumBatchTiles) return false;

@@ -58,7 +58,7 @@ template <int TX, int TY, int ST> struct TmaLaunch<D3Q19, float, TX, TY, ST> {
         using T = TmaTile<TX, TY, ST>;
         if (p.nx < TX || p.ny < TY) return cudaErrorInvalidValue;
         CUtensorMap map;
-        const cudaError_t me = encode_population_map(p, a.fin, T::BX, T::BY, &map);
+        const cudaError_t me = encode_population_map(p, a.fin, T::BX, T::BY, &map, ts.promo);
         if (me != cudaSuccess) return me;
         auto kern = sc_step_tma_kernel<TX, TY, ST>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
@@ -150,7 +150,8 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[11].stages == 6 && kTiles[12].ty == 8 && kTiles[13].tx == 64 && kTiles[14].stages == 4 &&
                       kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kTiles[18].kind == 5 &&
                       kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
-                      kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kNumTiles == 26,
+                      kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kTiles[26].promo == 2 &&
+                      kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kNumTiles == 30,
                   "tile table and dispatch disagree");
     if constexpr (Codec<S>::kRest) {
         // rest-offset storage: the kernels that pull through pull_node
@@ -199,6 +200,10 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
         case 23:
         case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
         case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+        case 26:
+        case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+        case 28:
+        case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -59,15 +59,17 @@ constexpr int kTY = 8;
 //         storage, lattices at least one tile wide in x and y), launched as
 //         clusters of cx x cy neighbouring tiles (co-scheduled on one GPC, so
 //         the halo lines the tiles share are fetched into one die's L2).
-struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1; };
-constexpr int kNumTiles = 26;
+//         promo: L2 promotion of the tensor copies (0 none, 1 64 B, 2 128 B, 3 256 B).
+struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3; };
+constexpr int kNumTiles = 30;
 constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
     {32, 8, 1, 3},       {32, 8, 1, 4},       {64, 4, 1, 3},       {32, 8, 2, 0},       {64, 4, 2, 0},
     {32, 4, 2, 0},       {32, 4, 3, 6},       {32, 8, 3, 3},       {64, 4, 3, 3},       {32, 4, 3, 4},
     {32, 4, 4, 3},       {32, 8, 4, 1},       {16, 8, 4, 3},       {32, 8, 5, 3},       {64, 4, 5, 3},
     {32, 4, 5, 4},       {32, 4, 5, 2},       {64, 4, 5, 3, 1, 2}, {64, 4, 5, 3, 1, 4}, {64, 4, 5, 3, 2, 2},
-    {32, 8, 5, 3, 2, 2}};
+    {32, 8, 5, 3, 2, 2}, {64, 4, 5, 3, 1, 2, 2}, {64, 4, 5, 3, 1, 2, 0}, {32, 8, 5, 3, 1, 1, 2},
+    {32, 8, 5, 3, 1, 1, 0}};
 
 inline bool tile_supported(int tile, int lattice, int precision) {
     if (tile < 0 || tile >= kNumTiles) return false;

@@ -51,8 +51,10 @@ EXPORTS = (
 
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
 # take D3Q19 lattices with FP32 storage at least one tile wide in x and y.
-BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4))
-BATCH_TILE_TMA = (False, False, False, True, True)
+# Persistent grids over an atomic work counter, or (GRID) one CTA per work item.
+BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4))
+BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False)
+BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True)
 
 
 def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
@@ -73,11 +75,14 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
 # 5: TMA-fed kernel (D3Q19, FP32 storage, lattices at least one tile wide), stages = smem stages.
 TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
          (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
-         (64, 4), (64, 4), (64, 4), (32, 8))
-TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5)
-TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3)
+         (64, 4), (64, 4), (64, 4), (32, 8), (64, 4), (64, 4),
+         (32, 8), (32, 8))
+TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5)
+TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3)
 # thread-block cluster of the TMA tiles (tiles in x, tiles in y)
-TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2))
+TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1))
+# L2 promotion (bytes fetched per L2 miss) of the TMA tiles' tensor copies
+TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0)
 
 
 def tile_supported(tile: int, lattice: int, precision: int) -> bool:

@@ -195,12 +195,14 @@ def test_batch_workspace_and_validation(lib):
                 ws = lib.lbm_sc_batch_workspace_bytes(hs, tile, zc)
                 assert ws >= items * 16 + len(hs) * 2 * 80
                 assert ws < items * 16 + len(hs) * 2 * 200 + 1024
-        assert lib.lbm_sc_batch_workspace_bytes(hs, 5, 0) == 0
-        # TMA-fed tiles need every lattice at least one tile wide (nx = 24 < 32 here)
-        assert lib.lbm_sc_batch_workspace_bytes(hs, 3, 0) == 0
-        assert lib.lbm_sc_batch_workspace_bytes(hs[2:], 3, 0) > 0
-        assert lib.lbm_sc_batch_workspace_bytes(hs[2:], 4, 0) > 0
-        assert lib.lbm_sc_batch_workspace_bytes(hs[1:], 4, 0) == 0  # nx = 9 < 64
+        assert lib.lbm_sc_batch_workspace_bytes(hs, len(lib.BATCH_TILES), 0) == 0
+        for t in range(len(lib.BATCH_TILES)):
+            tma = lib.BATCH_TILE_TMA[t]
+            # TMA-fed tiles need every lattice at least one tile wide (nx = 24 < 32 here)
+            assert (lib.lbm_sc_batch_workspace_bytes(hs, t, 0) == 0) == tma
+            assert lib.lbm_sc_batch_workspace_bytes(hs[2:], t, 0) > 0
+            fits = not tma or lib.BATCH_TILES[t][0] <= 9
+            assert (lib.lbm_sc_batch_workspace_bytes(hs[1:], t, 0) > 0) == fits  # nx = 9
         assert lib.lbm_sc_batch_workspace_bytes(hs, -1, 0) == 0
         assert lib.lbm_sc_batch_workspace_bytes(hs, 0, -1) == 0
         assert lib.lbm_sc_batch_workspace_bytes([], 0, 0) == 0
@@ -219,8 +221,9 @@ def test_batch_workspace_and_validation(lib):
                  ((0, 0, -2, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
                  ((0, 0, 0, 256 * 1024 + 8, need), lib.LBM_ERR_INVALID_ARG),  # misaligned
                  ((0, 0, 0, 256 * 1024, need - 1), lib.LBM_ERR_OUT_OF_MEMORY),
-                 ((5, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
-                 ((3, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG)]
+                 ((9, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
+                 ((3, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG),
+                 ((6, 0, 0, 256 * 1024, need), lib.LBM_ERR_INVALID_ARG)]
         for args, status in cases:
             with pytest.raises(lib.LbmError) as e:
                 lib.lbm_sc_batch_create(hs, *args, 0)

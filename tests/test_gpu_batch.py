@@ -98,12 +98,13 @@ def test_batch_graph_chunks(sc):
         for lat in solo:
             lat.step(23)
         ref = [_state(lat) for lat in solo]
-        lats = _make(sc, 1, MIX3_TMA, "f32")
-        b = sc.Batch(lats, tile=3, zchunk=16, graph_steps=4, stream=stream)
-        b.step(7).step(9).step(7)
-        stream.synchronize()
-        for k, lat in enumerate(lats):
-            _assert_same(_state(lat), ref[k], ("tma", k))
+        for tile in (3, 6):  # persistent over the work counter; one CTA per item
+            lats = _make(sc, 1, MIX3_TMA, "f32")
+            b = sc.Batch(lats, tile=tile, zchunk=16, graph_steps=4, stream=stream)
+            b.step(7).step(9).step(7)
+            stream.synchronize()
+            for k, lat in enumerate(lats):
+                _assert_same(_state(lat), ref[k], ("tma", tile, k))
 
 
 def test_batch_continues_solo_state(sc):
