@@ -130,7 +130,10 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * copies changed from 256 bytes: 26 = 64x4 in 1x2 with 128 bytes, 27 = the
  * same with none, 28 = 32x8 with 128 bytes, 29 = 32x8 with none (TMA-fed
  * kernel, D3Q19 with LBM_F32 only, lattices at least one tile wide in x and y
- * whose tile counts divide by the cluster shape).  zchunk is the number
+ * whose tile counts divide by the cluster shape); 30 = 64x4 in 1x2 clusters
+ * with 3 stages, 31 = the same with 4 stages, 32 = 32x8 with 3 stages (the
+ * TMA-fed kernel for the four 16-bit storage precisions, same size rules; the
+ * rest-offset ones also stage the FP32 densities).  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {

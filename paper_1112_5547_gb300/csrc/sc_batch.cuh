@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(TX* TY, 1)
                 nxt.nplanes = min(wn.z0 + an.zchunk, an.nz) - wn.z0 + 2;
             }
         }
-        const int n = tma_item<TX, TY, S>(&l->map[parity], a, w.x0, w.y0, w.z0, qbase, sm, l->err, preissued, nxt);
+        const int n =
+            tma_item<TX, TY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, qbase, sm, l->err, preissued, nxt);
         if (n < 0) break;  // a lost wait: the lattice's error word is raised
         qbase += (unsigned)n;
         // the next item's first planes went out with this one (the elected

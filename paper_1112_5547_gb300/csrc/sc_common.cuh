@@ -73,10 +73,10 @@ template <> struct Codec<__nv_bfloat16> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = false;
-    __device__ __forceinline__ static C decode(__nv_bfloat16 v, C off) { return __bfloat162float(v) + off; }
+    __device__ __forceinline__ static C decode(__nv_bfloat16 v, C off) { return __fadd_rn(__bfloat162float(v), off); }
     __device__ __forceinline__ static C load(const __nv_bfloat16* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__nv_bfloat16* p, C v, C off) {
-        *p = __float2bfloat16_rn(v - off);
+        *p = __float2bfloat16_rn(__fsub_rn(v, off));
     }
 };
 
@@ -84,10 +84,10 @@ template <> struct Codec<__half> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = false;
-    __device__ __forceinline__ static C decode(__half v, C off) { return __half2float(v) + off; }
+    __device__ __forceinline__ static C decode(__half v, C off) { return __fadd_rn(__half2float(v), off); }
     __device__ __forceinline__ static C load(const __half* p, C off) { return decode(__ldg(p), off); }
     __device__ __forceinline__ static void store(__half* p, C v, C off) {
-        *p = __float2half_rn(v - off);
+        *p = __float2half_rn(__fsub_rn(v, off));
     }
 };
 
@@ -103,6 +103,7 @@ template <> struct Codec<bf16_rest> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = true;
+    __device__ __forceinline__ static C decode(bf16_rest v, C off) { return __fadd_rn(__bfloat162float(v.v), off); }
     __device__ __forceinline__ static C load(const bf16_rest* p, C off) {
         return __fadd_rn(__bfloat162float(__ldg(&p->v)), off);
     }
@@ -115,6 +116,7 @@ template <> struct Codec<f16_rest> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = true;
+    __device__ __forceinline__ static C decode(f16_rest v, C off) { return __fadd_rn(__half2float(v.v), off); }
     __device__ __forceinline__ static C load(const f16_rest* p, C off) {
         return __fadd_rn(__half2float(__ldg(&p->v)), off);
     }

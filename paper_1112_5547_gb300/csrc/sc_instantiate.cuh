@@ -1,6 +1,8 @@
 // Typed launch helpers shared by the per-lattice translation units.
 #pragma once
 
+#include <cstring>
+
 #include "sc_async.cuh"
 #include "sc_tma.cuh"
 #include "sc_kernels.cuh"
@@ -52,34 +54,41 @@ cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st)
 template <class L, class S, int TX, int TY, int ST> struct TmaLaunch {
     static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
 };
-template <int TX, int TY, int ST> struct TmaLaunch<D3Q19, float, TX, TY, ST> {
-    static cudaError_t run(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
-        const TileShape& ts = kTiles[p.step_tile];
-        using T = TmaTile<TX, TY, ST>;
-        if (p.nx < TX || p.ny < TY) return cudaErrorInvalidValue;
-        CUtensorMap map;
-        const cudaError_t me = encode_population_map(p, a.fin, T::BX, T::BY, &map, ts.promo);
-        if (me != cudaSuccess) return me;
-        auto kern = sc_step_tma_kernel<TX, TY, ST>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
-        if (e != cudaSuccess) return e;
-        if (ts.cx == 1 && ts.cy == 1) {
-            kern<<<step_grid(p), dim3(TX, TY), T::smem_bytes, st>>>(map, a, p.err);
-            return cudaGetLastError();
+template <class S, int TX, int TY, int ST> struct TmaLaunch<D3Q19, S, TX, TY, ST> {
+    static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
+        if constexpr (sizeof(S) == 8) {
+            return cudaErrorInvalidValue;
+        } else {
+            const TileShape& ts = kTiles[p.step_tile];
+            using T = TmaTile<TX, TY, ST, S>;
+            if (p.nx < TX || p.ny < TY) return cudaErrorInvalidValue;
+            TmaMaps maps;
+            memset(&maps, 0, sizeof(maps));
+            cudaError_t e = encode_population_map(p, a.fin, T::BX, T::BY, &maps.pop, ts.promo, T::E);
+            if (e == cudaSuccess && T::REST)
+                e = encode_rho_map(p, rest_rho<D3Q19>(a.fin, p.Np), T::RBX, T::RBY, &maps.rho, ts.promo);
+            if (e != cudaSuccess) return e;
+            auto kern = sc_step_tma_kernel<TX, TY, ST, S>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+            if (e != cudaSuccess) return e;
+            if (ts.cx == 1 && ts.cy == 1) {
+                kern<<<step_grid(p), dim3(TX, TY), T::smem_bytes, st>>>(maps, a, p.err);
+                return cudaGetLastError();
+            }
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = step_grid(p);
+            cfg.blockDim = dim3(TX, TY);
+            cfg.dynamicSmemBytes = T::smem_bytes;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = ts.cx;
+            attr[0].val.clusterDim.y = ts.cy;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, kern, maps, a, p.err);
         }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = step_grid(p);
-        cfg.blockDim = dim3(TX, TY);
-        cfg.dynamicSmemBytes = T::smem_bytes;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = ts.cx;
-        attr[0].val.clusterDim.y = ts.cy;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        return cudaLaunchKernelEx(&cfg, kern, map, a, p.err);
     }
 };
 
@@ -151,7 +160,8 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kTiles[18].kind == 5 &&
                       kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
                       kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kTiles[26].promo == 2 &&
-                      kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kNumTiles == 30,
+                      kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kTiles[30].kind == 6 &&
+                      kTiles[31].stages == 4 && kTiles[32].tx == 32 && kNumTiles == 33,
                   "tile table and dispatch disagree");
     if constexpr (Codec<S>::kRest) {
         // rest-offset storage: the kernels that pull through pull_node
@@ -165,6 +175,9 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
             case 12: return step_reload<L, S, 32, 8, 3>(p, a, st);
             case 13: return step_reload<L, S, 64, 4, 3>(p, a, st);
             case 14: return step_reload<L, S, 32, 4, 4>(p, a, st);
+            case 30: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+            case 31: return TmaLaunch<L, S, 64, 4, 4>::run(p, a, st);
+            case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
         }
         return cudaErrorInvalidValue;
     } else {
@@ -192,18 +205,29 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
         case 15: return RegPipeLaunch<L, S, 32, 4, 3>::run(p, a, st);
         case 16: return RegPipeLaunch<L, S, 32, 8, 1>::run(p, a, st);
         case 17: return RegPipeLaunch<L, S, 16, 8, 3>::run(p, a, st);
-        case 18: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
-        case 19: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
-        case 20: return TmaLaunch<L, S, 32, 4, 4>::run(p, a, st);
-        case 21: return TmaLaunch<L, S, 32, 4, 2>::run(p, a, st);
-        case 22:
-        case 23:
-        case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
-        case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
-        case 26:
-        case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
-        case 28:
-        case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+    }
+    if constexpr (std::is_same<S, float>::value) {
+        switch (p.step_tile) {
+            case 18: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+            case 19: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+            case 20: return TmaLaunch<L, S, 32, 4, 4>::run(p, a, st);
+            case 21: return TmaLaunch<L, S, 32, 4, 2>::run(p, a, st);
+            case 22:
+            case 23:
+            case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+            case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+            case 26:
+            case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+            case 28:
+            case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+        }
+    }
+    if constexpr (sizeof(S) == 2) {
+        switch (p.step_tile) {
+            case 30: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
+            case 31: return TmaLaunch<L, S, 64, 4, 4>::run(p, a, st);
+            case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+        }
     }
     return cudaErrorInvalidValue;
 }

@@ -50,7 +50,7 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
             if constexpr (Codec<S>::kRest)
                 off = __fmul_rn((C)L::w(i), __ldg(rest_rho<L>(a.fin, a.Np) + (size_t)s * (size_t)a.Np + node));
             else
-                off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                off = Codec<S>::kOffset ? (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B)) : (C)0;
             f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.Np + node, off);
         }
     }
@@ -78,7 +78,7 @@ __device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
         for (int i = 0; i < L::Q; ++i) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                const C off = Codec<S>::kOffset ? (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B)) : (C)0;
                 Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], off);
             }
         }
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256)
                 if constexpr (Codec<S>::kRest) {
                     fr[s][i] = f;
                 } else {
-                    const C off = Codec<S>::kOffset ? (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B) : (C)0;
+                    const C off = Codec<S>::kOffset ? (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B)) : (C)0;
                     Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + n, f, off);
                 }
             }

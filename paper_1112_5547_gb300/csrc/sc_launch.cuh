@@ -58,10 +58,12 @@ constexpr int kTY = 8;
 // kind 5: TMA-fed kernel with `stages` shared-memory stages (D3Q19, FP32
 //         storage, lattices at least one tile wide in x and y), launched as
 //         clusters of cx x cy neighbouring tiles (co-scheduled on one GPC, so
-//         the halo lines the tiles share are fetched into one die's L2).
+//         the halo lines the tiles share are fetched into one die's L2);
+// kind 6: the TMA-fed kernel for 16-bit storage (D3Q19; the rest-offset
+//         modes also stage boxes of the FP32 node densities).
 //         promo: L2 promotion of the tensor copies (0 none, 1 64 B, 2 128 B, 3 256 B).
 struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3; };
-constexpr int kNumTiles = 30;
+constexpr int kNumTiles = 33;
 constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
     {32, 8, 1, 3},       {32, 8, 1, 4},       {64, 4, 1, 3},       {32, 8, 2, 0},       {64, 4, 2, 0},
@@ -69,7 +71,7 @@ constexpr TileShape kTiles[kNumTiles] = {
     {32, 4, 4, 3},       {32, 8, 4, 1},       {16, 8, 4, 3},       {32, 8, 5, 3},       {64, 4, 5, 3},
     {32, 4, 5, 4},       {32, 4, 5, 2},       {64, 4, 5, 3, 1, 2}, {64, 4, 5, 3, 1, 4}, {64, 4, 5, 3, 2, 2},
     {32, 8, 5, 3, 2, 2}, {64, 4, 5, 3, 1, 2, 2}, {64, 4, 5, 3, 1, 2, 0}, {32, 8, 5, 3, 1, 1, 2},
-    {32, 8, 5, 3, 1, 1, 0}};
+    {32, 8, 5, 3, 1, 1, 0}, {64, 4, 6, 3, 1, 2}, {64, 4, 6, 4, 1, 2}, {32, 8, 6, 3}};
 
 inline bool tile_supported(int tile, int lattice, int precision) {
     if (tile < 0 || tile >= kNumTiles) return false;
@@ -80,6 +82,7 @@ inline bool tile_supported(int tile, int lattice, int precision) {
         case 3: return true;
         case 4: return lattice == 1 && precision >= 1 && precision <= 3;
         case 5: return lattice == 1 && precision == 1;
+        case 6: return lattice == 1 && precision >= 2 && precision <= 5;
     }
     return false;
 }
@@ -89,7 +92,7 @@ inline bool tile_supported(int tile, int lattice, int precision) {
 inline bool tile_fits(int tile, const Plan& p) {
     if (!tile_supported(tile, p.lattice, p.precision)) return false;
     const TileShape& t = kTiles[tile];
-    if (t.kind == 5) {
+    if (t.kind == 5 || t.kind == 6) {
         const int tiles_x = (p.nx + t.tx - 1) / t.tx, tiles_y = (p.ny + t.ty - 1) / t.ty;
         return p.nx >= t.tx && p.ny >= t.ty && tiles_x % t.cx == 0 && tiles_y % t.cy == 0;
     }

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
                         const unsigned short bits = (unsigned short)(up ? (word >> 16) : (word & 0xffffu));
                         S v;
                         memcpy(&v, &bits, sizeof(S));
-                        const C off = (C)L::w(i) * (s == 0 ? a.ref_A : a.ref_B);
+                        const C off = (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B));
                         h[s][i] = Codec<S>::decode(v, off);
                     }
                 }

@@ -26,6 +26,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "sc_kernels.cuh"
 
 namespace lbmsc {
@@ -67,28 +69,49 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // plane's copies).
 constexpr int kMbarSpinLimit = 1 << 24;
 
-template <int TX, int TY, int S> struct TmaTile {
-    static constexpr int BX = TX + 8, BY = TY + 2;
+// Geometry of one CTA's stages for storage type St (FP32, or 16-bit offsets).
+// Population boxes: (TX + 2 PAD) x (TY + 2) values, PAD = 16 bytes of values on
+// each side in x (TMA copies start on 16-byte boundaries).  Rest-offset
+// storage also stages, per source plane z - 1, z, z + 1 and species, a box of
+// (TX + 8) x (TY + 4) FP32 densities rho_s of the storing nodes.
+template <int TX, int TY, int S, class St = float> struct TmaTile {
+    static constexpr int E = (int)sizeof(St);
+    static constexpr int PAD = 16 / E;
+    static constexpr int BX = TX + 2 * PAD, BY = TY + 2;
     static constexpr int FX = TX + 2, FY = TY + 2;
     static constexpr int H = 2 * FX + 2 * TY;
     static constexpr int Q2 = 2 * D3Q19::Q;
-    static constexpr unsigned box_bytes = BX * BY * 4;
+    static constexpr bool REST = Codec<St>::kRest;
+    static constexpr int RBX = TX + 8, RBY = TY + 4;
+    static constexpr int NR = REST ? 6 : 0;  // density boxes per plane
+    static constexpr unsigned box_bytes = BX * BY * E;
     static constexpr unsigned box_stride = (box_bytes + 127) / 128 * 128;  // TMA destinations 128-byte aligned
-    static constexpr unsigned stage_bytes = Q2 * box_stride;
+    static constexpr unsigned rbox_bytes = RBX * RBY * 4;
+    static constexpr unsigned rbox_stride = (rbox_bytes + 127) / 128 * 128;
+    static constexpr unsigned stage_bytes = Q2 * box_stride + NR * rbox_stride;
+    static constexpr unsigned tx_bytes = Q2 * box_bytes + NR * rbox_bytes;  // bytes landing per plane
     static constexpr size_t ring_bytes = (size_t)4 * 2 * FY * FX * 4;
     static constexpr size_t smem_bytes = 128 + (size_t)S * stage_bytes + ring_bytes + (size_t)S * 8;
+    static_assert((BX * E) % 16 == 0 && (RBX * 4) % 16 == 0, "TMA box rows are whole 16-byte units");
 };
 
-// Shared memory of one CTA: S stages of 38 boxes, the density ring, S mbarriers.
-template <int TX, int TY, int S> struct TmaSmem {
-    using T = TmaTile<TX, TY, S>;
-    float* stage;
+// The tensor maps of one population buffer: the 2Q population planes and, for
+// rest-offset storage, the two FP32 density planes.
+struct TmaMaps {
+    CUtensorMap pop;
+    CUtensorMap rho;
+};
+
+// Shared memory of one CTA: S stages of boxes, the density ring, S mbarriers.
+template <int TX, int TY, int S, class St = float> struct TmaSmem {
+    using T = TmaTile<TX, TY, S, St>;
+    unsigned char* stage;
     float (*ring)[2][T::FY][T::FX];
     uint64_t* bars;
 
     __device__ __forceinline__ explicit TmaSmem(unsigned char* raw) {
         unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~(uintptr_t)127);
-        stage = reinterpret_cast<float*>(base);
+        stage = base;
         ring = reinterpret_cast<float(*)[2][T::FY][T::FX]>(base + (size_t)S * T::stage_bytes);
         bars = reinterpret_cast<uint64_t*>(base + (size_t)S * T::stage_bytes + T::ring_bytes);
     }
@@ -103,19 +126,20 @@ template <int TX, int TY, int S> struct TmaSmem {
 };
 
 // The copies of plane q of a work item (tile x0, y0; planes z0 - 1 .. z1 of
-// its chunk) into the stage of pipeline slot g: 38 boxes, one per species and
-// direction, completing on the slot's mbarrier.  Elected thread only.
-template <int TX, int TY, int S>
-__device__ __forceinline__ void tma_issue_plane(const CUtensorMap* tmap, int x0, int y0, int z0, int gxo, int gyo,
-                                                int nz, int q, unsigned g, const TmaSmem<TX, TY, S>& sm) {
+// its chunk) into the stage of pipeline slot g: 38 population boxes, one per
+// species and direction (and the 6 density boxes of rest-offset storage),
+// completing on the slot's mbarrier.  Elected thread only.
+template <int TX, int TY, int S, class St>
+__device__ __forceinline__ void tma_issue_plane(const CUtensorMap* pmap, const CUtensorMap* rmap, int x0, int y0, int z0,
+                                                int gxo, int gyo, int nz, int q, unsigned g,
+                                                const TmaSmem<TX, TY, S, St>& sm) {
     using L = D3Q19;
-    using T = TmaTile<TX, TY, S>;
-    constexpr unsigned BS = T::box_stride / 4;
+    using T = TmaTile<TX, TY, S, St>;
     int z = z0 - 1 + q;
     z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
     const unsigned st = g % S;
-    mbar_arrive_expect_tx(&sm.bars[st], T::Q2 * T::box_bytes);
-    float* sb = sm.stage + (size_t)st * (T::stage_bytes / 4);
+    mbar_arrive_expect_tx(&sm.bars[st], T::tx_bytes);
+    unsigned char* sb = sm.stage + (size_t)st * T::stage_bytes;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         int zs = z - L::c(i, 2);
@@ -124,8 +148,42 @@ __device__ __forceinline__ void tma_issue_plane(const CUtensorMap* tmap, int x0,
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const int j = s * L::Q + i;
-            tma_load_4d(sb + (size_t)j * BS, tmap, &sm.bars[st], x0 + gxo - 4, cy, zs, j);
+            tma_load_4d(sb + (size_t)j * T::box_stride, pmap, &sm.bars[st], x0 + gxo - T::PAD, cy, zs, j);
         }
+    }
+    if constexpr (T::REST) {
+        unsigned char* rb = sb + (size_t)T::Q2 * T::box_stride;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zs = z + dz;
+            zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+                tma_load_4d(rb + (size_t)((dz + 1) * 2 + s) * T::rbox_stride, rmap, &sm.bars[st], x0 + gxo - 4,
+                            y0 + gyo - 2, zs, s);
+        }
+    }
+}
+
+// The pulled value f_is of frame node (fx, fy) (frame (1, 1) = tile node
+// (0, 0)) for direction i from a landed stage, decoded to FP32 with the same
+// operations as pull_node.
+template <int TX, int TY, int S, class St>
+__device__ __forceinline__ float tma_pulled(const unsigned char* sb, int s, int i, int fx, int fy, float ref_s) {
+    using L = D3Q19;
+    using T = TmaTile<TX, TY, S, St>;
+    const int j = s * L::Q + i;
+    const St* box = reinterpret_cast<const St*>(sb + (size_t)j * T::box_stride);
+    const St v = box[fy * T::BX + fx + T::PAD - 1 - L::c(i, 0)];
+    if constexpr (std::is_same<St, float>::value) {
+        return v;
+    } else if constexpr (T::REST) {
+        const float* rb = reinterpret_cast<const float*>(sb + (size_t)T::Q2 * T::box_stride +
+                                                         (size_t)((1 - L::c(i, 2)) * 2 + s) * T::rbox_stride);
+        const float rho = rb[(fy + 1 - L::c(i, 1)) * T::RBX + fx + 3 - L::c(i, 0)];
+        return Codec<St>::decode(v, __fmul_rn((float)L::w(i), rho));
+    } else {
+        return Codec<St>::decode(v, __fmul_rn((float)L::w(i), ref_s));
     }
 }
 
@@ -141,23 +199,21 @@ struct TmaNext {
 // planes z0 .. min(z0 + zchunk, nz) - 1.  qbase counts the planes this CTA
 // pushed through its stages before (the mbarrier phases continue from there).
 // preissued: the item's first S planes were issued by the previous item (as
-// its TmaNext).  Every thread returns the number of planes the item used, or
-// -1 if a wait was lost (the error word is then raised, and the copies still
-// in flight have been waited for, again with a bound).  The caller must
-// synchronise the CTA between two items.
-template <int TX, int TY, int S>
-__device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeArgs<float>& a, int x0, int y0, int z0,
-                                        unsigned qbase, const TmaSmem<TX, TY, S>& sm, int* __restrict__ err,
-                                        bool preissued = false, const TmaNext& nxt = TmaNext{nullptr, 0, 0, 0, 0, 0, 0, 0}) {
+// its TmaNext; FP32 batch kernel only).  Every thread returns the number of
+// planes the item used, or -1 if a wait was lost (the error word is then
+// raised, and the copies still in flight have been waited for, again with a
+// bound).  The caller must synchronise the CTA between two items.
+template <int TX, int TY, int S, class St = float>
+__device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorMap* rmap, const LatticeArgs<St>& a,
+                                        int x0, int y0, int z0, unsigned qbase, const TmaSmem<TX, TY, S, St>& sm,
+                                        int* __restrict__ err, bool preissued = false,
+                                        const TmaNext nxt = TmaNext{nullptr, 0, 0, 0, 0, 0, 0, 0}) {
     using L = D3Q19;
-    using T = TmaTile<TX, TY, S>;
+    using T = TmaTile<TX, TY, S, St>;
     using C = float;
-    constexpr int Q = L::Q, BX = T::BX, H = T::H;
-    constexpr unsigned BS = T::box_stride / 4;  // floats between boxes
+    constexpr int Q = L::Q, H = T::H;
     static_assert(H <= TX * TY, "halo ring must fit in the CTA");
-    static_assert(BX * 4 % 16 == 0, "TMA box rows are whole 16-byte units");
 
-    C* const stage = sm.stage;
     auto ring = sm.ring;
     uint64_t* const bars = sm.bars;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -174,10 +230,13 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
         const int z = z0 - 1 + q;
         return z < 0 ? z + nz : (z >= nz ? z - nz : z);
     };
-    // elected thread: the 38 boxes of plane q into its stage
+    // elected thread: the boxes of plane q into its stage.  (Spreading the 38
+    // copy instructions over the lanes of a warp measured 1.8x slower.)
     auto issue = [&](int q) {
-        tma_issue_plane<TX, TY, S>(tmap, x0, y0, z0, a.gxo, a.gyo, nz, q, qbase + q, sm);
+        fence_proxy_async_smem();  // earlier generic reads of the stage precede the async refill
+        tma_issue_plane<TX, TY, S, St>(pmap, rmap, x0, y0, z0, a.gxo, a.gyo, nz, q, qbase + q, sm);
     };
+    const bool issuer = tid == 0;
     auto try_plane = [&](int q) {
         const unsigned g = qbase + q;
         int n = 0;
@@ -186,19 +245,18 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
         return true;
     };
 
-    if (tid == 0 && !preissued) {
-        fence_proxy_async_smem();  // earlier generic reads of the stages precede the refill
+    if (issuer && !preissued)
         for (int q = 0; q < S && q < nplanes; ++q) issue(q);
-    }
 
     bool lost = false;
     // own pulls of plane q into X; own and halo densities into ring slot q % 4
     auto take_plane = [&](int q, C (&X)[2][Q]) {
-        const C* sb = stage + (size_t)((qbase + q) % S) * (T::stage_bytes / 4);
+        const unsigned char* sb = sm.stage + (size_t)((qbase + q) % S) * T::stage_bytes;
 #pragma unroll
         for (int i = 0; i < Q; ++i)
 #pragma unroll
-            for (int s = 0; s < 2; ++s) X[s][i] = sb[(size_t)(s * Q + i) * BS + (ty + 1) * BX + tx + 4 - L::c(i, 0)];
+            for (int s = 0; s < 2; ++s)
+                X[s][i] = tma_pulled<TX, TY, S, St>(sb, s, i, tx + 1, ty + 1, s == 0 ? a.ref_A : a.ref_B);
         ring[q & 3][0][ty + 1][tx + 1] = node_density<L, C>(X[0]);
         ring[q & 3][1][ty + 1][tx + 1] = node_density<L, C>(X[1]);
         if (halo) {
@@ -206,7 +264,8 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
 #pragma unroll
             for (int i = 0; i < Q; ++i)
 #pragma unroll
-                for (int s = 0; s < 2; ++s) h[s][i] = sb[(size_t)(s * Q + i) * BS + hfy * BX + hfx + 3 - L::c(i, 0)];
+                for (int s = 0; s < 2; ++s)
+                    h[s][i] = tma_pulled<TX, TY, S, St>(sb, s, i, hfx, hfy, s == 0 ? a.ref_A : a.ref_B);
             ring[q & 3][0][hfy][hfx] = node_density<L, C>(h[0]);
             ring[q & 3][1][hfy][hfx] = node_density<L, C>(h[1]);
         }
@@ -222,7 +281,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-        if (owner) store_node<L, float>(a, gx, gy, zof(q), X);
+        if (owner) store_node<L, St>(a, gx, gy, zof(q), X);
     };
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
     auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> int {
@@ -239,14 +298,13 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
             }
             return -1;
         }
-        if (tid == 0) {
+        if (issuer) {
             if (q + S < nplanes) {
-                fence_proxy_async_smem();  // the stage's generic reads precede the async refill
-                issue(q + S);
+                issue(q + S);  // the stage's reads by every thread precede the barrier above
             } else if (q + S - nplanes < nxt.nplanes) {
                 fence_proxy_async_smem();
-                tma_issue_plane<TX, TY, S>(nxt.map, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz, q + S - nplanes,
-                                           qbase + q + S, sm);
+                tma_issue_plane<TX, TY, S, St>(nxt.map, nullptr, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz,
+                                               q + S - nplanes, qbase + q + S, sm);
             }
         }
         if (q >= 2) collide(q - 1, Xp);
@@ -263,13 +321,14 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* tmap, const LatticeAr
     return r < 0 ? -1 : nplanes;
 }
 
-template <int TX, int TY, int S>
+template <int TX, int TY, int S, class St = float>
 __global__ void __launch_bounds__(TX* TY, 1)
-    sc_step_tma_kernel(const __grid_constant__ CUtensorMap tmap, const LatticeArgs<float> a, int* __restrict__ err) {
+    sc_step_tma_kernel(const __grid_constant__ TmaMaps maps, const LatticeArgs<St> a, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    TmaSmem<TX, TY, S> sm(smem_raw);
+    TmaSmem<TX, TY, S, St> sm(smem_raw);
     sm.init_barriers();
-    tma_item<TX, TY, S>(&tmap, a, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * a.zchunk, 0u, sm, err);
+    tma_item<TX, TY, S, St>(&maps.pop, &maps.rho, a, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * a.zchunk, 0u, sm,
+                            err);
 }
 
 }  // namespace lbmsc

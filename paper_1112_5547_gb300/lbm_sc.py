@@ -73,16 +73,18 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
 # 3: low-register re-pull kernel (stages = CTAs per SM asked of the register allocator).
 # 4: register-pipelined kernel, three planes of pulls in registers (D3Q19, 32- and 16-bit storage).
 # 5: TMA-fed kernel (D3Q19, FP32 storage, lattices at least one tile wide), stages = smem stages.
+# 6: the TMA-fed kernel for 16-bit storage (reference- or rest-offset; D3Q19, same size rule).
 TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
          (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
          (64, 4), (64, 4), (64, 4), (32, 8), (64, 4), (64, 4),
-         (32, 8), (32, 8))
-TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5)
-TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3)
+         (32, 8), (32, 8), (64, 4), (64, 4), (32, 8))
+TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6)
+TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 4, 3)
 # thread-block cluster of the TMA tiles (tiles in x, tiles in y)
-TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1))
+TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1), (1, 2), (1, 2),
+                                   (1, 1))
 # L2 promotion (bytes fetched per L2 miss) of the TMA tiles' tensor copies
-TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0)
+TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0, 256, 256, 256)
 
 
 def tile_supported(tile: int, lattice: int, precision: int) -> bool:
@@ -95,6 +97,8 @@ def tile_supported(tile: int, lattice: int, precision: int) -> bool:
         return True
     if kind in (1, 5):
         return lattice == LBM_D3Q19 and precision == LBM_F32
+    if kind == 6:
+        return lattice == LBM_D3Q19 and precision in (LBM_F32_STORE_BF16, LBM_F32_STORE_F16) + REST_PRECISIONS
     if kind == 4:
         return lattice == LBM_D3Q19 and precision in (LBM_F32, LBM_F32_STORE_BF16, LBM_F32_STORE_F16)
     return lattice == LBM_D3Q19 and precision not in REST_PRECISIONS

@@ -157,9 +157,11 @@ class Server:
         return int(lbm_sc.lbm_sc_workspace_bytes(p))
 
     @staticmethod
-    def batch_tile(lats) -> int:
-        """TMA-fed batch tile when every lattice takes it (D3Q19, FP32, >= 32 x 8), else the 32 x 8 z-marching one."""
-        return 3 if all(lbm_sc.batch_tile_fits(3, lat) for lat in lats) else 0
+    def batch_shape(lats):
+        """(tile, zchunk) of a batch: the TMA-fed tile with one CTA per work item and
+        16-plane chunks when every lattice takes it (D3Q19, FP32, >= 32 x 8; the
+        fastest on ragged D3Q19 batches), else the persistent 32 x 8 z-marching one."""
+        return (5, 16) if all(lbm_sc.batch_tile_fits(5, lat) for lat in lats) else (0, 0)
 
     def _check(self, slots: List[_Slot]) -> List[float]:
         """max|u_phys| of each slot's current state, one synchronisation for all."""
@@ -234,8 +236,9 @@ class Server:
                     for kind in (lbm_sc.LBM_D2Q9, lbm_sc.LBM_D3Q19):
                         lats = [s.lat for s in resident if s.req.lattice == kind]
                         if lats:
-                            batches[kind] = lbm_sc.Batch(lats, tile=self.batch_tile(lats),
-                                                         graph_steps=self.graph_steps, stream=self.stream)
+                            tile, zc = self.batch_shape(lats)
+                            batches[kind] = lbm_sc.Batch(lats, tile=tile, zchunk=zc, graph_steps=self.graph_steps,
+                                                         stream=self.stream)
                     rebuilds += 1
                     dirty = False
                 for b in batches.values():

@@ -105,6 +105,7 @@ def test_tuning_validation(lib):
             tx, ty = lib.TILES[t]
             cx, cy = lib.TILE_CLUSTER[t]
             fits = lib.TILE_KIND[t] != 5 or (64 >= tx and 8 >= ty and (64 // tx) % cx == 0 and (8 // ty) % cy == 0)
+            fits = fits and lib.TILE_KIND[t] != 6  # 16-bit storage only
             if not fits:
                 with pytest.raises(lib.LbmError):
                     lib.lbm_sc_set_tuning(h, t, 0)
@@ -131,8 +132,9 @@ def test_tuning_validation(lib):
                 ok = lib.tile_supported(t, lat, p.precision)
                 kind = lib.TILE_KIND[t]
                 assert ok == (kind in (0, 3) or (kind == 2 and lat == lib.LBM_D3Q19 and not rest)
-                              or (kind == 4 and lat == lib.LBM_D3Q19 and prec in ("f32", "bf16", "f16")))
-                if kind == 5:  # TMA kernel also needs one full tile in x and y
+                              or (kind == 4 and lat == lib.LBM_D3Q19 and prec in ("f32", "bf16", "f16"))
+                              or (kind == 6 and lat == lib.LBM_D3Q19 and prec in ("bf16", "bf16_rest")))
+                if kind in (5, 6):  # TMA kernels also need one full tile in x and y
                     ok = False
                 if ok:
                     lib.lbm_sc_set_tuning(h, t, 0)

@@ -220,6 +220,7 @@ def test_every_launch_shape_is_bit_identical(sc, precision):
     probe = sc.Lattice(1, shape, 0.9, 1.1, G0, precision, 0.5, 0.5)
     tiles = [t for t in range(len(sc.TILES)) if probe.tile_fits(t)]
     assert any(sc.TILE_KIND[t] == 5 for t in tiles) == (precision == "f32")
+    assert any(sc.TILE_KIND[t] == 6 for t in tiles) == (precision in ("bf16", "bf16_rest", "f16_rest"))
     for tile in tiles:
         for z in (0, 7, 40):
             lat = sc.Lattice(1, shape, 0.9, 1.1, G0, precision, 0.5, 0.5).init(*f).set_tuning(tile, z).step(6)
