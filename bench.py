@@ -10,7 +10,8 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
                     [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
                     [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
 
-Prints one JSON line (rank 0).  Beside the headline step it carries "batch"
+Prints one JSON line (rank 0).  Beside the headline step it carries
+"storage16" (the same step with 16-bit rest-offset storage), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
 lattices stepped one at a time) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
@@ -70,6 +71,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the continuous-batching serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--no-storage16", action="store_true", help="skip the 16-bit rest-offset storage line")
     return ap.parse_args()
 
 
@@ -84,7 +86,7 @@ def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1112_5547_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith((".cu", ".cuh", ".h")):
             h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
@@ -231,6 +233,51 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 0):
     del lats
     torch.cuda.empty_cache()
     return out
+
+
+def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: str = "bf16_rest",
+                      tile: int = 30, zchunk: int = 64):
+    """The same D3Q19 drop step with 16-bit rest-offset storage (FP32 arithmetic):
+    MLUPS and the HBM roofline of its 168 algorithmic bytes per LU, timed like
+    the headline step (CUDA events on the lattice's stream, inputs far larger
+    than L2).  Launch shape fixed to the TMA-fed 16-bit kernel, tile 64x4 in
+    1x2 clusters, 64-plane chunks (the fastest measured at 512^3)."""
+    import torch
+    from paper_1112_5547_gb300 import lbm_sc
+    st = torch.cuda.Stream()
+    G = G_RHO / (RHO_HI + RHO_LO)
+    rA, rB = drop_fields(L, np.float32, seed=2)
+    with torch.cuda.stream(st):
+        lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st).init(rA, rB)
+        del rA, rB
+        if lat.tile_fits(tile):
+            lat.set_tuning(tile, zchunk)
+        lat.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lat.step(steps)
+        e1.record(st)
+        e1.synchronize()
+        d = lat.diagnostics(check=False)
+        tile_used = lat.tuning()
+    ms = e0.elapsed_time(e1) / steps
+    N = L ** 3
+    bpl = bytes_per_lu(precision)
+    gbs = bpl * N / (ms / 1e3) / 1e9
+    del lat
+    torch.cuda.empty_cache()
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tf = json.load(open(TRAFFIC_FILE))
+        key = "d3q19_%s" % precision
+        if key in tf and tf[key].get("source_hash") == kernel_source_hash():
+            traffic = tf[key]["dram_bytes_per_lu"] * N
+    return {"precision": precision, "workload": "D3Q19 %d^3 drop, same as the headline" % L, "mlups": N / ms / 1e3,
+            "traffic": traffic,
+            "ms_per_step": ms, "steps": steps, "algorithmic_bytes_per_lu": bpl, "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "tile": list(lbm_sc.TILES[tile_used[0]]), "tile_id": tile_used[0],
+            "zchunk": tile_used[1], "diag_status": d["status"],
+            "accuracy": "radius / Laplace dP / max|u| within 1% of the FP64 oracle (tests/test_gpu_storage16.py)"}
 
 
 def serve_compare(n: int, rate: float, seed: int = 0):
@@ -390,9 +437,12 @@ def main():
         del staging, hA, hB, oA, oB, oP, oU, lat2
 
     bt = None
+    del lat
+    torch.cuda.empty_cache()
+    s16 = None
+    if not args.no_storage16 and rank == 0 and prec == "f32":
+        s16 = storage16_compare(L, max(10, K // 2), args.warmup, peak)
     if not args.no_batch and rank == 0:
-        del lat
-        torch.cuda.empty_cache()
         bt = batch_compare(args.batch_steps, args.warmup)
     sv = None
     if args.serve_requests > 0 and rank == 0:
@@ -433,6 +483,8 @@ def main():
         line["batch"] = bt
     if sv is not None:
         line["serving"] = sv
+    if s16 is not None:
+        line["storage16"] = s16
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))
