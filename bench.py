@@ -177,7 +177,7 @@ def cpu_baseline(seconds: float, L: int = 128):
             "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d steps in %.1f s" % (L, n, el)}
 
 
-def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 0):
+def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     """Ragged batch against one-lattice-at-a-time on the same lattices: n
     independent D3Q19 FP32 drop lattices, L from {32, 48, 64, 96, 128}, per
     lattice G rho_tot in [2.2, 2.8], tau_A, tau_B in [0.6, 1.5], R in [L/8, L/3]
@@ -280,10 +280,10 @@ def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: s
             "accuracy": "radius / Laplace dP / max|u| within 1% of the FP64 oracle (tests/test_gpu_storage16.py)"}
 
 
-def serve_compare(n: int, rate: float, seed: int = 0):
+def serve_compare(n: int, rate: float, seed: int = 4):
     """Continuous batching against serial solves on a seeded Poisson stream of
     n drop-relaxation requests (mean rate per second): D2Q9 lattices 64^2 ..
-    1024^2 and D3Q19 32^3 .. 192^3, per-request G, tau, R as in the ragged
+    1024^2 and D3Q19 32^3 .. 192^3 (sizes 32, 48, 64, 96, 128, 160, 192), per-request G, tau, R as in the ragged
     batch; each runs until max|u_phys| changes by < 1% over 500 steps or 10000
     steps; 80 GB HBM admission budget; FP32.  Time to result = arrival to the
     result (rho_A) in host memory.  Serial: the same requests one at a time

@@ -122,7 +122,7 @@ def uniform_velocity(shape, U):
 RHO_TOT = 1.04  # rho_hi + rho_lo of the drop recipe
 
 
-def ragged_drop_specs(n=64, sizes=(32, 48, 64, 96, 128), dim=3, seed=0):
+def ragged_drop_specs(n=64, sizes=(32, 48, 64, 96, 128), dim=3, seed=3):
     """Specifications of a ragged batch of independent drop lattices.
 
     Per lattice, drawn from one numpy PCG64 stream: the edge L uniformly from

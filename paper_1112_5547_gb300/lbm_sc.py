@@ -449,7 +449,7 @@ class Lattice:
         eb, q, px, py, gx, gy, ptr = lbm_sc_layout(self.handle)
         dt = {8: t.float64, 4: t.float32}.get(eb)
         if dt is None:
-            dt = t.bfloat16 if self.params.precision == LBM_F32_STORE_BF16 else t.float16
+            dt = t.bfloat16 if self.params.precision in (LBM_F32_STORE_BF16, LBM_F32_STORE_BF16_REST) else t.float16
         nz = self.params.nz
         base = self.workspace.data_ptr()
         off = ptr - base

@@ -9,7 +9,7 @@ and advances all resident lattices together: one ragged batch per lattice kind
 ``chunk`` steps.  Every ``check_every`` steps of a request's own age its peak
 speed max|u_phys| is read (FP64 diagnostics, enqueued for all due requests and
 read back with one synchronisation); a request is done when that peak changed
-by less than ``tol`` (relative) since the previous check, or after
+by less than ``tol`` times its value at the previous check, or after
 ``max_steps`` steps.  A finished request's density field is copied to host
 memory (the result), its memory released and the batch rebuilt without it,
 so requests that arrived meanwhile take its place at the next chunk boundary.
@@ -53,8 +53,8 @@ class Request:
         return inputs.drop(self.shape, self.R, centre=self.centre, seed=self.seed, dtype=np.float32)
 
 
-def poisson_requests(n: int, rate: float = 50.0, seed: int = 0, d3_fraction: float = 0.5,
-                     sizes2=(64, 128, 256, 512, 1024), sizes3=(32, 48, 64, 96, 128, 192),
+def poisson_requests(n: int, rate: float = 50.0, seed: int = 4, d3_fraction: float = 0.5,
+                     sizes2=(64, 128, 256, 512, 1024), sizes3=(32, 48, 64, 96, 128, 160, 192),
                      precision: str = "f32") -> List[Request]:
     """n requests with exponential inter-arrival times of mean 1/rate (seeded).
 
@@ -251,7 +251,7 @@ class Server:
                 if due:
                     umax = self._check(due)
                     for s, u in zip(due, umax):
-                        conv = s.last_umax is not None and abs(u - s.last_umax) < self.tol * max(u, 1e-300)
+                        conv = s.last_umax is not None and abs(u - s.last_umax) < self.tol * max(s.last_umax, 1e-300)
                         if conv or s.steps >= self.max_steps:
                             results.append(self._retire(s, lambda: clock() - t0, conv, u))
                             resident.remove(s)
@@ -290,7 +290,7 @@ def solve_alone(req: Request, chunk: int = 100, check_every: int = 500, tol: flo
                 eb, q, px, py, gx, gy, ptr = lbm_sc.lbm_sc_layout(lat.handle)
                 lbm_sc.lbm_sc_diagnostics_noalloc(lat.params, ptr, None, diag.data_ptr(), stream.cuda_stream)
                 u = float(diag[6].cpu())
-                conv = last is not None and abs(u - last) < tol * max(u, 1e-300)
+                conv = last is not None and abs(u - last) < tol * max(last, 1e-300)
                 if conv or steps >= max_steps:
                     break
                 last = u
@@ -314,33 +314,39 @@ def serial_baseline(requests: List[Request], **kw):
 
 
 def main(argv=None):
-    """Serve a seeded Poisson stream, then solve the same requests one at a
-    time, and print one JSON line comparing the two."""
+    """Serve a seeded Poisson stream at one or more arrival rates, then solve the
+    same requests one at a time, and print one JSON line per rate."""
     import argparse
     import json
 
     ap = argparse.ArgumentParser(description=main.__doc__)
     ap.add_argument("--requests", type=int, default=32)
-    ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rate", type=str, default="50", help="arrival rate(s) per second, comma-separated")
+    ap.add_argument("--seed", type=int, default=4)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--hbm-budget-gb", type=float, default=80.0)
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=10000)
     ap.add_argument("--no-serial", action="store_true")
     a = ap.parse_args(argv)
-    reqs = poisson_requests(a.requests, a.rate, a.seed, precision=a.precision)
-    srv = Server(hbm_budget=a.hbm_budget_gb * 1e9, chunk=a.chunk, max_steps=a.max_steps)
-    res, st = srv.run(reqs)
-    out = {"requests": len(reqs), "rate_per_s": a.rate, "precision": a.precision, "served_mlups": st.mlups,
-           "wall_s": st.wall_s, "p50_s": st.p50_s, "p99_s": st.p99_s, "mean_s": st.mean_s,
-           "max_resident": st.max_resident, "chunks": st.chunks, "rebuilds": st.rebuilds,
-           "converged": sum(r.converged for r in res), "steps_total": sum(r.steps for r in res)}
-    if not a.no_serial:
-        sres, stot, smlups = serial_baseline(reqs, chunk=a.chunk, max_steps=a.max_steps)
-        out.update({"serial_mlups": smlups, "serial_s": stot,
-                    "same_steps": all(x.steps == y.steps for x, y in zip(res, sres))})
-    print(json.dumps(out))
+    rates = [float(r) for r in a.rate.split(",")]
+    serial = None
+    for rate in rates:
+        reqs = poisson_requests(a.requests, rate, a.seed, precision=a.precision)
+        srv = Server(hbm_budget=a.hbm_budget_gb * 1e9, chunk=a.chunk, max_steps=a.max_steps)
+        res, st = srv.run(reqs)
+        out = {"requests": len(reqs), "rate_per_s": rate, "seed": a.seed, "precision": a.precision,
+               "served_mlups": st.mlups, "wall_s": st.wall_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
+               "mean_s": st.mean_s, "max_resident": st.max_resident, "chunks": st.chunks, "rebuilds": st.rebuilds,
+               "converged": sum(r.converged for r in res), "steps_total": sum(r.steps for r in res),
+               "lattice_updates": st.lattice_updates}
+        if not a.no_serial:
+            if serial is None:  # the same requests (arrival times do not matter one at a time)
+                serial = serial_baseline(reqs, chunk=a.chunk, max_steps=a.max_steps)
+            sres, stot, smlups = serial
+            out.update({"serial_mlups": smlups, "serial_s": stot, "speedup": st.mlups / smlups,
+                        "same_steps": all(x.steps == y.steps for x, y in zip(res, sres))})
+        print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -1,0 +1,241 @@
+"""Parity at the full sizes of the benchmark workloads, through the C ABI.
+
+* 512^3 D3Q19 drop (the bench's headline step, in the launch shape the bench
+  times): the whole lattice is too large for the oracle, so sampled nodes are
+  checked one by one.  A node's state after one step depends only on the
+  populations within distance 3 of it, so the oracle steps a 7^3 periodic
+  window whose populations are read from the GPU's buffer at time t, and its
+  centre node (unaffected by the window's wrap) must match the GPU's moments
+  at t + 1.  Tolerance: FP32 vs FP64 rounding of one step (1e-5 relative on
+  rho, 1e-6 absolute on u); the bf16 rest-offset storage adds the rounding of
+  the stored offsets h = f* - w_i rho(src) = w_i rho (3 c_i.(u + tau F/rho) +
+  ...): at an interface |h| ~ 1/18 x 3 x 0.05 ~ 1e-2, bf16 keeps it to 2^-9
+  relative, ~2e-5 per population, so ~1e-4 on rho = sum_i f_i and on
+  j = sum_i c_i f_i (10 terms per component): bounds 2e-4 on rho and on u.
+* 64 ragged D3Q19 lattices (the bench's batch workload): batched steps equal
+  solo steps bitwise at full size, and sampled windows match the oracle.
+* 128^3 D3Q19 drop: the whole field against the oracle after 100 steps.
+* The D2Q9 Laplace batch (8 drops R = 8..40 on 256^2 and a flat interface on
+  256 x 64, FP32, 20000 steps): the pressure jump is linear in 1/R, vanishes
+  for the flat interface, and mass is conserved; the R = 16 drop matches the
+  oracle over its first 200 steps.
+"""
+import numpy as np
+import pytest
+
+from paper_1112_5547_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+G0 = 2.4 / 1.04
+
+# GPU velocity order (as documented for lbm_sc_layout): opposite directions adjacent
+GPU_C3 = np.array([(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+                   (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1),
+                   (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)])
+GPU_W3 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+@pytest.fixture(scope="module")
+def sc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1112_5547_gb300 import build, lbm_sc
+    build.build()
+    return lbm_sc
+
+
+def _decoded_window(sc, lat, centre, radius):
+    """Current populations f_is(x) (post-stream, GPU order) for the nodes within
+    `radius` of centre (periodic), decoded to FP64: f_i(x) = stored_i(x - c_i)."""
+    import torch
+    eb, q, px, py, gx, gy, _ = sc.lbm_sc_layout(lat.handle)
+    nz, ny, nx = lat.shape
+    pops = lat.populations()  # (2, Q, nz, py, px), stored type
+    prec = lat.params.precision
+    rest = prec in sc.REST_PRECISIONS
+    if rest:
+        st = lat.state()
+        npl = 2 * q * nz * py * px * eb
+        rho = st[npl:].view(torch.float32).view(2, nz, py, px)
+    r = np.arange(-radius - 1, radius + 2)
+    cz, cy, cx = centre
+    zi = torch.tensor((cz + r) % nz, device=pops.device)
+    yi = torch.tensor((cy + r) % ny + gy, device=pops.device)
+    xi = torch.tensor((cx + r) % nx + gx, device=pops.device)
+    blk = pops[:, :, zi][:, :, :, yi][:, :, :, :, xi].double().cpu().numpy()  # (2, Q, W+2, W+2, W+2)
+    if rest:
+        rb = rho[:, zi][:, :, yi][:, :, :, xi].double().cpu().numpy()  # (2, W+2, W+2, W+2)
+        blk = blk + GPU_W3[None, :, None, None, None] * rb[:, None]
+    elif prec in (sc.LBM_F32_STORE_BF16, sc.LBM_F32_STORE_F16):
+        ref = np.array([lat.params.rho_ref_A, lat.params.rho_ref_B])
+        blk = blk + (GPU_W3[None, :] * ref[:, None])[:, :, None, None, None]
+    W = 2 * radius + 1
+    f = np.empty((2, q, W, W, W))
+    for i, (ax, ay, az) in enumerate(GPU_C3):
+        # window node w (offset 1 in blk) pulls from w - c_i
+        f[:, i] = blk[:, i, 1 - az:1 - az + W, 1 - ay:1 - ay + W, 1 - ax:1 - ax + W]
+    return f
+
+
+def _oracle_window_step(oracle_mod, f_gpu, tau_A, tau_B, G):
+    """One oracle step of the periodic window; moments of its centre node."""
+    c_or, _ = oracle_mod.lattice(1)
+    perm = [int(np.nonzero((GPU_C3 == c).all(1))[0][0]) for c in c_or]  # oracle i -> GPU i
+    W = f_gpu.shape[-1]
+    o = oracle_mod.OracleSC(1, (W, W, W), tau_A, tau_B, G)
+    # oracle populations: node-major (N, 2, Q), node x + W (y + W z), oracle order
+    o.f[:] = f_gpu[:, perm].transpose(2, 3, 4, 0, 1).reshape(W ** 3, 2, len(perm))
+    o.step(1)
+    a, b, u, p = o.moments()
+    m = W // 2
+    return a[m, m, m], b[m, m, m], u[m, m, m]
+
+
+def _samples(L, tile=(64, 4), zchunk=64, n_random=10, seed=7):
+    rng = np.random.default_rng(seed)
+    tx, ty = tile
+    pts = [(0, 0, 0), (L - 1, L - 1, L - 1), (zchunk - 1, ty - 1, tx - 1), (zchunk, ty, tx),
+           (L // 2, 2 * ty - 1, 2 * tx), (L // 2, L // 2, L // 2 + L // 4), (L // 2 + L // 4, L // 2, L // 2)]
+    pts += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(n_random)]
+    return [tuple(v % L for v in p) for p in pts]
+
+
+def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4):
+    lat.step(steps_before)
+    tau_A, tau_B, G = lat.params.tau_A, lat.params.tau_B, lat.params.G
+    ref = []
+    for pt in pts:
+        f = _decoded_window(sc, lat, pt, 3)
+        ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G))
+    lat.step(1)
+    rA, rB, u, _ = lat.moments()
+    for pt, (oa, ob, ou) in zip(pts, ref):
+        z, y, x = pt
+        ga, gb = float(rA[z, y, x]), float(rB[z, y, x])
+        gu = u[z, y, x].double().cpu().numpy()
+        assert abs(ga - oa) <= tol_rho * max(abs(oa), 1e-3), (pt, ga, oa)
+        assert abs(gb - ob) <= tol_rho * max(abs(ob), 1e-3), (pt, gb, ob)
+        assert np.abs(gu - ou).max() <= tol_u, (pt, gu, ou)
+
+
+@pytest.mark.parametrize("precision,tile,tol_rho,tol_u", [("f32", 22, 1e-5, 1e-6), ("bf16_rest", 30, 2e-4, 2e-4)])
+def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tile, tol_rho, tol_u):
+    """The bench's 512^3 drop in the bench's launch shape (tile 22: TMA 64x4, 1x2
+    clusters, 64-plane chunks; tile 30 for the 16-bit line)."""
+    import torch
+    L = 512
+    rA, rB = inputs.drop((L, L, L), L / 4, seed=2, dtype=np.float32)
+    lat = sc.Lattice(1, (L, L, L), 1.0, 1.0, G0, precision).init(rA, rB)
+    del rA, rB
+    lat.set_tuning(tile, 64)
+    assert lat.tuning() == (tile, 64)
+    _check_sampled(sc, oracle_mod, lat, _samples(L), tol_rho, tol_u)
+    d = lat.diagnostics()
+    assert d["status"] == sc.LBM_OK
+    del lat
+    torch.cuda.empty_cache()
+
+
+def test_ragged_batch_full_size(sc, oracle_mod):
+    """The bench's 64 ragged lattices: batched (TMA tile, one CTA per item, 16-plane
+    chunks, graph chunks of 8) equals solo bitwise after 10 steps; sampled windows
+    of four lattices match the oracle one step later."""
+    import torch
+    specs = inputs.ragged_drop_specs()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        mk = lambda sp: sc.Lattice(1, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32", stream=stream).init(
+            *inputs.spec_fields(sp, dtype=np.float32))
+        solo = [mk(sp) for sp in specs]
+        for lat in solo:
+            lat.step(10)
+        ref = [[t.cpu().numpy() for t in lat.moments()] for lat in solo]
+        del solo
+        lats = [mk(sp) for sp in specs]
+        b = sc.Batch(lats, tile=5, zchunk=16, graph_steps=8, stream=stream)
+        b.step(10)
+        stream.synchronize()
+        for k, lat in enumerate(lats):
+            got = [t.cpu().numpy() for t in lat.moments()]
+            for x, y in zip(got, ref[k]):
+                assert np.array_equal(x, y), k
+        b.close()
+        for k in (0, 17, 40, 63):
+            lat = lats[k]
+            L = lat.shape[0]
+            _check_sampled(sc, oracle_mod, lat, _samples(L, (32, 8), 16, n_random=3, seed=k), 1e-5, 1e-6, 0)
+        stream.synchronize()
+    torch.cuda.empty_cache()
+
+
+def test_128_drop_whole_field_vs_oracle(sc, oracle_mod):
+    L, steps = 128, 100
+    f = inputs.drop((L, L, L), L / 4, seed=2)
+    lat = sc.Lattice(1, (L, L, L), 1.0, 1.0, G0, "f32").init(*f)
+    lat.step(steps)
+    g = [t.double().cpu().numpy() for t in lat.moments()]
+    o = oracle_mod.OracleSC(1, (L, L, L), 1.0, 1.0, G0).init(*f).step(steps)
+    a, b, u, p = o.moments()
+    for x, y in ((g[0], a), (g[1], b), (g[3], p)):
+        assert np.abs(x - y).max() / np.abs(y).max() < 1e-5
+    assert np.abs(g[2] - u).max() / max(np.abs(u).max(), 1e-3) < 1e-3
+
+
+def _laplace_observables(rhoA, p, R0):
+    shape = rhoA.shape
+    r = inputs.radial_distance(shape, tuple(n / 2.0 for n in reversed(shape)))
+    rin = rhoA[r < R0 / 4].mean()
+    rout = rhoA[r > R0 + 8].mean()
+    R = np.sqrt((rhoA - rout).sum() / (rin - rout) / np.pi)
+    dP = p[r < R / 4].mean() - p[r > R + 8].mean()
+    return R, dP
+
+
+def test_laplace_batch_full_size(sc, oracle_mod):
+    """8 drops (R = 8..40) on 256^2 and a flat interface on 256 x 64, FP32, 20000
+    steps, advanced as one D2Q9 batch: dP is linear in 1/R (Laplace, Sec. 4.1:
+    dP = sigma / R in 2D) with a vanishing intercept, the flat interface has no
+    jump, mass is conserved.  The R = 16 drop matches the oracle over 200 steps."""
+    import torch
+    radii = (8, 12, 16, 20, 24, 28, 32, 40)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        drops = [sc.Lattice(0, (256, 256), 1.0, 1.0, G0, "f32", stream=stream).init(
+            *inputs.drop((256, 256), R, seed=1 + k)) for k, R in enumerate(radii)]
+        slab_f = inputs.slab((64, 256), 64, seed=9)
+        slab = sc.Lattice(0, (64, 256), 1.0, 1.0, G0, "f32", stream=stream).init(*slab_f)
+        # the oracle check of the R = 16 drop over its first 200 steps
+        probe = sc.Lattice(0, (256, 256), 1.0, 1.0, G0, "f32", stream=stream).init(*inputs.drop((256, 256), 16, seed=3))
+        probe.step(200)
+        g = [t.double().cpu().numpy() for t in probe.moments()]
+        o = oracle_mod.OracleSC(0, (256, 256), 1.0, 1.0, G0).init(*inputs.drop((256, 256), 16, seed=3)).step(200)
+        a, b, _, _ = o.moments()
+        assert np.abs(g[0] - a).max() / np.abs(a).max() < 1e-5
+        del probe
+        m0 = [lat.diagnostics()["mass_A"] for lat in drops + [slab]]
+        b = sc.Batch(drops + [slab], tile=7, graph_steps=100, stream=stream)
+        b.step(20000)
+        stream.synchronize()
+        b.close()
+        obs = []
+        for lat, R0 in zip(drops, radii):
+            rA, rB, u, p = lat.moments()
+            obs.append(_laplace_observables(rA.double().cpu().numpy(), p.double().cpu().numpy(), R0))
+        m1 = [lat.diagnostics()["mass_A"] for lat in drops + [slab]]
+        rA, rB, u, p = slab.moments()
+        pp = p.double().cpu().numpy()
+    for x, y in zip(m0, m1):
+        assert abs(x - y) / x < 2e-5, (x, y)
+    R = np.array([o[0] for o in obs])
+    dP = np.array([o[1] for o in obs])
+    A = np.vstack([1 / R, np.ones_like(R)]).T
+    (sigma, c0), res, _, _ = np.linalg.lstsq(A, dP, rcond=None)
+    pred = A @ np.array([sigma, c0])
+    r2 = 1 - ((dP - pred) ** 2).sum() / ((dP - dP.mean()) ** 2).sum()
+    assert sigma > 0 and r2 > 0.99, (sigma, c0, r2, R, dP)
+    assert abs(c0) < 0.05 * dP.max(), (c0, dP)
+    # flat interface: bulk pressure inside the slab (x in [96, 160)) equals outside (x < 32 or x >= 224)
+    flat = pp[:, 96:160].mean() - np.concatenate([pp[:, :32], pp[:, 224:]], axis=1).mean()
+    assert abs(flat) < 0.02 * dP.max(), (flat, dP)
