@@ -246,10 +246,11 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  * lattice alone.  The paper runs one lattice at a time; batching is a
  * throughput device for many small lattices, which alone cannot fill the GPU.
  *
- * The launch walks a work list of (lattice, x tile, y tile, z chunk) items,
- * longest first, with a persistent grid of CTAs; per-lattice arguments come
- * from a descriptor array.  Both live in the batch workspace (device memory
- * owned by the caller).  When graph_steps > 0 and the stream is not the legacy
+ * The launch covers a work list of (lattice, x tile, y tile, z chunk) items,
+ * longest first, either with a persistent grid of CTAs that take items from
+ * an atomic counter or with one CTA per item (see tile below); per-lattice
+ * arguments come from a descriptor array.  The list, the descriptors and the
+ * counter live in the batch workspace (device memory owned by the caller).  When graph_steps > 0 and the stream is not the legacy
  * default stream, whole chunks of graph_steps steps are replayed from a CUDA
  * graph captured on the first use (one per starting parity); the remaining
  * steps are direct launches.
@@ -267,7 +268,9 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  *           least one tile wide in x and y), all as persistent grids that
  *           take work items from an atomic counter in the batch workspace;
  *           5 = 32x8, 6 = 64x4 (TMA-fed) and 7 = 32x8, 8 = 64x4 (z-marching)
- *           launch one CTA per work item instead
+ *           launch one CTA per work item instead; 9 = TMA-fed, one CTA per
+ *           item, each lattice with its own tile: 64x4 if it is at least 64
+ *           wide, else 32x8 (same requirements as 5)
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

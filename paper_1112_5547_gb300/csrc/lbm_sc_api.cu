@@ -399,9 +399,10 @@ int batch_zchunk(const lbm_sc_handle* h, int zchunk) {
 std::vector<lbmsc::BatchItem> batch_items(lbm_sc_handle* const* handles, int n, int tile, int zchunk) {
     std::vector<lbmsc::BatchItem> items;
     std::vector<int> len;
-    const int tx = lbmsc::kBatchTileX[tile], ty = lbmsc::kBatchTileY[tile];
     for (int k = 0; k < n; ++k) {
         const lbm_sc_params& p = handles[k]->params;
+        int tx, ty;
+        lbmsc::batch_item_tile(tile, handles[k]->plan, tx, ty);
         const int zc = batch_zchunk(handles[k], zchunk);
         for (int z0 = 0; z0 < p.nz; z0 += zc)
             for (int y0 = 0; y0 < p.ny; y0 += ty)

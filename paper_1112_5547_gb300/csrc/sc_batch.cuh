@@ -151,6 +151,7 @@ struct BatchTmaLattice {  // CUtensorMap brings its own 128-byte alignment
     CUtensorMap map[2];
     LatticeArgs<float> a[2];
     int* err;
+    int wide;  // mixed-shape batches: 1 = this lattice's items are 64x4 tiles, 0 = 32x8
 };
 
 // TMA-fed batch step: persistent CTAs run tma_item (sc_tma.cuh) over the work
@@ -207,6 +208,32 @@ __global__ void __launch_bounds__(TX* TY, 1)
         __syncthreads();  // the next item rewrites the density ring; s_next is visible
     }
     queue.retire(tid);
+}
+
+// Mixed-shape TMA batch step, one CTA of 256 threads per work item: items of
+// lattices at least 64 wide run as 64x4 tiles (fewer halo rows and boxes
+// re-read per node), the others as 32x8 tiles; the shared memory holds the
+// larger of the two layouts.
+template <int S>
+__global__ void __launch_bounds__(256, 1)
+    sc_batch_tma_mixed_kernel(const BatchTmaLattice* __restrict__ lats, const BatchItem* __restrict__ items,
+                              int nitems, int parity) {
+    extern __shared__ unsigned char smem_raw[];
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const BatchItem w = items[it];
+    const BatchTmaLattice* l = lats + w.lat;
+    const LatticeArgs<float> a = l->a[parity];
+    if (threadIdx.x == 0) tma_prefetch_map(&l->map[parity]);
+    if (l->wide) {
+        TmaSmem<64, 4, S> sm(smem_raw);
+        sm.init_barriers();
+        tma_item<64, 4, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+    } else {
+        TmaSmem<32, 8, S> sm(smem_raw);
+        sm.init_barriers();
+        tma_item<32, 8, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+    }
 }
 
 }  // namespace lbmsc

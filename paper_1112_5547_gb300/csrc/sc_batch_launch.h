@@ -18,12 +18,22 @@ struct BatchItem {
 // 3 stages, D3Q19 with FP32 storage, lattices at least one tile wide in x and
 // y).  Tiles 0-4 run persistent grids over an atomic work counter; 5 = 32x8
 // and 6 = 64x4 TMA-fed, 7 = 32x8 and 8 = 64x4 z-marching launch one CTA per
-// work item and leave the order to the hardware's block scheduler.
-constexpr int kNumBatchTiles = 9;
-constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64};
-constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4};
-constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true, false, false};
-constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true, true, true};
+// work item and leave the order to the hardware's block scheduler; 9 = TMA-fed,
+// one CTA per item, with each lattice's own tile: 64x4 for lattices at least
+// 64 wide, else 32x8 (kBatchTileX/Y give the narrow one).
+constexpr int kNumBatchTiles = 10;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8};
+constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true, false, false, true};
+constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true, true, true, true};
+constexpr int kBatchTileMixed = 9;
+
+// The tile of one lattice's items in a batch of this tile kind.
+inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
+    const bool wide = tile == kBatchTileMixed && p.nx >= 64;
+    tx = wide ? 64 : kBatchTileX[tile];
+    ty = wide ? 4 : kBatchTileY[tile];
+}
 
 inline bool batch_tile_fits(int tile, const Plan& p) {
     if (tile < 0 || tile >= kNumBatchTiles) return false;

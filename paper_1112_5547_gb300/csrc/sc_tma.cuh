@@ -216,7 +216,10 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
 
     auto ring = sm.ring;
     uint64_t* const bars = sm.bars;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    // linear thread id: the tile shape need not be the block shape (the mixed
+    // batch kernel runs 64x4 and 32x8 items in 256-thread blocks)
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int z1 = min(z0 + a.zchunk, nz);
     const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1

@@ -52,9 +52,10 @@ EXPORTS = (
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
 # take D3Q19 lattices with FP32 storage at least one tile wide in x and y.
 # Persistent grids over an atomic work counter, or (GRID) one CTA per work item.
-BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4))
-BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False)
-BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True)
+# Tile 9 gives each lattice its own tile: 64x4 when it is at least 64 wide, else 32x8.
+BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8))
+BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True)
+BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True)
 
 
 def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
