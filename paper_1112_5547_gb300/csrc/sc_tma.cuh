@@ -1,4 +1,4 @@
-// TMA-fed D3Q19 step for FP32 storage.
+// TMA-fed D3Q19 step (FP32 storage, or 16-bit storage decoded on the pull).
 //
 // Same per-node arithmetic and order as the other step kernels (sc_node.cuh:
 // Eq. eq:be with the force of Eq. FORCE, paper Sec. 2.1), so results are
@@ -11,13 +11,14 @@
 //     y from y0 - 1 - c_y to y0 + TY - c_y,  z = plane - c_z (periodic).
 // The pulled value of frame node (fx, fy) (frame (1, 1) = tile (0, 0)) is then
 // box[fy][fx + 3 - c_x]: every pull, for the tile and for its one-node halo
-// ring, is a shared-memory load at a constant offset.  S stages keep S - 1
-// planes of copies in flight.
+// ring, is a shared-memory load at a constant offset (16-bit storage: boxes
+// of TX + 16 values from x0 - 8, same rule with 7 for 3).
 //
-// Per plane q: wait for its copies; read the own node's 38 pulls into
-// registers and write own and halo densities to the four-slot ring;
-// one barrier (ring complete, stage q free); the elected thread refills the
-// stage with plane q + S; collide plane q - 1 from registers and store.
+// Per plane q: wait for plane q's copies; read the own node's 38 pulls into
+// registers and write own and halo densities to the four-slot ring; one
+// barrier (ring complete, stage q read); the elected thread refills a stage;
+// collide plane q - 1 from registers and store.  The refill schedule (which
+// stage, before or after the wait) depends on the storage type, see tma_item.
 // Every mbarrier wait is bounded: on expiry the CTA raises the error word,
 // waits (bounded) for its copies still in flight and leaves (the host reports
 // LBM_ERR_TIMEOUT).  tma_item is the per-item pipeline; the solo kernel runs
@@ -188,7 +189,7 @@ __device__ __forceinline__ float tma_pulled(const unsigned char* sb, int s, int 
 }
 
 // The item a CTA runs after the current one (batch kernels): the elected
-// thread issues its first S planes into the stages the current item frees,
+// thread issues its first planes into the stages the current item frees,
 // so the pipeline does not drain between items.
 struct TmaNext {
     const CUtensorMap* map;
@@ -198,7 +199,7 @@ struct TmaNext {
 // One work item through the plane pipeline: the TX x TY tile at (x0, y0),
 // planes z0 .. min(z0 + zchunk, nz) - 1.  qbase counts the planes this CTA
 // pushed through its stages before (the mbarrier phases continue from there).
-// preissued: the item's first S planes were issued by the previous item (as
+// preissued: the item's first planes were issued by the previous item (as
 // its TmaNext; FP32 batch kernel only).  Every thread returns the number of
 // planes the item used, or -1 if a wait was lost (the error word is then
 // raised, and the copies still in flight have been waited for, again with a
@@ -225,9 +226,18 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
     const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
     const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
-    const bool halo = tid < H;
+    // Two issue schedules, measured per storage type at 512^3: FP32 refills a
+    // stage right after the barrier that frees it (S planes in flight ahead,
+    // 8.34 ms per step against 8.58 for the other schedule); 16-bit storage
+    // refills the stage of plane q - 1 before waiting for plane q (S - 1 planes
+    // ahead; 9.80 against 10.24 ms for the rest-offset mode), with the halo
+    // ring pulled by the last H threads so that warp 0, whose first thread
+    // issues the copies, carries no second pull.
+    constexpr bool kEarly = sizeof(St) == 2;
+    const int hid = kEarly ? tid - (TX * TY - H) : tid;  // halo cell index in [0, H) for halo threads
+    const bool halo = hid >= 0 && hid < H;
     int hfx, hfy;
-    halo_cell<TX, TY>(tid, hfx, hfy);
+    halo_cell<TX, TY>(halo ? hid : 0, hfx, hfy);
 
     auto zof = [&](int q) {
         const int z = z0 - 1 + q;
@@ -248,8 +258,13 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
         return true;
     };
 
+    // early schedule: planes 0 .. S-2 go out now and body(q) issues plane
+    // q + S - 1 into the stage plane q - 1 used (read by every thread before
+    // the barrier of body(q - 1)); late schedule: planes 0 .. S-1 now, and
+    // body(q) refills plane q's stage with plane q + S after its barrier
+    constexpr int kAhead = kEarly ? S - 1 : S;
     if (issuer && !preissued)
-        for (int q = 0; q < S && q < nplanes; ++q) issue(q);
+        for (int q = 0; q < kAhead && q < nplanes; ++q) issue(q);
 
     bool lost = false;
     // own pulls of plane q into X; own and halo densities into ring slot q % 4
@@ -289,6 +304,18 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
     auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> int {
         if (q >= nplanes) return 1;
+        if (kEarly && issuer) {
+            // before the wait: the issuing warp's copy instructions overlap the
+            // other warps' halo pulls instead of delaying everyone's collision
+            const int r = q + S - 1;
+            if (r < nplanes) {
+                issue(r);
+            } else if (r - nplanes < nxt.nplanes) {
+                fence_proxy_async_smem();
+                tma_issue_plane<TX, TY, S, St>(nxt.map, nullptr, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz,
+                                               r - nplanes, qbase + r, sm);
+            }
+        }
         if (!try_plane(q)) lost = true;
         take_plane(q, Xc);
         if (__syncthreads_or(lost)) {
@@ -296,18 +323,19 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
                 atomicExch(err, 1);
                 // drain: wait (bounded) for the planes issued from q on (the
                 // next item's first planes included)
-                const int last = nxt.nplanes > 0 ? nplanes + min(S, nxt.nplanes) : nplanes;
+                const int last = nxt.nplanes > 0 ? nplanes + min(kAhead, nxt.nplanes) : nplanes;
                 for (int r = q; r < last && r < q + S; ++r) try_plane(r);
             }
             return -1;
         }
-        if (issuer) {
-            if (q + S < nplanes) {
-                issue(q + S);  // the stage's reads by every thread precede the barrier above
-            } else if (q + S - nplanes < nxt.nplanes) {
+        if (!kEarly && issuer) {
+            const int r = q + S;  // into the stage plane q was read from, before the barrier above
+            if (r < nplanes) {
+                issue(r);
+            } else if (r - nplanes < nxt.nplanes) {
                 fence_proxy_async_smem();
                 tma_issue_plane<TX, TY, S, St>(nxt.map, nullptr, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz,
-                                               q + S - nplanes, qbase + q + S, sm);
+                                               r - nplanes, qbase + r, sm);
             }
         }
         if (q >= 2) collide(q - 1, Xp);
