@@ -300,15 +300,24 @@ def serve_compare(n: int, rate: float, seed: int = 4):
             "same_steps_as_alone": all(a.steps == b.steps for a, b in zip(res, sres))}
 
 
+def workload_config(L: int, prec: str, world: int) -> dict:
+    """The config object of the JSON line (shared by both arms)."""
+    N = L ** 3
+    return {"workload": "D3Q19 %d^3 two-component SC drop R=L/4, tau=1, G*rho_tot=2.4, seed 2" % L,
+            "lattice": "D3Q19", "L": L, "nodes": N, "storage": prec,
+            "l2": "inputs larger than L2 (%.1f GB per population buffer)" % (N * 38 * BYTES_PER_VALUE[prec] / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
     cb = cpu_baseline(max(5.0, args.cpu_seconds))
     line = {"impl": "reference", "metric": "2-comp SC D3Q19 MLUPS & HBM roofline %", "value": cb["value"],
             "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": args.L ** 3 / (cb["value"] * 1e6) * 1e3,  # at the oracle's sampled rate
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "D3Q19 %d^3 SC drop R=L/4 (oracle sample at 128^3)" % args.L,
-                                            "lattice": "D3Q19", "L": args.L},
+            "data": "synthetic", "config": workload_config(args.L, args.precision, world),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -465,10 +474,7 @@ def main():
         "vs_baseline": None,
         "dtype": DTYPE_NAME[prec],
         "data": "synthetic",
-        "config": {"workload": "D3Q19 %d^3 two-component SC drop R=L/4, tau=1, G*rho_tot=2.4, seed 2" % L,
-                   "lattice": "D3Q19", "L": L, "nodes": N, "storage": prec,
-                   "l2": "inputs larger than L2 (%.1f GB per population buffer)" % (N * 38 * BYTES_PER_VALUE[prec] / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU", "step_launch": tune_info},
+        "config": dict(workload_config(L, prec, world), step_launch=tune_info),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_lu": bpl,
