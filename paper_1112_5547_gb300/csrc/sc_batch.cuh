@@ -166,40 +166,55 @@ __global__ void __launch_bounds__(TX* TY, 1)
     TmaSmem<TX, TY, S> sm(smem_raw);
     const int tid = threadIdx.y * TX + threadIdx.x;
     BatchQueue queue{ctr, &s_next, 0};
-    queue.fetch(tid);
+    queue.fetch(tid);  // the first item
     sm.init_barriers();  // (ends with a CTA barrier)
     unsigned qbase = 0;
     bool preissued = false;
+    // The next item is taken from the counter a few planes before the end of
+    // the current one, not at its start: items then start in the order earlier
+    // ones finish, as with the hardware block scheduler, and neighbouring
+    // tiles stay in flight together (taking it a whole item ahead let the CTAs
+    // drift apart and lose the halo rows they share in L2).
+    int nit = 0;
+    BatchItem wn{0, 0, 0, 0};
+    TmaNext nxt{nullptr, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
     for (;;) {
         const int it = s_next;
         if (it >= nitems) break;
         __syncthreads();  // every thread has read s_next
-        queue.fetch(tid);
         const BatchItem w = items[it];
         const BatchTmaLattice* l = lats + w.lat;
         const LatticeArgs<float> a = l->a[parity];
-        TmaNext nxt{nullptr, 0, 0, 0, 0, 0, 0, 0};
-        if (tid == 0) {
-            if (!preissued) tma_prefetch_map(&l->map[parity]);
-            const int nit = s_next;  // written by this thread's fetch
-            if (nit < nitems) {
-                const BatchItem wn = items[nit];
-                const BatchTmaLattice* ln = lats + wn.lat;
-                const LatticeArgs<float>& an = ln->a[parity];
-                nxt.map = &ln->map[parity];
-                tma_prefetch_map(nxt.map);
-                nxt.x0 = wn.x0;
-                nxt.y0 = wn.y0;
-                nxt.z0 = wn.z0;
-                nxt.gxo = an.gxo;
-                nxt.gyo = an.gyo;
-                nxt.nz = an.nz;
-                nxt.nplanes = min(wn.z0 + an.zchunk, an.nz) - wn.z0 + 2;
+        if (tid == 0 && !preissued) tma_prefetch_map(&l->map[parity]);
+        nxt.nplanes = 0;
+        // elected thread, at the start of plane q: take the next index three
+        // planes before the pre-issue, read its item two before, its lattice one
+        // before (each load has a plane of time to land)
+        auto hook = [&](int q, int np) {
+            const int pre = np - S;  // plane whose barrier is followed by the first pre-issue
+            // (one CTA per item, ctr null: the static order, which ends the loop)
+            if (q == max(0, pre - 3)) nit = ctr ? atomicAdd(&ctr[0], 1) : it + (int)gridDim.x;
+            if (q == max(0, pre - 2) && nit < nitems) wn = items[nit];
+            if (q == max(0, pre - 1)) {
+                s_next = nit;  // visible to every thread after the end-of-item barrier
+                if (nit < nitems) {
+                    const BatchTmaLattice* ln = lats + wn.lat;
+                    const LatticeArgs<float>& an = ln->a[parity];
+                    nxt.map = &ln->map[parity];
+                    tma_prefetch_map(nxt.map);
+                    nxt.x0 = wn.x0;
+                    nxt.y0 = wn.y0;
+                    nxt.z0 = wn.z0;
+                    nxt.gxo = an.gxo;
+                    nxt.gyo = an.gyo;
+                    nxt.nz = an.nz;
+                    nxt.nplanes = min(wn.z0 + an.zchunk, an.nz) - wn.z0 + 2;
+                }
             }
-        }
-        const int n =
-            tma_item<TX, TY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, qbase, sm, l->err, preissued, nxt);
+        };
+        const int n = tma_item<TX, TY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, qbase, sm, l->err,
+                                          preissued, &nxt, hook);
         if (n < 0) break;  // a lost wait: the lattice's error word is raised
         qbase += (unsigned)n;
         // the next item's first planes went out with this one (the elected

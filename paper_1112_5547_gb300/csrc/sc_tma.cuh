@@ -196,6 +196,13 @@ struct TmaNext {
     int x0, y0, z0, gxo, gyo, nz, nplanes;  // nplanes = 0: no next item
 };
 
+// Called by the elected thread at the start of every plane of an item (plane
+// q of nplanes); the persistent batch kernel uses it to take its next work
+// item late in the current one and fill the TmaNext before the pre-issue.
+struct TmaNoHook {
+    __device__ __forceinline__ void operator()(int, int) const {}
+};
+
 // One work item through the plane pipeline: the TX x TY tile at (x0, y0),
 // planes z0 .. min(z0 + zchunk, nz) - 1.  qbase counts the planes this CTA
 // pushed through its stages before (the mbarrier phases continue from there).
@@ -204,11 +211,11 @@ struct TmaNext {
 // planes the item used, or -1 if a wait was lost (the error word is then
 // raised, and the copies still in flight have been waited for, again with a
 // bound).  The caller must synchronise the CTA between two items.
-template <int TX, int TY, int S, class St = float>
+template <int TX, int TY, int S, class St = float, class Hook = TmaNoHook>
 __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorMap* rmap, const LatticeArgs<St>& a,
                                         int x0, int y0, int z0, unsigned qbase, const TmaSmem<TX, TY, S, St>& sm,
-                                        int* __restrict__ err, bool preissued = false,
-                                        const TmaNext nxt = TmaNext{nullptr, 0, 0, 0, 0, 0, 0, 0}) {
+                                        int* __restrict__ err, bool preissued = false, const TmaNext* nxt = nullptr,
+                                        Hook hook = Hook()) {
     using L = D3Q19;
     using T = TmaTile<TX, TY, S, St>;
     using C = float;
@@ -304,15 +311,16 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
     auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> int {
         if (q >= nplanes) return 1;
+        if (issuer) hook(q, nplanes);
         if (kEarly && issuer) {
             // before the wait: the issuing warp's copy instructions overlap the
             // other warps' halo pulls instead of delaying everyone's collision
             const int r = q + S - 1;
             if (r < nplanes) {
                 issue(r);
-            } else if (r - nplanes < nxt.nplanes) {
+            } else if (nxt && r - nplanes < nxt->nplanes) {
                 fence_proxy_async_smem();
-                tma_issue_plane<TX, TY, S, St>(nxt.map, nullptr, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz,
+                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0, nxt->z0, nxt->gxo, nxt->gyo, nxt->nz,
                                                r - nplanes, qbase + r, sm);
             }
         }
@@ -323,7 +331,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
                 atomicExch(err, 1);
                 // drain: wait (bounded) for the planes issued from q on (the
                 // next item's first planes included)
-                const int last = nxt.nplanes > 0 ? nplanes + min(kAhead, nxt.nplanes) : nplanes;
+                const int last = nxt && nxt->nplanes > 0 ? nplanes + min(kAhead, nxt->nplanes) : nplanes;
                 for (int r = q; r < last && r < q + S; ++r) try_plane(r);
             }
             return -1;
@@ -332,9 +340,9 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
             const int r = q + S;  // into the stage plane q was read from, before the barrier above
             if (r < nplanes) {
                 issue(r);
-            } else if (r - nplanes < nxt.nplanes) {
+            } else if (nxt && r - nplanes < nxt->nplanes) {
                 fence_proxy_async_smem();
-                tma_issue_plane<TX, TY, S, St>(nxt.map, nullptr, nxt.x0, nxt.y0, nxt.z0, nxt.gxo, nxt.gyo, nxt.nz,
+                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0, nxt->z0, nxt->gxo, nxt->gyo, nxt->nz,
                                                r - nplanes, qbase + r, sm);
             }
         }
