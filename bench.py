@@ -235,23 +235,21 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     return out
 
 
-def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: str = "bf16_rest",
-                      tile: int = 30, zchunk: int = 64):
+def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: str = "bf16_rest"):
     """The same D3Q19 drop step with 16-bit rest-offset storage (FP32 arithmetic):
     MLUPS and the HBM roofline of its 168 algorithmic bytes per LU, timed like
     the headline step (CUDA events on the lattice's stream, inputs far larger
-    than L2).  Launch shape fixed to the TMA-fed 16-bit kernel, tile 64x4 in
-    1x2 clusters, 64-plane chunks (the fastest measured at 512^3)."""
+    than L2).  Launch shape from the tuning cache (autotuned on GB300), else
+    autotuned here."""
     import torch
-    from paper_1112_5547_gb300 import lbm_sc
+    from paper_1112_5547_gb300 import autotune, lbm_sc
     st = torch.cuda.Stream()
     G = G_RHO / (RHO_HI + RHO_LO)
     rA, rB = drop_fields(L, np.float32, seed=2)
     with torch.cuda.stream(st):
         lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st).init(rA, rB)
         del rA, rB
-        if lat.tile_fits(tile):
-            lat.set_tuning(tile, zchunk)
+        autotune.tuned(lat, store=False)
         lat.step(warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)

@@ -133,7 +133,11 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * whose tile counts divide by the cluster shape); 30 = 64x4 in 1x2 clusters
  * with 3 stages, 31 = the same with 4 stages, 32 = 32x8 with 3 stages (the
  * TMA-fed kernel for the four 16-bit storage precisions, same size rules; the
- * rest-offset ones also stage the FP32 densities).  zchunk is the number
+ * rest-offset ones also stage the FP32 densities); 33 = 64x6 with 2 stages in
+ * 1x2 clusters, 34 = the same without clusters (FP32, 384 threads: 12 warps
+ * per SM), 35 = 64x6 with 3 stages in 1x2 clusters (16-bit), 36 = 32x12 with
+ * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
+ * with 3 stages in 1x2 clusters (16-bit).  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {

@@ -161,7 +161,9 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
                       kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kTiles[26].promo == 2 &&
                       kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kTiles[30].kind == 6 &&
-                      kTiles[31].stages == 4 && kTiles[32].tx == 32 && kNumTiles == 33,
+                      kTiles[31].stages == 4 && kTiles[32].tx == 32 && kTiles[33].ty == 6 && kTiles[34].stages == 2 &&
+                      kTiles[35].kind == 6 && kTiles[36].ty == 12 && kTiles[37].cy == 1 && kTiles[38].kind == 6 &&
+                      kNumTiles == 39,
                   "tile table and dispatch disagree");
     if constexpr (Codec<S>::kRest) {
         // rest-offset storage: the kernels that pull through pull_node
@@ -178,6 +180,8 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
             case 30: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
             case 31: return TmaLaunch<L, S, 64, 4, 4>::run(p, a, st);
             case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+            case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
+            case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
         }
         return cudaErrorInvalidValue;
     } else {
@@ -220,6 +224,10 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
             case 28:
             case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+            case 33:
+            case 34: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
+            case 36:
+            case 37: return TmaLaunch<L, S, 32, 12, 2>::run(p, a, st);
         }
     }
     if constexpr (sizeof(S) == 2) {
@@ -227,6 +235,8 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 30: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
             case 31: return TmaLaunch<L, S, 64, 4, 4>::run(p, a, st);
             case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
+            case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
+            case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
         }
     }
     return cudaErrorInvalidValue;

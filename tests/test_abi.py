@@ -104,7 +104,8 @@ def test_tuning_validation(lib):
         for t in range(len(lib.TILES)):
             tx, ty = lib.TILES[t]
             cx, cy = lib.TILE_CLUSTER[t]
-            fits = lib.TILE_KIND[t] != 5 or (64 >= tx and 8 >= ty and (64 // tx) % cx == 0 and (8 // ty) % cy == 0)
+            # TMA tiles: at least one tile in x and y, tile counts (ragged tiles included) divisible by the cluster
+            fits = lib.TILE_KIND[t] != 5 or (64 >= tx and 8 >= ty and -(-64 // tx) % cx == 0 and -(-8 // ty) % cy == 0)
             fits = fits and lib.TILE_KIND[t] != 6  # 16-bit storage only
             if not fits:
                 with pytest.raises(lib.LbmError):

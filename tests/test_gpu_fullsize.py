@@ -120,18 +120,22 @@ def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4):
         assert np.abs(gu - ou).max() <= tol_u, (pt, gu, ou)
 
 
-@pytest.mark.parametrize("precision,tile,tol_rho,tol_u", [("f32", 22, 1e-5, 1e-6), ("bf16_rest", 30, 2e-4, 2e-4)])
-def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tile, tol_rho, tol_u):
-    """The bench's 512^3 drop in the bench's launch shape (tile 22: TMA 64x4, 1x2
-    clusters, 64-plane chunks; tile 30 for the 16-bit line)."""
+@pytest.mark.parametrize("precision,tol_rho,tol_u", [("f32", 1e-5, 1e-6), ("bf16_rest", 2e-4, 2e-4)])
+def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tol_rho, tol_u):
+    """The bench's 512^3 drop in the bench's launch shape (the tuning cache's
+    entry, which bench.py uses), and in the previous headline shape (TMA 64x4,
+    1x2 clusters, 64-plane chunks; tile 22, or 30 for the 16-bit line)."""
     import torch
+    from paper_1112_5547_gb300 import autotune
     L = 512
     rA, rB = inputs.drop((L, L, L), L / 4, seed=2, dtype=np.float32)
     lat = sc.Lattice(1, (L, L, L), 1.0, 1.0, G0, precision).init(rA, rB)
     del rA, rB
-    lat.set_tuning(tile, 64)
-    assert lat.tuning() == (tile, 64)
-    _check_sampled(sc, oracle_mod, lat, _samples(L), tol_rho, tol_u)
+    (tile, zc), _ = autotune.tuned(lat, store=False)
+    tx, ty = sc.TILES[tile]
+    _check_sampled(sc, oracle_mod, lat, _samples(L, (tx, ty), zc), tol_rho, tol_u)
+    lat.set_tuning(22 if precision == "f32" else 30, 64)
+    _check_sampled(sc, oracle_mod, lat, _samples(L, n_random=4, seed=8), tol_rho, tol_u, steps_before=1)
     d = lat.diagnostics()
     assert d["status"] == sc.LBM_OK
     del lat
