@@ -137,7 +137,9 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * 1x2 clusters, 34 = the same without clusters (FP32, 384 threads: 12 warps
  * per SM), 35 = 64x6 with 3 stages in 1x2 clusters (16-bit), 36 = 32x12 with
  * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
- * with 3 stages in 1x2 clusters (16-bit).  zchunk is the number
+ * with 3 stages in 1x2 clusters (16-bit), 39 = 64x8 with 2 stages in 1x2
+ * clusters (16-bit, 512 threads), 40 = 48x8 with 2 stages in 1x2 clusters,
+ * 41 = the same without clusters (FP32).  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {
@@ -274,7 +276,9 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  *           5 = 32x8, 6 = 64x4 (TMA-fed) and 7 = 32x8, 8 = 64x4 (z-marching)
  *           launch one CTA per work item instead; 9 = TMA-fed, one CTA per
  *           item, each lattice with its own tile: 64x4 if it is at least 64
- *           wide, else 32x8 (same requirements as 5)
+ *           wide, else 32x8 (same requirements as 5); 10 = 32x12 and 11 =
+ *           64x6 / 32x12 per lattice, the same with 384-thread CTAs (every
+ *           lattice at least 32 x 12)
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

@@ -12,6 +12,7 @@ import os
 import shutil
 import subprocess
 import sys
+import time
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -65,6 +66,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
+    # the library is stamped with the time the build started, so a source
+    # edited while it compiles is newer and triggers the next build
+    t_start = time.time()
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, srcs))
@@ -74,6 +78,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    os.utime(LIB, (t_start, t_start))
     return LIB
 
 

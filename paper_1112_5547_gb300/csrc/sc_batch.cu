@@ -49,25 +49,26 @@ cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitem
     return cudaGetLastError();
 }
 
+template <int WX, int WY, int NX, int NY, int S>
 cudaError_t launch_batch_tma_mixed(const void* lats, const BatchItem* items, int nitems, int parity,
                                    cudaStream_t st) {
-    constexpr int S = 3;
-    constexpr size_t smem = TmaTile<64, 4, S>::smem_bytes > TmaTile<32, 8, S>::smem_bytes
-                                ? TmaTile<64, 4, S>::smem_bytes
-                                : TmaTile<32, 8, S>::smem_bytes;
-    auto kern = sc_batch_tma_mixed_kernel<S>;
+    constexpr size_t smem = TmaTile<WX, WY, S>::smem_bytes > TmaTile<NX, NY, S>::smem_bytes
+                                ? TmaTile<WX, WY, S>::smem_bytes
+                                : TmaTile<NX, NY, S>::smem_bytes;
+    auto kern = sc_batch_tma_mixed_kernel<WX, WY, NX, NY, S>;
     static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     if (nitems < 1) return cudaSuccess;
-    kern<<<(unsigned)nitems, 256, smem, st>>>(static_cast<const BatchTmaLattice*>(lats), items, nitems, parity);
+    kern<<<(unsigned)nitems, WX * WY, smem, st>>>(static_cast<const BatchTmaLattice*>(lats), items, nitems, parity);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
                         int* ctr, cudaStream_t st) {
-    static_assert(kNumBatchTiles == 10 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
-                      !kBatchTileTma[7] && kBatchTileY[8] == 4 && kBatchTileMixed == 9,
+    static_assert(kNumBatchTiles == 12 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
+                      !kBatchTileTma[7] && kBatchTileY[8] == 4 && kBatchTileMixed == 9 && kBatchTileY[10] == 12 &&
+                      kBatchTileMixed384 == 11,
                   "batch tile table and dispatch disagree");
     switch (tile) {
         case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, false, st);
@@ -82,7 +83,9 @@ cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int 
             case 4: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, false, st);
             case 5: return launch_batch_tma<32, 8, 3>(lats, items, nitems, parity, sm_count, ctr, true, st);
             case 6: return launch_batch_tma<64, 4, 3>(lats, items, nitems, parity, sm_count, ctr, true, st);
-            case 9: return launch_batch_tma_mixed(lats, items, nitems, parity, st);
+            case 9: return launch_batch_tma_mixed<64, 4, 32, 8, 3>(lats, items, nitems, parity, st);
+            case 10: return launch_batch_tma<32, 12, 2>(lats, items, nitems, parity, sm_count, ctr, true, st);
+            case 11: return launch_batch_tma_mixed<64, 6, 32, 12, 2>(lats, items, nitems, parity, st);
         }
     }
     return cudaErrorInvalidValue;
@@ -148,7 +151,7 @@ cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, in
         bl.err = p.err;
         int tx, ty;
         batch_item_tile(tile, p, tx, ty);
-        bl.wide = tx == 64 && ty == 4 ? 1 : 0;
+        bl.wide = tx == 64 ? 1 : 0;
         memcpy(dst, &bl, sizeof(bl));
         return cudaSuccess;
     }

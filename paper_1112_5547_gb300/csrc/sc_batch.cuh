@@ -225,14 +225,15 @@ __global__ void __launch_bounds__(TX* TY, 1)
     queue.retire(tid);
 }
 
-// Mixed-shape TMA batch step, one CTA of 256 threads per work item: items of
-// lattices at least 64 wide run as 64x4 tiles (fewer halo rows and boxes
-// re-read per node), the others as 32x8 tiles; the shared memory holds the
-// larger of the two layouts.
-template <int S>
-__global__ void __launch_bounds__(256, 1)
+// Mixed-shape TMA batch step, one CTA per work item: items of lattices at
+// least WX wide run as WX x WY tiles (fewer halo rows and boxes re-read per
+// node), the others as NX x NY tiles of the same thread count; the shared
+// memory holds the larger of the two layouts.
+template <int WX, int WY, int NX, int NY, int S>
+__global__ void __launch_bounds__(WX* WY, 1)
     sc_batch_tma_mixed_kernel(const BatchTmaLattice* __restrict__ lats, const BatchItem* __restrict__ items,
                               int nitems, int parity) {
+    static_assert(WX * WY == NX * NY, "both tile shapes use the same block");
     extern __shared__ unsigned char smem_raw[];
     const int it = blockIdx.x;
     if (it >= nitems) return;
@@ -241,13 +242,13 @@ __global__ void __launch_bounds__(256, 1)
     const LatticeArgs<float> a = l->a[parity];
     if (threadIdx.x == 0) tma_prefetch_map(&l->map[parity]);
     if (l->wide) {
-        TmaSmem<64, 4, S> sm(smem_raw);
+        TmaSmem<WX, WY, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<64, 4, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<WX, WY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
     } else {
-        TmaSmem<32, 8, S> sm(smem_raw);
+        TmaSmem<NX, NY, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<32, 8, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<NX, NY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
     }
 }
 

@@ -20,19 +20,25 @@ struct BatchItem {
 // and 6 = 64x4 TMA-fed, 7 = 32x8 and 8 = 64x4 z-marching launch one CTA per
 // work item and leave the order to the hardware's block scheduler; 9 = TMA-fed,
 // one CTA per item, with each lattice's own tile: 64x4 for lattices at least
-// 64 wide, else 32x8 (kBatchTileX/Y give the narrow one).
-constexpr int kNumBatchTiles = 10;
-constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32};
-constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8};
-constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true, false, false, true};
-constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true, true, true, true};
+// 64 wide, else 32x8 (kBatchTileX/Y give the narrow one); with 384 threads
+// (12 warps per SM, 2 stages): 10 = 32x12 TMA-fed one CTA per item, 11 = the
+// mixed form with 64x6 and 32x12.
+constexpr int kNumBatchTiles = 12;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32, 32, 32};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8, 12, 12};
+constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true,
+                                                false, false, true, true, true};
+constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true,
+                                                 true, true, true, true, true};
 constexpr int kBatchTileMixed = 9;
+constexpr int kBatchTileMixed384 = 11;
 
 // The tile of one lattice's items in a batch of this tile kind.
 inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
-    const bool wide = tile == kBatchTileMixed && p.nx >= 64;
+    const bool mixed = tile == kBatchTileMixed || tile == kBatchTileMixed384;
+    const bool wide = mixed && p.nx >= 64;
     tx = wide ? 64 : kBatchTileX[tile];
-    ty = wide ? 4 : kBatchTileY[tile];
+    ty = wide ? (tile == kBatchTileMixed ? 4 : 6) : kBatchTileY[tile];
 }
 
 inline bool batch_tile_fits(int tile, const Plan& p) {

@@ -163,7 +163,7 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kTiles[30].kind == 6 &&
                       kTiles[31].stages == 4 && kTiles[32].tx == 32 && kTiles[33].ty == 6 && kTiles[34].stages == 2 &&
                       kTiles[35].kind == 6 && kTiles[36].ty == 12 && kTiles[37].cy == 1 && kTiles[38].kind == 6 &&
-                      kNumTiles == 39,
+                      kTiles[39].ty == 8 && kTiles[40].tx == 48 && kTiles[41].cy == 1 && kNumTiles == 42,
                   "tile table and dispatch disagree");
     if constexpr (Codec<S>::kRest) {
         // rest-offset storage: the kernels that pull through pull_node
@@ -182,6 +182,7 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
             case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
             case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
             case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
+            case 39: return TmaLaunch<L, S, 64, 8, 2>::run(p, a, st);
         }
         return cudaErrorInvalidValue;
     } else {
@@ -228,6 +229,8 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 34: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
             case 36:
             case 37: return TmaLaunch<L, S, 32, 12, 2>::run(p, a, st);
+            case 40:
+            case 41: return TmaLaunch<L, S, 48, 8, 2>::run(p, a, st);
         }
     }
     if constexpr (sizeof(S) == 2) {
@@ -237,6 +240,7 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 32: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
             case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
             case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
+            case 39: return TmaLaunch<L, S, 64, 8, 2>::run(p, a, st);
         }
     }
     return cudaErrorInvalidValue;

@@ -63,7 +63,7 @@ constexpr int kTY = 8;
 //         modes also stage boxes of the FP32 node densities).
 //         promo: L2 promotion of the tensor copies (0 none, 1 64 B, 2 128 B, 3 256 B).
 struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3; };
-constexpr int kNumTiles = 39;
+constexpr int kNumTiles = 42;
 constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
     {32, 8, 1, 3},       {32, 8, 1, 4},       {64, 4, 1, 3},       {32, 8, 2, 0},       {64, 4, 2, 0},
@@ -73,7 +73,7 @@ constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 5, 3, 2, 2}, {64, 4, 5, 3, 1, 2, 2}, {64, 4, 5, 3, 1, 2, 0}, {32, 8, 5, 3, 1, 1, 2},
     {32, 8, 5, 3, 1, 1, 0}, {64, 4, 6, 3, 1, 2}, {64, 4, 6, 4, 1, 2}, {32, 8, 6, 3},
     {64, 6, 5, 2, 1, 2}, {64, 6, 5, 2},       {64, 6, 6, 3, 1, 2}, {32, 12, 5, 2, 1, 2}, {32, 12, 5, 2},
-    {32, 12, 6, 3, 1, 2}};
+    {32, 12, 6, 3, 1, 2}, {64, 8, 6, 2, 1, 2}, {48, 8, 5, 2, 1, 2}, {48, 8, 5, 2}};
 
 inline bool tile_supported(int tile, int lattice, int precision) {
     if (tile < 0 || tile >= kNumTiles) return false;

@@ -52,10 +52,12 @@ EXPORTS = (
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
 # take D3Q19 lattices with FP32 storage at least one tile wide in x and y.
 # Persistent grids over an atomic work counter, or (GRID) one CTA per work item.
-# Tile 9 gives each lattice its own tile: 64x4 when it is at least 64 wide, else 32x8.
-BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8))
-BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True)
-BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True)
+# Tile 9 gives each lattice its own tile: 64x4 when it is at least 64 wide, else 32x8;
+# tiles 10 (32x12) and 11 (64x6 / 32x12 per lattice) run 384-thread CTAs.
+BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (32, 12),
+               (32, 12))
+BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True, True, True)
+BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True, True, True)
 
 
 def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
@@ -78,14 +80,15 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
 TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
          (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
          (64, 4), (64, 4), (64, 4), (32, 8), (64, 4), (64, 4),
-         (32, 8), (32, 8), (64, 4), (64, 4), (32, 8), (64, 6), (64, 6), (64, 6), (32, 12), (32, 12), (32, 12))
-TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 5, 5, 6, 5, 5, 6)
-TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 4, 3, 2, 2, 3, 2, 2, 3)
+         (32, 8), (32, 8), (64, 4), (64, 4), (32, 8), (64, 6), (64, 6), (64, 6), (32, 12), (32, 12), (32, 12),
+         (64, 8), (48, 8), (48, 8))
+TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 5, 5, 6, 5, 5, 6, 6, 5, 5)
+TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 4, 3, 2, 2, 3, 2, 2, 3, 2, 2, 2)
 # thread-block cluster of the TMA tiles (tiles in x, tiles in y)
 TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1), (1, 2), (1, 2),
-                                   (1, 1), (1, 2), (1, 1), (1, 2), (1, 2), (1, 1), (1, 2))
+                                   (1, 1), (1, 2), (1, 1), (1, 2), (1, 2), (1, 1), (1, 2), (1, 2), (1, 2), (1, 1))
 # L2 promotion (bytes fetched per L2 miss) of the TMA tiles' tensor copies
-TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0) + (256,) * 9
+TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0) + (256,) * 12
 
 
 def tile_supported(tile: int, lattice: int, precision: int) -> bool:

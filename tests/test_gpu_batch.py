@@ -32,6 +32,9 @@ MIX3_TMA = [((40, 20, 64), 1.0, 1.0, G0), ((17, 33, 70), 0.8, 1.3, 2.0), ((64, 4
 # TMA-fed tiles of both widths in one batch (tile 9: 64x4 for nx >= 64, else 32x8)
 MIX3_MIXED = [((40, 20, 48), 1.0, 1.0, G0), ((17, 33, 70), 0.8, 1.3, 2.0), ((20, 16, 32), 1.1, 0.9, 2.2),
               ((33, 65, 65), 1.2, 1.2, 1.6), ((9, 8, 128), 1.0, 1.0, G0)]
+# every lattice at least 32 x 12: the 384-thread batch tiles (10: 32x12; 11: 64x6 or 32x12 per lattice)
+MIX3_TALL = [((40, 20, 48), 1.0, 1.0, G0), ((17, 33, 70), 0.8, 1.3, 2.0), ((20, 16, 32), 1.1, 0.9, 2.2),
+             ((33, 65, 65), 1.2, 1.2, 1.6), ((9, 12, 128), 1.0, 1.0, G0)]
 MIX2 = [((64, 64), 1.0, 1.0, G0), ((37, 50), 0.8, 1.3, 2.0), ((7, 130), 1.0, 1.0, 2.2), ((96, 33), 1.1, 0.9, G0)]
 
 
@@ -62,7 +65,7 @@ def _assert_same(a, b, what):
 @pytest.mark.parametrize("lattice,mix,precision", [(1, MIX3, "f32"), (0, MIX2, "f64"), (1, MIX3, "bf16"),
                                                    (0, MIX2, "f16"), (1, MIX3_TMA, "f32"),
                                                    (1, MIX3, "bf16_rest"), (0, MIX2, "f16_rest"),
-                                                   (1, MIX3_MIXED, "f32")])
+                                                   (1, MIX3_MIXED, "f32"), (1, MIX3_TALL, "f32")])
 def test_batch_equals_solo(sc, lattice, mix, precision):
     steps = 13
     solo = _make(sc, lattice, mix, precision)
@@ -70,10 +73,12 @@ def test_batch_equals_solo(sc, lattice, mix, precision):
         lat.step(steps)
     ref = [_state(lat) for lat in solo]
     tiles = [t for t in range(len(sc.BATCH_TILES)) if all(sc.batch_tile_fits(t, lat) for lat in solo)]
-    if mix is MIX3_TMA:
-        assert tiles == list(range(len(sc.BATCH_TILES)))
+    if mix is MIX3_TMA:  # every tile of at most 8 rows (one lattice is 8 tall)
+        assert tiles == [t for t in range(len(sc.BATCH_TILES)) if sc.BATCH_TILES[t][1] <= 8]
     if mix is MIX3_MIXED:
         assert 9 in tiles
+    if mix is MIX3_TALL:
+        assert 10 in tiles and 11 in tiles
     for tile in tiles:
         for zchunk in ((0, 8) if lattice == 1 else (0,)):
             lats = _make(sc, lattice, mix, precision)
