@@ -131,6 +131,13 @@ cudaError_t d2q9_init(const Plan& p, const void* rA, const void* rB, const void*
                       cudaStream_t st);
 cudaError_t d2q9_moments(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st);
 cudaError_t d3q19_step(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+// the step of each storage precision (sc_d3q19_step_*.cu)
+cudaError_t d3q19_step_f64(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+cudaError_t d3q19_step_f32(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+cudaError_t d3q19_step_bf16(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+cudaError_t d3q19_step_f16(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+cudaError_t d3q19_step_bf16_rest(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+cudaError_t d3q19_step_f16_rest(const Plan& p, const void* fin, void* fout, cudaStream_t st);
 cudaError_t d3q19_init(const Plan& p, const void* rA, const void* rB, const void* u, void* fout,
                        cudaStream_t st);
 cudaError_t d3q19_moments(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st);
