@@ -168,3 +168,23 @@ def test_batch_one_lattice_vs_oracle(sc, oracle_mod):
     a, bb, _, _ = o.moments()
     for x, y in ((g[0], a), (g[1], bb)):
         assert np.abs(x - y).max() / np.abs(y).max() < 1e-5
+
+
+def test_batch_autotuner_restores_state(sc):
+    """tune_batch times every candidate on the caller's lattices and puts their
+    states back: afterwards they continue exactly as if never tuned."""
+    import torch
+    from paper_1112_5547_gb300 import autotune
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a = _make(sc, 1, MIX3_TALL, "f32")
+        b = _make(sc, 1, MIX3_TALL, "f32")
+        for lat in a + b:
+            lat.step(3)
+        best, table = autotune.tune_batch(a, trial_steps=2, warmup_steps=2, stream=stream,
+                                          cands=autotune.batch_candidates(a, zchunks=(0, 16), graph_steps=(0, 2)))
+        assert len(table) >= 8 and best in [c for c, _ in table]
+        for lat in a + b:
+            lat.step(5)
+        for x, y in zip(a, b):
+            _assert_same(_state(x), _state(y), "restored")
