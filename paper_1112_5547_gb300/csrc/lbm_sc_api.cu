@@ -411,7 +411,7 @@ std::vector<lbmsc::BatchItem> batch_items(lbm_sc_handle* const* handles, int n, 
                     len.push_back(std::min(zc, p.nz - z0));
                 }
     }
-    // longest items first, so the grid-stride walk ends with the short ones
+    // longest items first, so the walk (counter or block order) ends with the short ones
     std::vector<size_t> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return len[a] > len[b]; });

@@ -1,11 +1,13 @@
 // Ragged batch: one launch advances many independent lattices by one step.
 //
 // The host builds a work list of items (lattice, x tile, y tile, z chunk) for
-// every lattice of the batch, longest items first; persistent CTAs walk it with
-// a grid stride.  Each item runs the z-marching step of sc_fused_kernel on its
-// own lattice's arguments (read from a device descriptor array holding both
-// ping-pong parities), so every lattice gets exactly the arithmetic of a solo
-// step: batched and solo results are bit-identical.
+// every lattice of the batch, longest items first.  Either persistent CTAs take
+// items from an atomic counter, or the launch has one CTA per item.  Each item
+// runs the per-node code of a solo step (the z-marching body of
+// sc_fused_kernel, or tma_item of the TMA-fed kernel) on its own lattice's
+// arguments, read from a device descriptor array holding both ping-pong
+// parities, so every lattice gets exactly the arithmetic of a solo step:
+// batched and solo results are bit-identical.
 #pragma once
 
 #include "sc_batch_launch.h"
@@ -16,8 +18,9 @@ namespace lbmsc {
 
 // Work list order of a batch launch.  With a counter (persistent grids): CTAs
 // take items in list order from an atomic counter, so a CTA that finishes
-// early takes more; the next index is fetched while the current item runs,
-// and the last CTA to find the list empty resets both counters for the next
+// early takes more; the next index is fetched while the current item runs (the
+// TMA-fed kernel fetches it itself, late in the item), and the last CTA to
+// find the list empty resets both counters for the next
 // launch (no memset between launches; graph replays work).  Without a counter
 // (one CTA per item, grid = item count): CTA b runs item b, and the hardware's
 // block scheduler starts each item as an earlier one retires, which keeps the

@@ -225,7 +225,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     auto ring = sm.ring;
     uint64_t* const bars = sm.bars;
     // linear thread id: the tile shape need not be the block shape (the mixed
-    // batch kernel runs 64x4 and 32x8 items in 256-thread blocks)
+    // batch kernels run two tile shapes in blocks of the same thread count)
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
