@@ -30,3 +30,21 @@ def test_footprint_is_the_workspace():
     assert serving.Server.footprint(r) == lbm_sc.lbm_sc_workspace_bytes(p)
     # the largest D3Q19 request: two FP32 buffers of 2 x 19 values per node
     assert serving.Server.footprint(r) >= 2 * 2 * 19 * 4 * 192 ** 3
+
+
+def test_ragged_batch_specs_seeded_and_in_range():
+    """The ragged-batch recipe: seeded, sizes from the set, G rho_tot, tau and R in range."""
+    from paper_1112_5547_gb300 import inputs
+    a = inputs.ragged_drop_specs()
+    b = inputs.ragged_drop_specs()
+    assert [(s["shape"], s["G"], s["R"], s["centre"]) for s in a] == [(s["shape"], s["G"], s["R"], s["centre"]) for s in b]
+    assert len(a) == 64
+    assert {s["shape"][0] for s in a} <= {32, 48, 64, 96, 128}
+    for s in a:
+        L = s["shape"][0]
+        assert s["shape"] == (L, L, L)
+        assert 2.2 <= s["G"] * inputs.RHO_TOT <= 2.8
+        assert 0.6 <= s["tau_A"] <= 1.5 and 0.6 <= s["tau_B"] <= 1.5
+        assert L / 8 <= s["R"] <= L / 3
+    rA, rB = inputs.spec_fields(a[0])
+    assert rA.shape == a[0]["shape"] and abs((rA + rB).mean() - inputs.RHO_TOT) < 1e-3
