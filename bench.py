@@ -298,6 +298,23 @@ def serve_compare(n: int, rate: float, seed: int = 4):
             "same_steps_as_alone": all(a.steps == b.steps for a, b in zip(res, sres))}
 
 
+def max_over_ranks(value: float, dist=None, device: str = "cuda") -> float:
+    """The largest of one float over all ranks (the job's time is its slowest
+    rank's); with no process group, the value itself."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank advanced its own lattice of nodes_per_rank
+    nodes by `steps` steps within `seconds` (weak scaling, replicas)."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def workload_config(L: int, prec: str, world: int) -> dict:
     """The config object of the JSON line (shared by both arms)."""
     N = L ** 3
@@ -394,14 +411,12 @@ def main():
     total_ms = start.elapsed_time(stop)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist)
         dist.barrier()
     d = lat.diagnostics(check=False)
 
     ms_per_step = total_ms / K
-    value = world * N * K / (total_ms / 1e3) / 1e6
+    value = job_mlups(world, N, K, total_ms / 1e3)
     avg_launch_s = statistics.mean(launch_ms) / 1e3
     bpl = bytes_per_lu(prec)
     achieved = bpl * N / avg_launch_s / 1e9
@@ -434,11 +449,9 @@ def main():
                                oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
         e2e_s = time.perf_counter() - t0
         if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s = max_over_ranks(e2e_s, dist)
         esz = 8 if prec == "f64" else 4
-        e2e = {"value": world * N * K / e2e_s / 1e6, "unit": "MLUPS",
+        e2e = {"value": job_mlups(world, N, K, e2e_s), "unit": "MLUPS",
                "h2d_bytes_per_step": 2 * N * esz / K, "d2h_bytes_per_step": 6 * N * esz / K,
                "note": "one job of %d steps: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p; bytes per step = job bytes / steps" % K}
         del staging, hA, hB, oA, oB, oP, oU, lat2
