@@ -131,12 +131,23 @@ class Server:
 
     def __init__(self, hbm_budget: float = 80e9, chunk: int = 100, check_every: int = 500, tol: float = 0.01,
                  max_steps: int = 10000, graph_steps: int = 0, keep_fields: bool = False, device="cuda",
-                 prep_workers: int = 4):
+                 prep_workers: int = 4, max_active_nodes: Optional[int] = None, order: str = "arrival"):
+        """max_active_nodes: admit a waiting request only while the resident
+        lattices hold fewer nodes than this (besides the HBM budget), so that the
+        GPU is kept full without sharing it among every queued request: earlier
+        requests then finish sooner.  None: the HBM budget alone decides.
+        order: which waiting request is admitted next, "arrival" (first come,
+        first served) or "size" (fewest nodes first, a shortest-job-first proxy:
+        the step count to convergence is not known in advance)."""
+        if order not in ("arrival", "size"):
+            raise ValueError("order must be 'arrival' or 'size'")
+        self.order = order
         import torch
         if check_every % chunk:
             raise ValueError("chunk must divide check_every")
         self.torch = torch
         self.budget = float(hbm_budget)
+        self.max_active_nodes = max_active_nodes
         self.chunk = int(chunk)
         self.check_every = int(check_every)
         self.tol = float(tol)
@@ -220,8 +231,12 @@ class Server:
                     r = pending.popleft()
                     waiting.append(r)
                     prep[r.rid] = pool.submit(r.fields)
-                # admission: arrival order, while the head of the queue fits the budget
-                while waiting and used + self.footprint(waiting[0]) <= self.budget:
+                # admission: arrival (or size) order, while the head of the queue fits
+                if self.order == "size" and len(waiting) > 1:
+                    waiting = deque(sorted(waiting, key=lambda r: (r.nodes, r.arrival)))
+                while (waiting and used + self.footprint(waiting[0]) <= self.budget
+                       and (self.max_active_nodes is None or not resident
+                            or sum(x.req.nodes for x in resident) + waiting[0].nodes <= self.max_active_nodes)):
                     r = waiting.popleft()
                     s = self._admit(r, prep.pop(r.rid).result(), clock() - t0)
                     resident.append(s)
@@ -333,14 +348,21 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--max-steps", type=int, default=10000)
     ap.add_argument("--no-serial", action="store_true")
+    ap.add_argument("--order", type=str, default="arrival", help="admission order(s): arrival, size")
+    ap.add_argument("--max-active-mnodes", type=str, default="none",
+                    help="cap(s) on resident lattice nodes, millions, comma-separated ('none': HBM budget only)")
     a = ap.parse_args(argv)
     rates = [float(r) for r in a.rate.split(",")]
+    caps = [None if c.strip().lower() == "none" else int(float(c) * 1e6) for c in a.max_active_mnodes.split(",")]
     serial = None
-    for rate in rates:
+    orders = a.order.split(",")
+    for rate, cap, order in [(r, c, o) for r in rates for c in caps for o in orders]:
         reqs = poisson_requests(a.requests, rate, a.seed, precision=a.precision)
-        srv = Server(hbm_budget=a.hbm_budget_gb * 1e9, chunk=a.chunk, max_steps=a.max_steps)
+        srv = Server(hbm_budget=a.hbm_budget_gb * 1e9, chunk=a.chunk, max_steps=a.max_steps, max_active_nodes=cap,
+                     order=order)
         res, st = srv.run(reqs)
         out = {"requests": len(reqs), "rate_per_s": rate, "seed": a.seed, "precision": a.precision,
+               "max_active_nodes": cap, "order": order,
                "served_mlups": st.mlups, "wall_s": st.wall_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
                "mean_s": st.mean_s, "max_resident": st.max_resident, "chunks": st.chunks, "rebuilds": st.rebuilds,
                "converged": sum(r.converged for r in res), "steps_total": sum(r.steps for r in res),

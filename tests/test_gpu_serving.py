@@ -47,3 +47,15 @@ def test_admission_respects_budget(sv):
     for r in reqs[:2]:
         alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
         assert np.array_equal(res[r.rid].rhoA, alone.rhoA)
+
+
+def test_active_node_cap(sv):
+    """With a cap on resident nodes, no more than the cap is resident (beyond a
+    single over-sized request), and results are unchanged."""
+    reqs = sv.poisson_requests(6, rate=1000.0, seed=6, d3_fraction=1.0, sizes3=(32,))
+    srv = sv.Server(chunk=100, check_every=500, max_steps=1000, keep_fields=True, max_active_nodes=2 * 32 ** 3)
+    res, st = srv.run(reqs)
+    assert st.max_resident == 2
+    for r in reqs[:2]:
+        alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
+        assert np.array_equal(res[r.rid].rhoA, alone.rhoA)
