@@ -1,4 +1,5 @@
 // Host launchers of the ragged-batch step (sc_batch.cuh).
+#include <atomic>
 #include <cstring>
 #include <type_traits>
 
@@ -10,21 +11,53 @@ namespace lbmsc {
 
 namespace {
 
+// Kernel attributes and occupancy belong to a device: the one-time setup of a
+// kernel is kept per device ordinal (the first call on each device does it).
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kMaxDevices ? dev : -1;
+}
+
+template <auto Kern> cudaError_t dynamic_smem_once(int bytes) {
+    static std::atomic<int> done[kMaxDevices];  // zero-initialised: not yet set
+    const int dev = current_device();
+    if (dev >= 0 && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev >= 0) done[dev].store(1, std::memory_order_release);
+    return e;
+}
+
+template <auto Kern> cudaError_t blocks_per_sm_once(int threads, int* out) {
+    static std::atomic<int> cache[kMaxDevices];  // zero: not yet asked (a kernel always fits once)
+    const int dev = current_device();
+    if (dev >= 0) {
+        const int c = cache[dev].load(std::memory_order_acquire);
+        if (c > 0) {
+            *out = c;
+            return cudaSuccess;
+        }
+    }
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Kern, threads, 0);
+    if (e != cudaSuccess) return e;
+    *out = n > 0 ? n : 1;
+    if (dev >= 0) cache[dev].store(*out, std::memory_order_release);
+    return cudaSuccess;
+}
+
 // grid: one CTA per item (ctr unused), else a persistent grid over the counter.
 template <class L, class S, int TX, int TY>
 cudaError_t launch_batch(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
                          bool grid_mode, cudaStream_t st) {
     using C = typename Codec<S>::C;
     constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : 2);
-    auto kern = sc_batch_step_kernel<L, S, TX, TY, kMin>;
-    static int per_sm = -1;  // resident CTAs per SM, asked once per instantiation
-    if (per_sm < 0) {
-        int n = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0);
-        if (e != cudaSuccess) return e;
-        per_sm = n;
-    }
-    long long grid = grid_mode ? nitems : (long long)sm_count * (per_sm > 0 ? per_sm : 1);
+    constexpr auto kern = sc_batch_step_kernel<L, S, TX, TY, kMin>;
+    int per_sm = 1;  // resident CTAs per SM
+    const cudaError_t oe = blocks_per_sm_once<kern>(TX * TY, &per_sm);
+    if (oe != cudaSuccess) return oe;
+    long long grid = grid_mode ? nitems : (long long)sm_count * per_sm;
     if (grid > nitems) grid = nitems;
     if (grid < 1) return cudaSuccess;
     kern<<<(unsigned)grid, dim3(TX, TY), 0, st>>>(static_cast<const BatchLattice<S>*>(lats), items, nitems, parity,
@@ -36,9 +69,8 @@ template <int TX, int TY, int ST>
 cudaError_t launch_batch_tma(const void* lats, const BatchItem* items, int nitems, int parity, int sm_count, int* ctr,
                              bool grid_mode, cudaStream_t st) {
     using T = TmaTile<TX, TY, ST>;
-    auto kern = sc_batch_tma_kernel<TX, TY, ST>;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+    constexpr auto kern = sc_batch_tma_kernel<TX, TY, ST>;
+    const cudaError_t attr = dynamic_smem_once<kern>((int)T::smem_bytes);
     if (attr != cudaSuccess) return attr;
     // persistent: one CTA per SM (the stages take most of shared memory)
     long long grid = grid_mode ? nitems : sm_count;
@@ -55,8 +87,8 @@ cudaError_t launch_batch_tma_mixed(const void* lats, const BatchItem* items, int
     constexpr size_t smem = TmaTile<WX, WY, S>::smem_bytes > TmaTile<NX, NY, S>::smem_bytes
                                 ? TmaTile<WX, WY, S>::smem_bytes
                                 : TmaTile<NX, NY, S>::smem_bytes;
-    auto kern = sc_batch_tma_mixed_kernel<WX, WY, NX, NY, S>;
-    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto kern = sc_batch_tma_mixed_kernel<WX, WY, NX, NY, S>;
+    const cudaError_t attr = dynamic_smem_once<kern>((int)smem);
     if (attr != cudaSuccess) return attr;
     if (nitems < 1) return cudaSuccess;
     kern<<<(unsigned)nitems, WX * WY, smem, st>>>(static_cast<const BatchTmaLattice*>(lats), items, nitems, parity);
