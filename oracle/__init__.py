@@ -46,7 +46,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double),
-                ("G", ctypes.c_double)]
+                ("G", ctypes.c_double), ("body_A", ctypes.c_double), ("body_y0", ctypes.c_int),
+                ("body_ly", ctypes.c_int)]
 
 
 _lib = None
@@ -110,9 +111,13 @@ class OracleSC:
 
     ``lat`` is D2Q9 (0) or D3Q19 (1); ``shape`` is (ny, nx) for D2Q9 or
     (nz, ny, nx) for D3Q19; tau_A, tau_B, G as in Eq. eq:be / Eq. FORCE.
+    ``body_A`` is the amplitude of the Kolmogorov force of Eq. kolmo (Sec. 4.2),
+    F_s,x = rho_s A sin(2 pi (y + body_y0) / body_ly) (body_ly = 0: ny); the
+    offset and period let a window of a larger lattice see its forcing.
     """
 
-    def __init__(self, lat: int, shape, tau_A: float, tau_B: float, G: float):
+    def __init__(self, lat: int, shape, tau_A: float, tau_B: float, G: float, body_A: float = 0.0,
+                 body_y0: int = 0, body_ly: int = 0):
         self.lat = int(lat)
         shape = tuple(int(s) for s in shape)
         if self.lat == D2Q9:
@@ -123,7 +128,8 @@ class OracleSC:
             assert len(shape) == 3
             nz, ny, nx = shape
         self.shape = shape
-        self.p = _Params(self.lat, nx, ny, nz, float(tau_A), float(tau_B), float(G))
+        self.p = _Params(self.lat, nx, ny, nz, float(tau_A), float(tau_B), float(G), float(body_A),
+                         int(body_y0), int(body_ly))
         self.N = nx * ny * nz
         self.Q = 9 if self.lat == D2Q9 else 19
         self.f = np.zeros((self.N, 2, self.Q))
@@ -168,6 +174,17 @@ class OracleSC:
             raise ValueError("oracle_moments failed")
         s = self.shape
         return rA.reshape(s), rB.reshape(s), u.reshape(s + (3,)), pr.reshape(s)
+
+    def kinetic_energy(self) -> float:
+        """Total kinetic energy sum_x (rho/2) |u_phys|^2 (Sec. 4.2)."""
+        a, b, u, _ = self.moments()
+        return float(0.5 * ((a + b) * (u * u).sum(-1)).sum())
+
+    def droplet_nodes(self, phi_T: float = 0.0) -> int:
+        """Nodes inside the drop, phi = rho_A - rho_B >= phi_T (Sec. 4.2, M(t) of
+        the mass leakage L(t) = M(t) / M_0)."""
+        a, b, _, _ = self.moments()
+        return int(np.count_nonzero(a - b >= phi_T))
 
     def total_momentum(self) -> np.ndarray:
         out = np.zeros(3)

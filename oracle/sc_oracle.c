@@ -13,6 +13,10 @@
  *   common velocity u' = sum_s (1/tau_s) sum_i f_is c_i
  *                        / sum_s rho_s / tau_s                       (Sec. 2.1, moments)
  *   force          F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x + c_i) c_i (Eq. FORCE)
+ *                  plus, when A != 0, the Kolmogorov body force of Eq. kolmo
+ *                  (Sec. 4.2), F_x = rho A sin(2 pi y / L_y), shared between
+ *                  the species in proportion to their densities:
+ *                  F_s,x(x) += rho_s(x) A sin(2 pi y / L_y)
  *   collision      f*_is = f_is - (f_is - f^eq_is(rho_s, u' + tau_s F_s / rho_s)) / tau_s
  *                                                                   (Eq. eq:be, dt = 1)
  *   streaming      f_is(x + c_i, t + 1) = f*_is(x), periodic box    (Eq. eq:be; Sec. 4)
@@ -28,7 +32,9 @@
  * Parity status: every function here is pinned by the CPU tests (lattice
  * sums in exact rationals, equilibrium moments, conservation laws, exact
  * rational one-step trace, shear-wave and diffusion decay rates, the paper's
- * linear spinodal rate, the paper's coexistence example, Laplace's law).
+ * linear spinodal rate, the paper's coexistence example, Laplace's law; the
+ * body force by an exact rational trace with the force, the closed-form
+ * first step of a forced uniform fluid and the steady Kolmogorov profile).
  *
  * Node index n = x + nx * (y + ny * z).  Populations: f[(n * 2 + s) * Q + i].
  * Built with -O2 -ffp-contract=off so no fused multiply-add changes rounding;
@@ -49,6 +55,9 @@ typedef struct {
     int nx, ny, nz;
     double tau_A, tau_B;
     double G;         /* coupling G_AB = G_BA, one value (Eq. FORCE) */
+    double body_A;    /* amplitude A of the Kolmogorov force (Eq. kolmo); 0 = none */
+    int body_y0;      /* global y of row 0 (a window cut from a larger lattice) */
+    int body_ly;      /* period L_y of the forcing; 0 = ny */
 } oracle_params;
 
 typedef struct {
@@ -113,6 +122,7 @@ static int check_params(const oracle_params* p)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
     if (p->lattice == 0 && p->nz != 1) return -1;
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return -1;
+    if (p->body_ly < 0) return -1;
     return 0;
 }
 
@@ -200,12 +210,15 @@ static void compute_moments(const oracle_params* p, const velocity_set* vs, cons
         }
 }
 
-/* F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x + c_i) c_i, s' the other species (Eq. FORCE). */
+/* F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x + c_i) c_i, s' the other species (Eq. FORCE),
+ * plus rho_s(x) A sin(2 pi y / L_y) along x (Eq. kolmo). */
 static void compute_force(const oracle_params* p, const velocity_set* vs, const double* rho,
                           double* F)
 {
     const int Q = vs->q;
     const long N = (long)p->nx * p->ny * p->nz;
+    const double two_pi = 2.0 * acos(-1.0);
+    const double ly = p->body_ly > 0 ? (double)p->body_ly : (double)p->ny;
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n)
         for (int s = 0; s < 2; ++s) {
@@ -216,6 +229,10 @@ static void compute_force(const oracle_params* p, const velocity_set* vs, const 
                 for (int a = 0; a < 3; ++a) sum[a] += vs->w[i] * r * vs->c[i][a];
             }
             for (int a = 0; a < 3; ++a) F[(s * N + n) * 3 + a] = -p->G * rho[s * N + n] * sum[a];
+            if (p->body_A != 0.0) {
+                const long y = (n / p->nx) % p->ny + p->body_y0;
+                F[(s * N + n) * 3 + 0] += rho[s * N + n] * p->body_A * sin(two_pi * (double)y / ly);
+            }
         }
 }
 

@@ -6,7 +6,9 @@ of the equilibrium).  Used only to pin the oracle.
 The model (Sec. 2.1): moments rho_s = sum_i f_is, u' = sum_s j_s/tau_s /
 sum_s rho_s/tau_s; force F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x+c_i) c_i
 (Eq. FORCE); BGK relaxation to f^eq(rho_s, u' + tau_s F_s/rho_s) (Eq. eq:be)
-followed by streaming along c_i on a periodic box.
+followed by streaming along c_i on a periodic box.  Optional Kolmogorov body
+force (Eq. kolmo, Sec. 4.2): F_s,x += rho_s A sin(2 pi y / ny), kept exact by
+allowing only ny in {1, 2, 4}, where the sine takes the values 0 and +-1.
 """
 from fractions import Fraction as Fr
 
@@ -29,10 +31,15 @@ def feq_hermite(rho, u):
 class ExactSC:
     """f[s][y][x] is a list of 9 Fractions."""
 
-    def __init__(self, nx, ny, tau_A, tau_B, G):
+    def __init__(self, nx, ny, tau_A, tau_B, G, body_A=0):
         self.nx, self.ny = nx, ny
         self.tau = (Fr(tau_A), Fr(tau_B))
         self.G = Fr(G)
+        self.A = Fr(body_A)
+        # sin(2 pi y / ny) for ny = 4: 0, 1, 0, -1; ny = 1, 2: zeros
+        quarter = [Fr(0), Fr(1), Fr(0), Fr(-1)]
+        assert ny in (1, 2, 4) or self.A == 0
+        self.sin_y = [quarter[(4 // ny) * y % 4] if ny in (1, 2, 4) else Fr(0) for y in range(ny)]
         self.f = None
 
     def init(self, rhoA, rhoB):
@@ -57,7 +64,8 @@ class ExactSC:
                         r = rho[o][(y + cy) % self.ny][(x + cx) % self.nx]
                         sx += w * r * cx
                         sy += w * r * cy
-                    F[s][y][x] = (-self.G * rho[s][y][x] * sx, -self.G * rho[s][y][x] * sy)
+                    F[s][y][x] = (-self.G * rho[s][y][x] * sx + rho[s][y][x] * self.A * self.sin_y[y],
+                                  -self.G * rho[s][y][x] * sy)
         return rho, j, F
 
     def step(self):

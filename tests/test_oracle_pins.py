@@ -348,3 +348,123 @@ def test_laplace_law(oracle_mod):
     assert slope > 0
     assert r2 > 0.99
     assert abs(icpt) < 0.05 * slope / 8
+
+
+# --- Kolmogorov body force (Eq. kolmo, Sec. 4.2) ------------------------------
+@pytest.mark.parametrize("tau_A,tau_B,G,A", [(1, 1, 0, Fraction(1, 50)),
+                                             (Fraction(3, 2), Fraction(4, 5), Fraction(2, 1), Fraction(-1, 40))])
+def test_exact_rational_steps_4x4_body_force(oracle_mod, tau_A, tau_B, G, A):
+    """The 4x4 trace with the forcing F_s,x += rho_s A sin(2 pi y / 4): the sine
+    is 0, 1, 0, -1 there, so the brute force stays exact."""
+    rng = np.random.default_rng(5)
+    nums = rng.integers(1, 40, size=(2, 4, 4))
+    rA = [[Fraction(int(nums[0, y, x]), 20) for x in range(4)] for y in range(4)]
+    rB = [[Fraction(int(nums[1, y, x]), 25) for x in range(4)] for y in range(4)]
+    ex = exact_sc.ExactSC(4, 4, tau_A, tau_B, G, body_A=A).init(rA, rB)
+    o = oracle_mod.OracleSC(0, (4, 4), float(tau_A), float(tau_B), float(G), body_A=float(A))
+    o.init(np.array(rA, dtype=float), np.array(rB, dtype=float))
+    for _ in range(2):
+        ex.step()
+        o.step(1)
+        a, b, u, p = o.moments()
+        eA, eB, eux, euy, ep = (np.array([float(v) for v in arr]).reshape(4, 4) for arr in ex.fields())
+        np.testing.assert_allclose(a, eA, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(b, eB, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(u[..., 0], eux, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(u[..., 1], euy, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(p, ep, rtol=2e-15, atol=0)
+    # the forcing is really exercised: without it the trace differs
+    ex0 = exact_sc.ExactSC(4, 4, tau_A, tau_B, G).init(rA, rB).step().step()
+    assert max(abs(float(x - y)) for x, y in zip(ex0.fields()[2], ex.fields()[2])) > 1e-3
+
+
+@pytest.mark.parametrize("lat,shape,G", [(0, (24, 3), 0.0), (0, (7, 2), G0), (1, (3, 20, 2), G0), (1, (2, 9, 3), 0.0)])
+def test_body_force_first_step_closed_form(oracle_mod, lat, shape, G):
+    """Uniform rho_A != rho_B at rest, tau_A != tau_B, forcing A along x:
+    uniform densities make the interaction force vanish, so the collision gives
+    f*_i = (1 - 1/tau_s) w_i rho_s + f^eq_i(rho_s, tau_s A sin(k y) e_x) / tau_s,
+    k = 2 pi / L_y.  After streaming, j_s,x(y) = 3 rho_s A sum_i w_i c_ix^2
+    sin(k (y - c_iy)), where sum_i w_i c_ix^2 is 2/9 over the velocities with
+    c_iy = 0 and 1/18 over each of c_iy = +-1 (D2Q9 and D3Q19 alike):
+    j_s,x = rho_s A sin(k y) (2 + cos k) / 3.  The quadratic terms of f^eq
+    cancel row by row (their weights sum to zero), so rho_s is unchanged and
+    j_y = j_z = 0.  With the F/2 shift, u_phys,x = A sin(k y) ((2 + cos k)/3 + 1/2)."""
+    A = 3e-4
+    ly = shape[-2]
+    k = 2 * np.pi / ly
+    rA = np.full(shape, 0.9)
+    rB = np.full(shape, 0.15)
+    o = oracle_mod.OracleSC(lat, shape, 0.7, 1.3, G, body_A=A).init(rA, rB).step(1)
+    a, b, u, _ = o.moments()
+    np.testing.assert_allclose(a, 0.9, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(b, 0.15, rtol=1e-15, atol=0)
+    y = np.arange(ly).reshape([ly if ax == len(shape) - 2 else 1 for ax in range(len(shape))])
+    expect = A * np.sin(k * y) * ((2 + np.cos(k)) / 3 + 0.5)
+    # rounding: j is a sum of populations of size ~0.1, each rounded to ~1e-17
+    np.testing.assert_allclose(u[..., 0], np.broadcast_to(expect, shape), rtol=0, atol=5e-16)
+    np.testing.assert_allclose(u[..., 1:], 0.0, rtol=0, atol=5e-16)
+
+
+def _steady_kolmogorov_ratio(oracle_mod, lat, ly, tau, A=1e-5):
+    """Steady amplitude of u_phys,x over the Navier-Stokes value A / (nu k^2),
+    and the largest deviation of the profile from a pure sine (relative)."""
+    shape = (ly, 2) if lat == 0 else (2, ly, 2)
+    r = np.full(shape, 0.5)
+    k = 2 * np.pi / ly
+    nu = CS2 * (tau - 0.5)
+    o = oracle_mod.OracleSC(lat, shape, tau, tau, 0.0, body_A=A).init(r, r)
+    o.step(int(25 / (nu * k * k)))  # 25 e-folds of the slowest transient
+    u = o.moments()[2][..., 0]
+    amp = _mode_amp(u, len(shape) - 2)
+    s = np.sin(k * np.arange(ly)).reshape([ly if ax == len(shape) - 2 else 1 for ax in range(len(shape))])
+    return amp / (A / (nu * k * k)), float(np.abs(u - amp * s).max() / amp)
+
+
+@pytest.mark.parametrize("lat", [0, 1])
+def test_kolmogorov_steady_profile(oracle_mod, lat):
+    """G = 0, one fluid (rho_A = rho_B): the steady state of the forcing of
+    Eq. kolmo solves nu u'' + A sin(k y) = 0, u = A sin(k y) / (nu k^2) with
+    nu = cs2 (tau - 1/2) (Sec. 2.1).  The profile is a pure sine; the lattice
+    shifts the amplitude at second order in k (the deviation falls fourfold when
+    L_y doubles, and is below 1 % at L_y = 32 for tau <= 1), and at tau = 1 the
+    second-order term vanishes: the deviation is fourth order (below 1e-5 at
+    L_y = 32, sixteenfold smaller at 64)."""
+    r1, d1 = _steady_kolmogorov_ratio(oracle_mod, lat, 32, 1.0)
+    r1b, _ = _steady_kolmogorov_ratio(oracle_mod, lat, 64, 1.0)
+    assert abs(r1 - 1) < 1e-5 and d1 < 1e-9, (r1, d1)
+    assert 14.4 < (r1 - 1) / (r1b - 1) < 17.6, (r1, r1b)
+    for tau in (0.6, 0.8):
+        r32, d32 = _steady_kolmogorov_ratio(oracle_mod, lat, 32, tau)
+        r64, _ = _steady_kolmogorov_ratio(oracle_mod, lat, 64, tau)
+        assert abs(r32 - 1) < 1e-2 and d32 < 1e-9, (tau, r32, d32)
+        assert 3.6 < (r32 - 1) / (r64 - 1) < 4.4, (tau, r32, r64)
+
+
+def test_droplet_node_count(oracle_mod):
+    """M(t) of the leakage L(t) = M(t)/M_0 (Sec. 4.2) counts the nodes with
+    phi = rho_A - rho_B >= 0: a tanh drop of radius R covers pi R^2 nodes to
+    within its perimeter; a uniform A-rich lattice counts every node, a B-rich
+    one none."""
+    L, R = 48, 12
+    rA, rB = inputs.drop((L, L), R, seed=0)
+    o = oracle_mod.OracleSC(0, (L, L), 1.0, 1.0, G0, body_A=1e-5).init(rA, rB)
+    m0 = o.droplet_nodes()
+    assert abs(m0 - np.pi * R * R) < 2 * np.pi * R
+    u = np.full((8, 8), 0.6)
+    assert oracle_mod.OracleSC(0, (8, 8), 1.0, 1.0, G0).init(u, 1.2 - u).droplet_nodes() == 64
+    assert oracle_mod.OracleSC(0, (8, 8), 1.0, 1.0, G0).init(u - 0.1, u).droplet_nodes() == 0
+
+
+def test_kinetic_energy_of_forced_uniform_fluid(oracle_mod):
+    """Kinetic energy sum_x (rho/2)|u_phys|^2 after the first forced step of a
+    uniform fluid (closed form of test_body_force_first_step_closed_form):
+    (rho/2) (A c)^2 sum_y sin^2(k y) nx = (rho/2) (A c)^2 N / 2, c = (2 + cos k)/3 + 1/2.
+    At rest (t = 0) only the F/2 shift moves the fluid: c = 1/2."""
+    shape, A = (16, 5), 2e-4
+    N = shape[0] * shape[1]
+    k = 2 * np.pi / shape[0]
+    o = oracle_mod.OracleSC(0, shape, 0.9, 0.9, 0.0, body_A=A).init(np.full(shape, 0.3), np.full(shape, 0.5))
+    assert abs(o.kinetic_energy() / (0.5 * 0.8 * (A * 0.5) ** 2 * N / 2) - 1) < 1e-12
+    o.step(1)
+    c = (2 + np.cos(k)) / 3 + 0.5
+    assert abs(o.kinetic_energy() / (0.5 * 0.8 * (A * c) ** 2 * N / 2) - 1) < 1e-12
