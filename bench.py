@@ -9,9 +9,11 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
                     [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
+                    [--no-storage16] [--no-kolmogorov]
 
 Prints one JSON line (rank 0).  Beside the headline step it carries
-"storage16" (the same step with 16-bit rest-offset storage), "batch"
+"storage16" (the same step with 16-bit rest-offset storage), "kolmogorov"
+(the same drop under the Kolmogorov forcing of Sec. 4.2), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
 lattices stepped one at a time) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
@@ -72,6 +74,7 @@ def parse():
                     help="requests of the continuous-batching serving run (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-storage16", action="store_true", help="skip the 16-bit rest-offset storage line")
+    ap.add_argument("--no-kolmogorov", action="store_true", help="skip the Kolmogorov-forced drop line")
     return ap.parse_args()
 
 
@@ -235,20 +238,22 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     return out
 
 
-def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: str = "bf16_rest"):
-    """The same D3Q19 drop step with 16-bit rest-offset storage (FP32 arithmetic):
-    MLUPS and the HBM roofline of its 168 algorithmic bytes per LU, timed like
-    the headline step (CUDA events on the lattice's stream, inputs far larger
-    than L2).  Launch shape from the tuning cache (autotuned on GB300), else
-    autotuned here."""
+def _drop_leg(L: int, steps: int, warmup: int, peak: float, precision: str, body_A: float = 0.0):
+    """One D3Q19 L^3 drop (the headline's lattice and fields) timed like the
+    headline step: CUDA events on the lattice's stream over `steps` steps after
+    `warmup`, inputs far larger than L2.  Launch shape from the tuning cache
+    (autotuned on GB300), else autotuned here.  Returns the timing, the launch
+    shape and the diagnostics before and after."""
     import torch
     from paper_1112_5547_gb300 import autotune, lbm_sc
     st = torch.cuda.Stream()
     G = G_RHO / (RHO_HI + RHO_LO)
     rA, rB = drop_fields(L, np.float32, seed=2)
     with torch.cuda.stream(st):
-        lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st).init(rA, rB)
+        lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st,
+                             body_A=body_A).init(rA, rB)
         del rA, rB
+        d0 = lat.diagnostics(check=False)
         autotune.tuned(lat, store=False)
         lat.step(warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -259,23 +264,44 @@ def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: s
         d = lat.diagnostics(check=False)
         tile_used = lat.tuning()
     ms = e0.elapsed_time(e1) / steps
+    del lat
+    torch.cuda.empty_cache()
     N = L ** 3
     bpl = bytes_per_lu(precision)
     gbs = bpl * N / (ms / 1e3) / 1e9
-    del lat
-    torch.cuda.empty_cache()
+    return {"precision": precision, "mlups": N / ms / 1e3, "ms_per_step": ms, "steps": steps,
+            "algorithmic_bytes_per_lu": bpl, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "tile": list(lbm_sc.TILES[tile_used[0]]), "tile_id": tile_used[0], "zchunk": tile_used[1]}, d0, d
+
+
+def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: str = "bf16_rest"):
+    """The same D3Q19 drop step with 16-bit rest-offset storage (FP32 arithmetic):
+    MLUPS and the HBM roofline of its 168 algorithmic bytes per LU."""
+    out, _, d = _drop_leg(L, steps, warmup, peak, precision)
+    N = L ** 3
     traffic = None
     if os.path.exists(TRAFFIC_FILE):
         tf = json.load(open(TRAFFIC_FILE))
         key = "d3q19_%s" % precision
         if key in tf and tf[key].get("source_hash") == kernel_source_hash():
             traffic = tf[key]["dram_bytes_per_lu"] * N
-    return {"precision": precision, "workload": "D3Q19 %d^3 drop, same as the headline" % L, "mlups": N / ms / 1e3,
-            "traffic": traffic,
-            "ms_per_step": ms, "steps": steps, "algorithmic_bytes_per_lu": bpl, "achieved_gbs": gbs, "peak_gbs": peak,
-            "frac": gbs / peak, "tile": list(lbm_sc.TILES[tile_used[0]]), "tile_id": tile_used[0],
-            "zchunk": tile_used[1], "diag_status": d["status"],
-            "accuracy": "radius / Laplace dP / max|u| within 1% of the FP64 oracle (tests/test_gpu_storage16.py)"}
+    out.update({"workload": "D3Q19 %d^3 drop, same as the headline" % L, "traffic": traffic,
+                "diag_status": d["status"],
+                "accuracy": "radius / Laplace dP / max|u| within 1% of the FP64 oracle (tests/test_gpu_storage16.py)"})
+    return out
+
+
+def kolmogorov_compare(L: int, steps: int, warmup: int, peak: float, A: float = 1e-6):
+    """The headline drop under the Kolmogorov forcing of Eq. kolmo (Sec. 4.2),
+    F_x = rho A sin(2 pi y / L), A = 1e-6 as in the paper: the same fused step
+    with the body force, MLUPS and roofline fraction, plus the kinetic energy
+    and the leakage L(t) = M(t) / M_0 (nodes with rho_A >= rho_B) after the run."""
+    out, d0, d = _drop_leg(L, steps, warmup, peak, "f32", body_A=A)
+    out.update({"workload": "D3Q19 %d^3 drop, Kolmogorov forcing A = %g" % (L, A), "body_A": A,
+                "kinetic_energy": d["kinetic_energy"], "leakage": d["droplet_nodes"] / d0["droplet_nodes"],
+                "steps_run": warmup + steps, "diag_status": d["status"],
+                "parity": "tests/test_gpu_kolmogorov.py (FP64 1e-12, FP32 1e-5 vs the oracle; closed form at 512^3)"})
+    return out
 
 
 def serve_compare(n: int, rate: float, seed: int = 4):
@@ -466,6 +492,9 @@ def main():
     s16 = None
     if not args.no_storage16 and rank == 0 and prec == "f32":
         s16 = storage16_compare(L, max(10, K // 2), args.warmup, peak)
+    kf = None
+    if not args.no_kolmogorov and rank == 0 and prec == "f32":
+        kf = kolmogorov_compare(L, max(10, K // 2), args.warmup, peak)
     if not args.no_batch and rank == 0:
         bt = batch_compare(args.batch_steps, args.warmup)
     sv = None
@@ -506,6 +535,8 @@ def main():
         line["serving"] = sv
     if s16 is not None:
         line["storage16"] = s16
+    if kf is not None:
+        line["kolmogorov"] = kf
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

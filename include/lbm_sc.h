@@ -76,7 +76,8 @@ typedef enum {
     LBM_F32_STORE_F16_REST = 5
 } lbm_precision;
 
-/* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE). */
+/* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE, and the optional
+ * Kolmogorov forcing of Eq. kolmo). */
 typedef struct {
     int32_t lattice;     /* lbm_lattice                                              */
     int32_t precision;   /* lbm_precision                                            */
@@ -86,6 +87,10 @@ typedef struct {
     double G;            /* coupling G_AB = G_BA (> 0 repulsive)                     */
     double rho_ref_A;    /* reference densities of the 16-bit storage offsets;      */
     double rho_ref_B;    /* ignored for LBM_F64 / LBM_F32                            */
+    double body_A;       /* amplitude A of the Kolmogorov body force of Eq. kolmo   */
+                         /* (Sec. 4.2), F_x = rho A sin(2 pi y / ny), y = 0..ny-1,  */
+                         /* shared by the species in proportion to their densities */
+                         /* (F_s,x = rho_s A sin(2 pi y / ny)); finite; 0 = none    */
 } lbm_sc_params;
 
 /* Optional spherical windows for the drop diagnostics: nodes whose periodic
@@ -98,8 +103,8 @@ typedef struct {
 
 /* FP64 scalars of the current state.  The velocity is the physical one,
  * u_phys = (sum_s j_s + (1/2) sum_s F_s) / (rho_A + rho_B) (Sec. 2.3, momentum
- * shifted by F dt/2); p = cs2 (rho_A + rho_B) + cs2 G rho_A rho_B (bulk part of
- * the pressure tensor, Sec. 2.1). */
+ * shifted by F dt/2; F includes the body force); p = cs2 (rho_A + rho_B) +
+ * cs2 G rho_A rho_B (bulk part of the pressure tensor, Sec. 2.1). */
 typedef struct {
     double mass_A, mass_B;        /* sum_x rho_A, sum_x rho_B                          */
     double momentum[3];           /* sum_x (j_A + j_B + (F_A + F_B) / 2)               */
@@ -109,6 +114,9 @@ typedef struct {
     double nonfinite;             /* number of nodes with a non-finite moment          */
     double in_count, in_rho_A, in_p;    /* inner window: node count, sum rho_A, sum p */
     double out_count, out_rho_A, out_p; /* outer window: node count, sum rho_A, sum p */
+    double droplet_nodes;         /* nodes with phi = rho_A - rho_B >= 0, compared in  */
+                                  /* the compute type: M(t) of the mass leakage       */
+                                  /* L(t) = M(t) / M_0 (Sec. 4.2)                      */
 } lbm_sc_diag;
 
 typedef struct lbm_sc_handle lbm_sc_handle;
@@ -176,8 +184,9 @@ LBM_SC_API lbm_status lbm_sc_init_fields(lbm_sc_handle* h, const void* d_rhoA, c
 
 /* Advance nsteps time steps (Eq. eq:be with Eq. FORCE): one fused kernel per
  * step pulls the populations along -c_i (periodic), forms rho_s and j_s, the
- * force from the neighbours' densities, the common velocity u', relaxes each
- * species to f^eq(rho_s, u' + tau_s F_s / rho_s) and stores.  nsteps >= 0. */
+ * force from the neighbours' densities (plus the body force of Eq. kolmo when
+ * body_A != 0), the common velocity u', relaxes each species to
+ * f^eq(rho_s, u' + tau_s F_s / rho_s) and stores.  nsteps >= 0. */
 LBM_SC_API lbm_status lbm_sc_step(lbm_sc_handle* h, int nsteps);
 
 /* Macroscopic fields of the current state (moments of the populations at the
@@ -195,7 +204,8 @@ LBM_SC_API lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* 
  * device memory -- for example code running inside someone else's CUDA graph
  * capture or custom allocator, or a plugin that is handed device buffers but
  * may not call cudaMalloc itself.  It needs no handle and no workspace: the
- * per-CTA partial sums go to a fixed 2 MiB array in the library's static
+ * per-CTA partial sums go to a fixed array of 16384 slots of 17 doubles
+ * (2.1 MiB) in the library's static
  * device memory (allocated when the library is loaded, on every GPU that
  * loads it, and kept until the process exits).  The paper has no counterpart;
  * this is an interface convenience.

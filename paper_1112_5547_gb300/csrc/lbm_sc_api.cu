@@ -60,6 +60,7 @@ bool valid(const lbm_sc_params* p) {
     if (N >= (1LL << 31)) return false;
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return false;
     if (!(p->G == p->G) || !(p->rho_ref_A == p->rho_ref_A) || !(p->rho_ref_B == p->rho_ref_B)) return false;
+    if (!(p->body_A - p->body_A == 0.0)) return false;  // finite
     return true;
 }
 
@@ -95,6 +96,7 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.G = p->G;
     pl.ref_A = p->rho_ref_A;
     pl.ref_B = p->rho_ref_B;
+    pl.body_A = p->body_A;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo,
                             pl.Np);
     return pl;
@@ -283,6 +285,7 @@ lbm_status lbm_sc_diagnostics(lbm_sc_handle* h, const lbm_sc_window* window, lbm
     host_out->out_count = r[lbmsc::kOutCount];
     host_out->out_rho_A = r[lbmsc::kOutRhoA];
     host_out->out_p = r[lbmsc::kOutP];
+    host_out->droplet_nodes = r[lbmsc::kDropNodes];
     if (err_word != 0) return LBM_ERR_TIMEOUT;
     if (host_out->nonfinite > 0 || !(host_out->min_rho_A > 0) || !(host_out->min_rho_B > 0))
         return LBM_ERR_UNSTABLE;

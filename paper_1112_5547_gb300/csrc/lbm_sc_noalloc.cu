@@ -13,7 +13,7 @@
 namespace {
 
 // Largest diagnostics grid the static scratch holds: one slot of kNumDiag
-// doubles per CTA of the moments kernel (2 MiB in total on every device that
+// doubles per CTA of the moments kernel (2.1 MiB in total on every device that
 // loads the library, held until the process exits).
 constexpr long long kStaticDiagSlots = 16384;
 
@@ -67,6 +67,7 @@ extern "C" LBM_SC_API lbm_status lbm_sc_diagnostics_noalloc(const lbm_sc_params*
     pl.G = p->G;
     pl.ref_A = p->rho_ref_A;
     pl.ref_B = p->rho_ref_B;
+    pl.body_A = p->body_A;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, elem_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo, pl.Np);
     pl.err = nullptr;
 

@@ -153,6 +153,7 @@ template <class S> struct LatticeArgs {
     C tau_A, tau_B;
     C G;
     C ref_A, ref_B;     // rho_ref_s of the 16-bit offsets (0 otherwise)
+    C body_A;           // amplitude A of the Kolmogorov forcing (Eq. kolmo); 0 = none
 };
 
 // Outputs of the moments kernel (any pointer may be null).
@@ -169,7 +170,7 @@ template <class C> struct FieldArgs {
 // Order of the diagnostics partials (matches lbm_sc_diag).
 enum DiagSlot {
     kMassA = 0, kMassB, kMomX, kMomY, kMomZ, kKE, kMaxSpeed, kMinRhoA, kMinRhoB, kNonFinite,
-    kInCount, kInRhoA, kInP, kOutCount, kOutRhoA, kOutP, kNumDiag
+    kInCount, kInRhoA, kInP, kOutCount, kOutRhoA, kOutP, kDropNodes, kNumDiag
 };
 
 // Explicitly rounded arithmetic.  The node update is written with these so the

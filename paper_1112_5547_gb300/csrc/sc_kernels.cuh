@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         };
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
+        node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
         const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
             node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
@@ -246,6 +247,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                         acc[kOutRhoA] += dA;
                         acc[kOutP] += (double)p;
                     }
+                    // inside the drop: phi = rho_A - rho_B >= 0, compared in the compute type (Sec. 4.2)
+                    if (rA >= rB) acc[kDropNodes] += 1.0;
                 }
             }
         }
@@ -354,6 +357,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const Latt
         };
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
+        node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
         node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         if (owner) store_node<L, S>(a, gx, gy, z, f);
     };

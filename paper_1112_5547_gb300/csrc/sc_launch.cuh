@@ -19,6 +19,7 @@ struct Plan {
     int step_zchunk;
     int sm_count;   // multiprocessors of the device (persistent grids)
     double tau_A, tau_B, G, ref_A, ref_B;
+    double body_A;         // Kolmogorov forcing amplitude (Eq. kolmo); 0 = none
     int px, py, gxo, gyo;  // ghost-padded storage geometry (see LatticeArgs)
     long long Np;          // values per population plane
     int* err;              // device error word (set by a kernel whose bounded wait expired)

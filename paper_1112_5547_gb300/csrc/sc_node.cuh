@@ -4,6 +4,7 @@
 // For one node with pulled populations f_is (post-streaming, pre-collision):
 //   rho_s = sum_i f_is,  j_s = sum_i f_is c_i                      (Sec. 2.1 moments)
 //   g_s = F_s / rho_s = -G sum_i w_i rho_s'(x + c_i) c_i           (Eq. FORCE)
+//         [+ A sin(2 pi y / ny) e_x: Kolmogorov forcing, Eq. kolmo]
 //   u' = (j_A / tau_A + j_B / tau_B) / (rho_A / tau_A + rho_B / tau_B)
 //   f_is += (1 / tau_s) (f^eq_i(rho_s, u' + tau_s g_s) - f_is)      (Eq. eq:be)
 // with f^eq_i(rho, u) = w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u].
@@ -86,6 +87,36 @@ __device__ __forceinline__ void node_force(const Nbr& nbr, C G, C (&gA)[3], C (&
         gA[d] = A::mul(gA[d], mG);
         gB[d] = A::mul(gB[d], mG);
     }
+}
+
+// sin(2 pi y / ny) of the Kolmogorov forcing, y in [0, ny).
+template <class C> __device__ __forceinline__ C kolmogorov_sine(int y, int ny);
+template <> __device__ __forceinline__ float kolmogorov_sine<float>(int y, int ny) {
+    return sinpif(__fdiv_rn((float)(2 * y), (float)ny));
+}
+template <> __device__ __forceinline__ double kolmogorov_sine<double>(int y, int ny) {
+    return sinpi(__ddiv_rn((double)(2 * y), (double)ny));
+}
+
+// The Kolmogorov body force of Eq. kolmo (Sec. 4.2), F_x = rho A sin(2 pi y / ny),
+// shared by the species in proportion to their densities (F_s,x = rho_s A sin):
+// per unit density both g_A and g_B gain b = A sin(2 pi y / ny) along x, which
+// then enters the shifted velocities u' + tau_s g_s and the F/2 shift of u_phys.
+// A = 0 leaves g untouched.  b depends on the row only, so a kernel whose
+// threads keep their row may form it once (kolmogorov_accel) and add it per
+// node (node_add_body); node_body_force does both.
+template <class C> __device__ __forceinline__ C kolmogorov_accel(C A, int y, int ny) {
+    return A == (C)0 ? (C)0 : Ar<C>::mul(A, kolmogorov_sine<C>(y, ny));
+}
+template <class C> __device__ __forceinline__ void node_add_body(C A, C b, C (&gA)[3], C (&gB)[3]) {
+    if (A == (C)0) return;
+    gA[0] = Ar<C>::add(gA[0], b);
+    gB[0] = Ar<C>::add(gB[0], b);
+}
+template <class C>
+__device__ __forceinline__ void node_body_force(C A, int y, int ny, C (&gA)[3], C (&gB)[3]) {
+    if (A == (C)0) return;
+    node_add_body<C>(A, kolmogorov_accel<C>(A, y, ny), gA, gB);
 }
 
 // BGK relaxation of one species towards f^eq(rho, u).

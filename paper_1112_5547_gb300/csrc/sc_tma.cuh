@@ -233,6 +233,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     const int nplanes = z1 - z0 + 2;  // planes z0-1 .. z1
     const bool owner = (x0 + tx) < nx && (y0 + ty) < ny;
     const int gx = (x0 + tx) % nx, gy = (y0 + ty) % ny;
+    const C kolmo = kolmogorov_accel<C>(a.body_A, gy, ny);  // the row's forcing, the same on every plane
     // Two issue schedules, measured per storage type at 512^3: FP32 refills a
     // stage right after the barrier that frees it (S planes in flight ahead,
     // 8.34 ms per step against 8.58 for the other schedule); 16-bit storage
@@ -305,6 +306,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
         };
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
+        node_add_body<C>(a.body_A, kolmo, gA, gB);
         node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         if (owner) store_node<L, St>(a, gx, gy, zof(q), X);
     };

@@ -112,7 +112,7 @@ class lbm_sc_params(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double), ("G", ctypes.c_double),
-                ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double)]
+                ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double), ("body_A", ctypes.c_double)]
 
 
 class lbm_sc_window(ctypes.Structure):
@@ -125,7 +125,8 @@ class lbm_sc_diag(ctypes.Structure):
                 ("kinetic_energy", ctypes.c_double), ("max_speed", ctypes.c_double),
                 ("min_rho_A", ctypes.c_double), ("min_rho_B", ctypes.c_double), ("nonfinite", ctypes.c_double),
                 ("in_count", ctypes.c_double), ("in_rho_A", ctypes.c_double), ("in_p", ctypes.c_double),
-                ("out_count", ctypes.c_double), ("out_rho_A", ctypes.c_double), ("out_p", ctypes.c_double)]
+                ("out_count", ctypes.c_double), ("out_rho_A", ctypes.c_double), ("out_p", ctypes.c_double),
+                ("droplet_nodes", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "momentum"}
@@ -202,8 +203,9 @@ def _check(status: int, where: str):
 
 
 def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
-                rho_ref_A: float = 0.0, rho_ref_B: float = 0.0) -> lbm_sc_params:
-    """Parameters for a lattice of numpy-style shape (ny, nx) or (nz, ny, nx)."""
+                rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, body_A: float = 0.0) -> lbm_sc_params:
+    """Parameters for a lattice of numpy-style shape (ny, nx) or (nz, ny, nx);
+    body_A is the Kolmogorov forcing amplitude of Eq. kolmo (0: none)."""
     shape = tuple(int(s) for s in shape)
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
@@ -211,7 +213,7 @@ def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, preci
         nz, ny, nx = shape
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return lbm_sc_params(int(lattice), prec, nx, ny, nz, 0, float(tau_A), float(tau_B), float(G),
-                         float(rho_ref_A), float(rho_ref_B))
+                         float(rho_ref_A), float(rho_ref_B), float(body_A))
 
 
 # ---- one Python function per C entry point ----------------------------------
@@ -346,14 +348,16 @@ class Lattice:
     """A lattice whose workspace is a torch uint8 tensor on ``device``.
 
     ``shape`` is numpy order: (ny, nx) for D2Q9, (nz, ny, nx) for D3Q19.
+    ``body_A`` switches on the Kolmogorov forcing F_x = rho A sin(2 pi y / ny)
+    of Eq. kolmo (Sec. 4.2).
     """
 
     def __init__(self, lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
-                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None):
+                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None, body_A: float = 0.0):
         import torch
 
         self.torch = torch
-        self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B)
+        self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B, body_A)
         self.shape = tuple(int(s) for s in shape)
         self.lattice = int(lattice)
         self.D = 2 if self.lattice == LBM_D2Q9 else 3

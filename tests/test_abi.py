@@ -237,3 +237,35 @@ def test_batch_workspace_and_validation(lib):
     finally:
         for h in hs:
             lib.lbm_sc_destroy(h)
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout (gcc reads
+    include/lbm_sc.h: sizes and the offset of every field)."""
+    import subprocess
+    structs = {"lbm_sc_params": lib.lbm_sc_params, "lbm_sc_diag": lib.lbm_sc_diag,
+               "lbm_sc_window": lib.lbm_sc_window, "lbm_sc_tuning": lib.lbm_sc_tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm_sc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[name + "." + field]) == getattr(cls, field).offset, (name, field)
+
+
+def test_body_force_must_be_finite(lib):
+    for A in (float("nan"), float("inf")):
+        p = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.0, "f32", body_A=A)
+        assert lib.lbm_sc_workspace_bytes(p) == 0
+    p = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.0, "f32", body_A=-1e-6)
+    assert lib.lbm_sc_workspace_bytes(p) > 0

@@ -40,7 +40,7 @@ def test_noalloc_diagnostics_match_handle_diagnostics(sc, lattice, shape, precis
     win = sc.Window(centre, 3.0, min(shape) / 2.5)
     ref = lat.diagnostics(win)
     eb, q, px, py, gx, gy, pop = sc.lbm_sc_layout(lat.handle)
-    out = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = torch.zeros(ctypes.sizeof(sc.lbm_sc_diag) // 8, dtype=torch.float64, device="cuda")
     for call in range(2):  # two calls in a row share the static scratch
         out.fill_(-7.0)
         sc.lbm_sc_diagnostics_noalloc(lat.params, pop, win.to_c(), out.data_ptr(), lat.stream.cuda_stream)
@@ -49,14 +49,14 @@ def test_noalloc_diagnostics_match_handle_diagnostics(sc, lattice, shape, precis
         for k in SUMS:
             assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-12), (call, k)
         np.testing.assert_allclose(got["momentum"], ref["momentum"], rtol=0, atol=1e-10)
-        for k in ("max_speed", "min_rho_A", "min_rho_B", "nonfinite"):
+        for k in ("max_speed", "min_rho_A", "min_rho_B", "nonfinite", "droplet_nodes"):
             assert got[k] == ref[k], (call, k)
 
 
 def test_noalloc_rejects_a_lattice_too_large_for_the_static_scratch(sc):
     import torch
     p = sc.make_params(sc.LBM_D2Q9, (4200, 1024), 1.0, 1.0, 1.0, "f32")  # 4.3M nodes > 16384 tiles of 32 x 8
-    out = torch.zeros(16, dtype=torch.float64, device="cuda")
+    out = torch.zeros(ctypes.sizeof(sc.lbm_sc_diag) // 8, dtype=torch.float64, device="cuda")
     with pytest.raises(sc.LbmError) as e:
         sc.lbm_sc_diagnostics_noalloc(p, 1 << 20, None, out.data_ptr(), 0)
     assert e.value.status == sc.LBM_ERR_INVALID_ARG
