@@ -47,7 +47,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double),
                 ("G", ctypes.c_double), ("body_A", ctypes.c_double), ("body_y0", ctypes.c_int),
-                ("body_ly", ctypes.c_int)]
+                ("body_ly", ctypes.c_int), ("forcing", ctypes.c_int)]
 
 
 _lib = None
@@ -114,10 +114,15 @@ class OracleSC:
     ``body_A`` is the amplitude of the Kolmogorov force of Eq. kolmo (Sec. 4.2),
     F_s,x = rho_s A sin(2 pi (y + body_y0) / body_ly) (body_ly = 0: ny); the
     offset and period let a window of a larger lattice see its forcing.
+    ``forcing`` selects how forces enter the collision: "shift" (the velocity
+    shift of Sec. 2.1, the paper's model) or "guo" (the Guo et al. source term
+    that Sec. 2.3 names as the cure of the tau-dependent coupling).
     """
 
+    FORCING = {"shift": 0, "guo": 1}
+
     def __init__(self, lat: int, shape, tau_A: float, tau_B: float, G: float, body_A: float = 0.0,
-                 body_y0: int = 0, body_ly: int = 0):
+                 body_y0: int = 0, body_ly: int = 0, forcing: str = "shift"):
         self.lat = int(lat)
         shape = tuple(int(s) for s in shape)
         if self.lat == D2Q9:
@@ -129,7 +134,7 @@ class OracleSC:
             nz, ny, nx = shape
         self.shape = shape
         self.p = _Params(self.lat, nx, ny, nz, float(tau_A), float(tau_B), float(G), float(body_A),
-                         int(body_y0), int(body_ly))
+                         int(body_y0), int(body_ly), self.FORCING[forcing])
         self.N = nx * ny * nz
         self.Q = 9 if self.lat == D2Q9 else 19
         self.f = np.zeros((self.N, 2, self.Q))

@@ -20,6 +20,14 @@
  *   collision      f*_is = f_is - (f_is - f^eq_is(rho_s, u' + tau_s F_s / rho_s)) / tau_s
  *                                                                   (Eq. eq:be, dt = 1)
  *   streaming      f_is(x + c_i, t + 1) = f*_is(x), periodic box    (Eq. eq:be; Sec. 4)
+ * Alternative forcing (forcing = 1): the discrete-forcing cure of Guo, Zheng
+ * and Shi that Sec. 2.3 names as the way to remove the tau-dependent coupling
+ * g_tau (the paper gives no formulas; the standard form, for each species):
+ *   u_G  = sum_s (j_s + F_s / 2) / tau_s / sum_s rho_s / tau_s
+ *   f*_is = f_is - (f_is - f^eq_is(rho_s, u_G)) / tau_s
+ *           + (1 - 1 / (2 tau_s)) w_i [(c_i - u_G) / cs2 + (c_i.u_G) c_i / cs2^2] . F_s
+ * (u_G is the barycentric velocity for equal tau_s; the 1/tau_s weights make
+ * the collision add exactly sum_s F_s to the momentum for any tau_s.)
  * The equilibrium is the Maxwellian truncated at second order in u, which
  * the paper names without printing (Sec. 2.1):
  *   f^eq_i(rho, u) = w_i rho [1 + c.u / cs2 + (c.u)^2 / (2 cs2^2) - u.u / (2 cs2)],
@@ -58,6 +66,7 @@ typedef struct {
     double body_A;    /* amplitude A of the Kolmogorov force (Eq. kolmo); 0 = none */
     int body_y0;      /* global y of row 0 (a window cut from a larger lattice) */
     int body_ly;      /* period L_y of the forcing; 0 = ny */
+    int forcing;      /* 0: velocity shift of Sec. 2.1; 1: Guo et al. source term (Sec. 2.3) */
 } oracle_params;
 
 typedef struct {
@@ -123,6 +132,7 @@ static int check_params(const oracle_params* p)
     if (p->lattice == 0 && p->nz != 1) return -1;
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return -1;
     if (p->body_ly < 0) return -1;
+    if (p->forcing != 0 && p->forcing != 1) return -1;
     return 0;
 }
 
@@ -261,6 +271,32 @@ int oracle_step(const oracle_params* p, double* f, double* f_tmp, int nsteps)
             for (int s = 0; s < 2; ++s) {
                 for (int a = 0; a < 3; ++a) num[a] += j[(s * N + n) * 3 + a] / tau[s];
                 den += rho[s * N + n] / tau[s];
+            }
+            if (p->forcing == 1) {
+                /* Guo forcing: f^eq at u_G, plus the discrete source term */
+                double uG[3];
+                for (int a = 0; a < 3; ++a) {
+                    double m = 0.0;
+                    for (int s = 0; s < 2; ++s)
+                        m += (j[(s * N + n) * 3 + a] + 0.5 * F[(s * N + n) * 3 + a]) / tau[s];
+                    uG[a] = m / den;
+                }
+                for (int s = 0; s < 2; ++s) {
+                    double feq[MAXQ];
+                    equilibrium(&vs, rho[s * N + n], uG, feq);
+                    const double* Fs = F + (s * N + n) * 3;
+                    const double* fn = f + (n * 2 + s) * Q;
+                    for (int i = 0; i < Q; ++i) {
+                        double cu = 0.0, src = 0.0;
+                        for (int a = 0; a < 3; ++a) cu += vs.c[i][a] * uG[a];
+                        for (int a = 0; a < 3; ++a)
+                            src += ((vs.c[i][a] - uG[a]) / CS2 + cu * vs.c[i][a] / (CS2 * CS2)) * Fs[a];
+                        double post = fn[i] - (fn[i] - feq[i]) / tau[s] + (1.0 - 0.5 / tau[s]) * vs.w[i] * src;
+                        long m = neighbour(p, n, vs.c[i]);
+                        f_tmp[(m * 2 + s) * Q + i] = post;
+                    }
+                }
+                continue;
             }
             for (int s = 0; s < 2; ++s) {
                 double r = rho[s * N + n];

@@ -9,6 +9,10 @@ sum_s rho_s/tau_s; force F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x+c_i) c_i
 followed by streaming along c_i on a periodic box.  Optional Kolmogorov body
 force (Eq. kolmo, Sec. 4.2): F_s,x += rho_s A sin(2 pi y / ny), kept exact by
 allowing only ny in {1, 2, 4}, where the sine takes the values 0 and +-1.
+Optional Guo forcing (guo=True), the discrete-forcing cure Sec. 2.3 names:
+relaxation to f^eq(rho_s, u_G), u_G = sum_s (j_s + F_s/2)/tau_s / sum_s
+rho_s/tau_s, plus (1 - 1/(2 tau_s)) times the source written here in its
+Hermite form w_i [c.F/cs2 + (c_a c_b - cs2 delta_ab)(u_a F_b + F_a u_b)/(2 cs2^2)].
 """
 from fractions import Fraction as Fr
 
@@ -31,7 +35,8 @@ def feq_hermite(rho, u):
 class ExactSC:
     """f[s][y][x] is a list of 9 Fractions."""
 
-    def __init__(self, nx, ny, tau_A, tau_B, G, body_A=0):
+    def __init__(self, nx, ny, tau_A, tau_B, G, body_A=0, guo=False):
+        self.guo = guo
         self.nx, self.ny = nx, ny
         self.tau = (Fr(tau_A), Fr(tau_B))
         self.G = Fr(G)
@@ -68,8 +73,38 @@ class ExactSC:
                                   -self.G * rho[s][y][x] * sy)
         return rho, j, F
 
+    @staticmethod
+    def source_hermite(u, F):
+        out = []
+        for (cx, cy), w in zip(C, W):
+            cF = cx * F[0] + cy * F[1]
+            q = ((cx * cx - CS2) * 2 * u[0] * F[0] + cx * cy * (u[0] * F[1] + F[0] * u[1])
+                 + cy * cx * (u[1] * F[0] + F[1] * u[0]) + (cy * cy - CS2) * 2 * u[1] * F[1])
+            out.append(w * (cF / CS2 + q / (2 * CS2 * CS2)))
+        return out
+
+    def _step_guo(self, rho, j, F):
+        post = [[[None] * self.nx for _ in range(self.ny)] for _ in (0, 1)]
+        for y in range(self.ny):
+            for x in range(self.nx):
+                den = sum(rho[s][y][x] / self.tau[s] for s in (0, 1))
+                uG = tuple(sum((j[s][y][x][a] + F[s][y][x][a] / 2) / self.tau[s] for s in (0, 1)) / den
+                           for a in (0, 1))
+                for s in (0, 1):
+                    fe = feq_hermite(rho[s][y][x], uG)
+                    src = self.source_hermite(uG, F[s][y][x])
+                    t = self.tau[s]
+                    post[s][y][x] = [fi - (fi - e) / t + (1 - 1 / (2 * t)) * si
+                                     for fi, e, si in zip(self.f[s][y][x], fe, src)]
+        return post
+
     def step(self):
         rho, j, F = self._moments()
+        if self.guo:
+            post = self._step_guo(rho, j, F)
+            self.f = [[[[post[s][(y - cy) % self.ny][(x - cx) % self.nx][i] for i, (cx, cy) in enumerate(C)]
+                        for x in range(self.nx)] for y in range(self.ny)] for s in (0, 1)]
+            return self
         post = [[[None] * self.nx for _ in range(self.ny)] for _ in (0, 1)]
         for y in range(self.ny):
             for x in range(self.nx):

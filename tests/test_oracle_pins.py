@@ -378,8 +378,9 @@ def test_exact_rational_steps_4x4_body_force(oracle_mod, tau_A, tau_B, G, A):
     assert max(abs(float(x - y)) for x, y in zip(ex0.fields()[2], ex.fields()[2])) > 1e-3
 
 
+@pytest.mark.parametrize("forcing", ["shift", "guo"])
 @pytest.mark.parametrize("lat,shape,G", [(0, (24, 3), 0.0), (0, (7, 2), G0), (1, (3, 20, 2), G0), (1, (2, 9, 3), 0.0)])
-def test_body_force_first_step_closed_form(oracle_mod, lat, shape, G):
+def test_body_force_first_step_closed_form(oracle_mod, lat, shape, G, forcing):
     """Uniform rho_A != rho_B at rest, tau_A != tau_B, forcing A along x:
     uniform densities make the interaction force vanish, so the collision gives
     f*_i = (1 - 1/tau_s) w_i rho_s + f^eq_i(rho_s, tau_s A sin(k y) e_x) / tau_s,
@@ -388,13 +389,16 @@ def test_body_force_first_step_closed_form(oracle_mod, lat, shape, G):
     c_iy = 0 and 1/18 over each of c_iy = +-1 (D2Q9 and D3Q19 alike):
     j_s,x = rho_s A sin(k y) (2 + cos k) / 3.  The quadratic terms of f^eq
     cancel row by row (their weights sum to zero), so rho_s is unchanged and
-    j_y = j_z = 0.  With the F/2 shift, u_phys,x = A sin(k y) ((2 + cos k)/3 + 1/2)."""
+    j_y = j_z = 0.  With the F/2 shift, u_phys,x = A sin(k y) ((2 + cos k)/3 + 1/2).
+    Guo forcing gives the same first step: f^eq at u_G = A sin(k y)/2 carries
+    rho_s A sin/(2 tau_s), the source (1 - 1/(2 tau_s)) rho_s A sin, whose row
+    sums are the same 2/9, 1/18 weights."""
     A = 3e-4
     ly = shape[-2]
     k = 2 * np.pi / ly
     rA = np.full(shape, 0.9)
     rB = np.full(shape, 0.15)
-    o = oracle_mod.OracleSC(lat, shape, 0.7, 1.3, G, body_A=A).init(rA, rB).step(1)
+    o = oracle_mod.OracleSC(lat, shape, 0.7, 1.3, G, body_A=A, forcing=forcing).init(rA, rB).step(1)
     a, b, u, _ = o.moments()
     np.testing.assert_allclose(a, 0.9, rtol=1e-15, atol=0)
     np.testing.assert_allclose(b, 0.15, rtol=1e-15, atol=0)
@@ -468,3 +472,87 @@ def test_kinetic_energy_of_forced_uniform_fluid(oracle_mod):
     o.step(1)
     c = (2 + np.cos(k)) / 3 + 0.5
     assert abs(o.kinetic_energy() / (0.5 * 0.8 * (A * c) ** 2 * N / 2) - 1) < 1e-12
+
+
+# --- Guo forcing: the cure of the tau-dependent coupling named in Sec. 2.3 ----
+@pytest.mark.parametrize("tau_A,tau_B,G,A", [(1, 1, Fraction(3, 2), 0),
+                                             (Fraction(3, 2), Fraction(4, 5), Fraction(2, 1), Fraction(-1, 40))])
+def test_exact_rational_steps_4x4_guo(oracle_mod, tau_A, tau_B, G, A):
+    """The 4x4 trace with Guo forcing, against the tracer's Hermite-form source
+    term (written independently of the oracle's expanded form)."""
+    rng = np.random.default_rng(5)
+    nums = rng.integers(1, 40, size=(2, 4, 4))
+    rA = [[Fraction(int(nums[0, y, x]), 20) for x in range(4)] for y in range(4)]
+    rB = [[Fraction(int(nums[1, y, x]), 25) for x in range(4)] for y in range(4)]
+    ex = exact_sc.ExactSC(4, 4, tau_A, tau_B, G, body_A=A, guo=True).init(rA, rB)
+    o = oracle_mod.OracleSC(0, (4, 4), float(tau_A), float(tau_B), float(G), body_A=float(A), forcing="guo")
+    o.init(np.array(rA, dtype=float), np.array(rB, dtype=float))
+    for _ in range(2):
+        ex.step()
+        o.step(1)
+        a, b, u, p = o.moments()
+        eA, eB, eux, euy, ep = (np.array([float(v) for v in arr]).reshape(4, 4) for arr in ex.fields())
+        np.testing.assert_allclose(a, eA, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(b, eB, rtol=2e-15, atol=0)
+        np.testing.assert_allclose(u[..., 0], eux, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(u[..., 1], euy, rtol=0, atol=1e-14)
+    shift = exact_sc.ExactSC(4, 4, tau_A, tau_B, G, body_A=A).init(rA, rB).step().step()
+    assert max(abs(float(x - y)) for x, y in zip(shift.fields()[2], ex.fields()[2])) > 1e-2
+
+
+@pytest.mark.parametrize("tau,g", [(1.0, 1.0), (0.7, 1.0), (1.0, 1.5), (0.7, 1.5), (0.6, 1.0)])
+def test_guo_spinodal_rate_with_plain_g(oracle_mod, tau, g):
+    """Sec. 2.3: the tau-dependent coupling g_tau = tau g/(tau - 1/2) comes from
+    the velocity-shift forcing, and Guo's discrete forcing removes it.  With
+    Guo forcing the phi mode decays at the rate of the linear theory with the
+    plain g, while the velocity-shift model follows g_tau
+    (test_linear_spinodal_rate_with_g_tau); at these parameters the two
+    predictions differ by 50 % or more."""
+    L, rho = 64, 1.0
+    rA, rB = inputs.phi_mode((4, L), rho, 1e-4)
+    o = oracle_mod.OracleSC(0, (4, L), tau, tau, g, forcing="guo").init(rA, rB)
+    o.step(100)
+    m = o.moments()
+    a1 = _mode_amp(m[0] - m[1], 1)
+    o.step(1000)
+    m = o.moments()
+    a2 = _mode_amp(m[0] - m[1], 1)
+    k = 2 * np.pi / L
+    rate = np.log(a1 / a2) / 1000.0
+
+    def theory(gg):
+        return rho * (tau - 0.5) * (CS2 * (1 / rho - gg / 2) * k * k + gg / 4 * CS2 * CS2 * k ** 4)
+    assert abs(rate / theory(g) - 1) < 1e-2
+    assert abs(rate / theory(tau * g / (tau - 0.5)) - 1) > 0.3
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.7])
+def test_guo_coexistence_with_plain_g(oracle_mod, tau):
+    """The paper's Sec. 4 example (rho = 1.4, g_tau = 1.804 -> phi = +-1) with Guo
+    forcing: the same coexistence follows from the plain coupling g = 1.804 at
+    any tau, and ln(rho_A/rho_B) = g phi in the bulk (mu constant, Sec. 2.1)."""
+    with open(os.path.join(GOLDEN, "paper_sec4_coexistence.json")) as fh:
+        gold = json.load(fh)
+    L = 128
+    rho, phi0 = gold["rho"], gold["phi_bulk"]
+    g = gold["tau"] * gold["g_AB"] / (gold["tau"] - 0.5)  # 1.804
+    rA, rB = inputs.slab((4, L), L / 4, rho_hi=(rho + phi0) / 2, rho_lo=(rho - phi0) / 2, noise=0.0)
+    o = oracle_mod.OracleSC(0, (4, L), tau, tau, g, forcing="guo").init(rA, rB).step(20000)
+    a, b, _, _ = o.moments()
+    ra, rb = a[0, L // 2], b[0, L // 2]
+    assert abs((ra - rb) - phi0) < 0.06 * phi0
+    assert abs((a - b)[0, 0] + phi0) < 0.06 * phi0
+    assert abs(np.log(ra / rb) / (g * (ra - rb)) - 1) < 2e-2
+
+
+def test_guo_conserves_mass_and_momentum(oracle_mod):
+    """Unequal tau_s: per-species mass is conserved, and with the 1/tau_s-weighted
+    u_G the collision adds exactly sum_s F_s, which sums to zero over a periodic
+    lattice (Eq. FORCE pairs c_i with -c_i), so the total momentum stays put."""
+    f = inputs.drop((48, 40), 10, seed=1)
+    o = oracle_mod.OracleSC(0, (48, 40), 0.7, 1.3, G0, forcing="guo").init(*f)
+    m0 = o.total_momentum()
+    o.step(200)
+    a, b, _, _ = o.moments()
+    assert abs(a.sum() / f[0].sum() - 1) < 1e-13 and abs(b.sum() / f[1].sum() - 1) < 1e-13
+    assert np.abs(o.total_momentum() - m0).max() < 1e-12
