@@ -9,11 +9,12 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
                     [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
-                    [--no-storage16] [--no-kolmogorov]
+                    [--no-storage16] [--no-kolmogorov] [--no-guo]
 
 Prints one JSON line (rank 0).  Beside the headline step it carries
 "storage16" (the same step with 16-bit rest-offset storage), "kolmogorov"
-(the same drop under the Kolmogorov forcing of Sec. 4.2), "batch"
+(the same drop under the Kolmogorov forcing of Sec. 4.2), "guo" (the same
+drop with Guo forcing, Sec. 2.3), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
 lattices stepped one at a time) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
@@ -75,6 +76,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--no-storage16", action="store_true", help="skip the 16-bit rest-offset storage line")
     ap.add_argument("--no-kolmogorov", action="store_true", help="skip the Kolmogorov-forced drop line")
+    ap.add_argument("--no-guo", action="store_true", help="skip the Guo-forcing line")
     return ap.parse_args()
 
 
@@ -238,12 +240,14 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     return out
 
 
-def _drop_leg(L: int, steps: int, warmup: int, peak: float, precision: str, body_A: float = 0.0):
+def _drop_leg(L: int, steps: int, warmup: int, peak: float, precision: str, body_A: float = 0.0,
+              forcing: str = "shift", tile=None):
     """One D3Q19 L^3 drop (the headline's lattice and fields) timed like the
     headline step: CUDA events on the lattice's stream over `steps` steps after
     `warmup`, inputs far larger than L2.  Launch shape from the tuning cache
-    (autotuned on GB300), else autotuned here.  Returns the timing, the launch
-    shape and the diagnostics before and after."""
+    (autotuned on GB300), else autotuned here, unless `tile` = (tile, zchunk)
+    fixes it.  Returns the timing, the launch shape and the diagnostics before
+    and after."""
     import torch
     from paper_1112_5547_gb300 import autotune, lbm_sc
     st = torch.cuda.Stream()
@@ -251,10 +255,13 @@ def _drop_leg(L: int, steps: int, warmup: int, peak: float, precision: str, body
     rA, rB = drop_fields(L, np.float32, seed=2)
     with torch.cuda.stream(st):
         lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st,
-                             body_A=body_A).init(rA, rB)
+                             body_A=body_A, forcing=forcing).init(rA, rB)
         del rA, rB
         d0 = lat.diagnostics(check=False)
-        autotune.tuned(lat, store=False)
+        if tile is not None:
+            lat.set_tuning(*tile)
+        else:
+            autotune.tuned(lat, store=False)
         lat.step(warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
@@ -288,6 +295,17 @@ def storage16_compare(L: int, steps: int, warmup: int, peak: float, precision: s
     out.update({"workload": "D3Q19 %d^3 drop, same as the headline" % L, "traffic": traffic,
                 "diag_status": d["status"],
                 "accuracy": "radius / Laplace dP / max|u| within 1% of the FP64 oracle (tests/test_gpu_storage16.py)"})
+    return out
+
+
+def guo_compare(L: int, steps: int, warmup: int, peak: float):
+    """The headline drop with Guo forcing (the cure of the tau-dependent
+    coupling named in Sec. 2.3) instead of the velocity shift: the same 304
+    algorithmic bytes per LU, a longer collision (the source term), on the
+    headline's tile 34 (its Guo instantiation)."""
+    out, _, d = _drop_leg(L, steps, warmup, peak, "f32", forcing="guo", tile=(34, 32))
+    out.update({"workload": "D3Q19 %d^3 drop, Guo forcing" % L, "forcing": "guo", "diag_status": d["status"],
+                "parity": "tests/test_gpu_guo.py (FP64 1e-12, FP32 1e-5 vs the oracle; sampled nodes at 512^3)"})
     return out
 
 
@@ -495,6 +513,9 @@ def main():
     kf = None
     if not args.no_kolmogorov and rank == 0 and prec == "f32":
         kf = kolmogorov_compare(L, max(10, K // 2), args.warmup, peak)
+    gf = None
+    if not args.no_guo and rank == 0 and prec == "f32":
+        gf = guo_compare(L, max(10, K // 2), args.warmup, peak)
     if not args.no_batch and rank == 0:
         bt = batch_compare(args.batch_steps, args.warmup)
     sv = None
@@ -537,6 +558,8 @@ def main():
         line["storage16"] = s16
     if kf is not None:
         line["kolmogorov"] = kf
+    if gf is not None:
+        line["guo"] = gf
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -76,13 +76,24 @@ typedef enum {
     LBM_F32_STORE_F16_REST = 5
 } lbm_precision;
 
+/* How the forces (Eq. FORCE and the body force) enter the collision.
+ * LBM_FORCING_SHIFT is the paper's model (Sec. 2.1): each species relaxes to
+ * f^eq(rho_s, u' + tau_s F_s / rho_s).  LBM_FORCING_GUO is the discrete-forcing
+ * cure of Guo, Zheng and Shi that Sec. 2.3 names as the way to remove the
+ * tau-dependent coupling g_tau = tau g / (tau - 1/2) of the shift; the paper
+ * prints no formulas, and the library uses the standard form per species:
+ * relaxation to f^eq(rho_s, u_G), u_G = sum_s (j_s + F_s/2)/tau_s /
+ * sum_s rho_s/tau_s, plus (1 - 1/(2 tau_s)) w_i [3 (c_i - u_G).F_s +
+ * 9 (c_i.u_G)(c_i.F_s)].  The reported velocity u_phys is the same for both. */
+typedef enum { LBM_FORCING_SHIFT = 0, LBM_FORCING_GUO = 1 } lbm_forcing;
+
 /* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE, and the optional
  * Kolmogorov forcing of Eq. kolmo). */
 typedef struct {
     int32_t lattice;     /* lbm_lattice                                              */
     int32_t precision;   /* lbm_precision                                            */
     int32_t nx, ny, nz;  /* >= 1 each; nz must be 1 for D2Q9; nx*ny*nz < 2^31        */
-    int32_t reserved;    /* set to 0                                                 */
+    int32_t forcing;     /* lbm_forcing (0 = the paper's velocity shift)             */
     double tau_A, tau_B; /* relaxation times tau_s (> 1/2)                           */
     double G;            /* coupling G_AB = G_BA (> 0 repulsive)                     */
     double rho_ref_A;    /* reference densities of the 16-bit storage offsets;      */
@@ -147,7 +158,9 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
  * with 3 stages in 1x2 clusters (16-bit), 39 = 64x8 with 2 stages in 1x2
  * clusters (16-bit, 512 threads), 40 = 48x8 with 2 stages in 1x2 clusters,
- * 41 = the same without clusters (FP32).  zchunk is the number
+ * 41 = the same without clusters (FP32).  With LBM_FORCING_GUO the accepted
+ * tiles are those of the register and low-register kernels (0-4, 11-14) and
+ * the TMA tile 34.  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {
@@ -288,7 +301,9 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  *           item, each lattice with its own tile: 64x4 if it is at least 64
  *           wide, else 32x8 (same requirements as 5); 10 = 32x12 and 11 =
  *           64x6 / 32x12 per lattice, the same with 384-thread CTAs (every
- *           lattice at least 32 x 12)
+ *           lattice at least 32 x 12).  The TMA-fed tiles (3-6, 9-11) need
+ *           every lattice on LBM_FORCING_SHIFT; the z-marching ones take
+ *           lattices of either forcing, mixed.
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

@@ -119,7 +119,8 @@ CACHE_PATH = __import__("os").path.join(__import__("os").path.dirname(__import__
 def cache_key(lattice: "lbm_sc.Lattice") -> str:
     prec = {v: k for k, v in lbm_sc.PRECISIONS.items()}[lattice.params.precision]
     kind = "D2Q9" if lattice.lattice == lbm_sc.LBM_D2Q9 else "D3Q19"
-    return "%s/%s/%s" % (kind, prec, "x".join(str(s) for s in reversed(lattice.shape)))
+    key = "%s/%s/%s" % (kind, prec, "x".join(str(s) for s in reversed(lattice.shape)))
+    return key + "/guo" if lattice.params.forcing == lbm_sc.LBM_FORCING_GUO else key
 
 
 def tuned(lattice: "lbm_sc.Lattice", path: str = CACHE_PATH, store: bool = True, **kw):

@@ -61,6 +61,7 @@ bool valid(const lbm_sc_params* p) {
     if (!(p->tau_A > 0.5) || !(p->tau_B > 0.5)) return false;
     if (!(p->G == p->G) || !(p->rho_ref_A == p->rho_ref_A) || !(p->rho_ref_B == p->rho_ref_B)) return false;
     if (!(p->body_A - p->body_A == 0.0)) return false;  // finite
+    if (p->forcing != LBM_FORCING_SHIFT && p->forcing != LBM_FORCING_GUO) return false;
     return true;
 }
 
@@ -97,6 +98,7 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.ref_A = p->rho_ref_A;
     pl.ref_B = p->rho_ref_B;
     pl.body_A = p->body_A;
+    pl.forcing = p->forcing;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo,
                             pl.Np);
     return pl;

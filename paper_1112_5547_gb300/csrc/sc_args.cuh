@@ -31,6 +31,7 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     a.ref_A = Codec<S>::kOffset ? (C)p.ref_A : (C)0;
     a.ref_B = Codec<S>::kOffset ? (C)p.ref_B : (C)0;
     a.body_A = (C)p.body_A;
+    a.forcing = p.forcing;
     return a;
 }
 

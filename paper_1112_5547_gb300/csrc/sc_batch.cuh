@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             C gA[3], gB[3];
             node_force<L, C>(nbr, a.G, gA, gB);
             node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
-            node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
             if (owner) store_node<L, S>(a, gx, gy, z, f);
         };
 

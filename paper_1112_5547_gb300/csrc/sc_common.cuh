@@ -154,7 +154,11 @@ template <class S> struct LatticeArgs {
     C G;
     C ref_A, ref_B;     // rho_ref_s of the 16-bit offsets (0 otherwise)
     C body_A;           // amplitude A of the Kolmogorov forcing (Eq. kolmo); 0 = none
+    int forcing;        // kForcingShift (Sec. 2.1) or kForcingGuo (Sec. 2.3)
 };
+
+// How forces enter the collision (lbm_forcing).
+constexpr int kForcingShift = 0, kForcingGuo = 1;
 
 // Outputs of the moments kernel (any pointer may be null).
 template <class C> struct FieldArgs {

@@ -51,10 +51,10 @@ cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <class L, class S, int TX, int TY, int ST> struct TmaLaunch {
+template <class L, class S, int TX, int TY, int ST, int FORCING = kForcingShift> struct TmaLaunch {
     static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
 };
-template <class S, int TX, int TY, int ST> struct TmaLaunch<D3Q19, S, TX, TY, ST> {
+template <class S, int TX, int TY, int ST, int FORCING> struct TmaLaunch<D3Q19, S, TX, TY, ST, FORCING> {
     static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
         if constexpr (sizeof(S) == 8) {
             return cudaErrorInvalidValue;
@@ -68,7 +68,7 @@ template <class S, int TX, int TY, int ST> struct TmaLaunch<D3Q19, S, TX, TY, ST
             if (e == cudaSuccess && T::REST)
                 e = encode_rho_map(p, rest_rho<D3Q19>(a.fin, p.Np), T::RBX, T::RBY, &maps.rho, ts.promo);
             if (e != cudaSuccess) return e;
-            auto kern = sc_step_tma_kernel<TX, TY, ST, S>;
+            auto kern = sc_step_tma_kernel<TX, TY, ST, S, FORCING>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
             if (e != cudaSuccess) return e;
             if (ts.cx == 1 && ts.cy == 1) {
@@ -151,6 +151,7 @@ template <> struct AsyncDispatch<D3Q19, float> {
 template <class L, class S> cudaError_t step_typed_other(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st);
 
 template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fin, void* fout, cudaStream_t st) {
+    if (!tile_supported(p.step_tile, p.lattice, p.precision, p.forcing)) return cudaErrorInvalidValue;
     LatticeArgs<S> a = make_args<S>(p, fin, fout);
     a.zchunk = p.step_zchunk;
     static_assert(kTiles[0].tx == 32 && kTiles[0].ty == 8 && kTiles[1].ty == 16 && kTiles[2].tx == 64 &&
@@ -225,8 +226,10 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
             case 28:
             case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
-            case 33:
-            case 34: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
+            case 33: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
+            case 34:
+                return p.forcing == kForcingGuo ? TmaLaunch<L, S, 64, 6, 2, kForcingGuo>::run(p, a, st)
+                                                : TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
             case 36:
             case 37: return TmaLaunch<L, S, 32, 12, 2>::run(p, a, st);
             case 40:

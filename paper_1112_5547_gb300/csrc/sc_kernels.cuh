@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
         const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
-            node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
             if (owner) store_node<L, S>(a, gx, gy, z, f);
         } else {
             // physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2 shift, Sec. 2.3)
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const Latt
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
-        node_collide<L, C>(f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         if (owner) store_node<L, S>(a, gx, gy, z, f);
     };
 

@@ -163,4 +163,79 @@ __device__ __forceinline__ void node_collide(C (&f)[2][L::Q], C rA, C rB, const 
     node_relax<L, C>(f[1], rB, uB, omega_B);
 }
 
+// Guo forcing, the discrete-forcing cure that Sec. 2.3 names for the
+// tau-dependent coupling of the velocity shift (the paper prints no formulas;
+// this is the standard form, per species, with F_s = rho_s g_s):
+//   u_G = sum_s (j_s + F_s / 2) / tau_s / sum_s rho_s / tau_s
+//   f_is += (1 / tau_s) (f^eq_i(rho_s, u_G) - f_is) + (1 - 1 / (2 tau_s)) S_is
+//   S_is = w_i [3 (c_i - u_G).F_s + 9 (c_i.u_G) (c_i.F_s)]
+// The source's rest component is closed as S_0 = -sum_{i>0} S_i (its sum over
+// i vanishes in exact arithmetic), like f^eq_0.
+template <class L, class C>
+__device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)[3], const C (&F)[3], C omega) {
+    using A = Ar<C>;
+    C uu = L::D == 3 ? A::fma(u[0], u[0], A::fma(u[1], u[1], A::mul(u[2], u[2]))) : A::fma(u[0], u[0], A::mul(u[1], u[1]));
+    C uF = L::D == 3 ? A::fma(u[0], F[0], A::fma(u[1], F[1], A::mul(u[2], F[2]))) : A::fma(u[0], F[0], A::mul(u[1], F[1]));
+    const C base = A::fma((C)-1.5, uu, (C)1);
+    const C keep = A::fma((C)-0.5, omega, (C)1);  // 1 - 1 / (2 tau)
+    C feq[L::Q], src[L::Q];
+    C moved = (C)0, sources = (C)0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        C cu = (C)0, cF = (C)0;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) {
+                cu = A::add(cu, u[d]);
+                cF = A::add(cF, F[d]);
+            }
+            if (L::c(i, d) == -1) {
+                cu = A::sub(cu, u[d]);
+                cF = A::sub(cF, F[d]);
+            }
+        }
+        const C wr = A::mul((C)L::w(i), rho);
+        feq[i] = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
+        moved = A::add(moved, feq[i]);
+        src[i] = A::mul((C)L::w(i), A::fma(A::mul((C)9, cu), cF, A::mul((C)3, A::sub(cF, uF))));
+        sources = A::add(sources, src[i]);
+    }
+    feq[0] = A::sub(rho, moved);
+    src[0] = -sources;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) f[i] = A::fma(keep, src[i], A::fma(omega, A::sub(feq[i], f[i]), f[i]));
+}
+
+template <class L, class C>
+__device__ __forceinline__ void node_collide_guo(C (&f)[2][L::Q], C rA, C rB, const C (&gA)[3], const C (&gB)[3],
+                                                 C omega_A, C omega_B) {
+    using A = Ar<C>;
+    C jA[3], jB[3];
+    node_momentum<L, C>(f[0], jA);
+    node_momentum<L, C>(f[1], jB);
+    const C inv_den = A::rcp(A::fma(rA, omega_A, A::mul(rB, omega_B)));
+    C FA[3], FB[3], u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        FA[d] = A::mul(rA, gA[d]);
+        FB[d] = A::mul(rB, gB[d]);
+        const C mA = A::fma((C)0.5, FA[d], jA[d]);
+        const C mB = A::fma((C)0.5, FB[d], jB[d]);
+        u[d] = A::mul(A::fma(mA, omega_A, A::mul(mB, omega_B)), inv_den);
+    }
+    node_relax_guo<L, C>(f[0], rA, u, FA, omega_A);
+    node_relax_guo<L, C>(f[1], rB, u, FB, omega_B);
+}
+
+// The collision of the lattice's forcing scheme, chosen at run time (kernels
+// whose launch shapes accept either scheme).
+template <class L, class C>
+__device__ __forceinline__ void node_collide_any(int forcing, C (&f)[2][L::Q], C rA, C rB, const C (&gA)[3],
+                                                 const C (&gB)[3], C omega_A, C omega_B, C tau_A, C tau_B) {
+    if (forcing == kForcingGuo)
+        node_collide_guo<L, C>(f, rA, rB, gA, gB, omega_A, omega_B);
+    else
+        node_collide<L, C>(f, rA, rB, gA, gB, omega_A, omega_B, tau_A, tau_B);
+}
+
 }  // namespace lbmsc

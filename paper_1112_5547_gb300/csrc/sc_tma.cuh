@@ -211,7 +211,7 @@ struct TmaNoHook {
 // planes the item used, or -1 if a wait was lost (the error word is then
 // raised, and the copies still in flight have been waited for, again with a
 // bound).  The caller must synchronise the CTA between two items.
-template <int TX, int TY, int S, class St = float, class Hook = TmaNoHook>
+template <int TX, int TY, int S, class St = float, class Hook = TmaNoHook, int FORCING = kForcingShift>
 __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorMap* rmap, const LatticeArgs<St>& a,
                                         int x0, int y0, int z0, unsigned qbase, const TmaSmem<TX, TY, S, St>& sm,
                                         int* __restrict__ err, bool preissued = false, const TmaNext* nxt = nullptr,
@@ -307,7 +307,10 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
         C gA[3], gB[3];
         node_force<L, C>(nbr, a.G, gA, gB);
         node_add_body<C>(a.body_A, kolmo, gA, gB);
-        node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        if constexpr (FORCING == kForcingGuo)
+            node_collide_guo<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B);
+        else
+            node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         if (owner) store_node<L, St>(a, gx, gy, zof(q), X);
     };
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
@@ -362,14 +365,16 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     return r < 0 ? -1 : nplanes;
 }
 
-template <int TX, int TY, int S, class St = float>
+// FORCING: the collision's forcing scheme, fixed at compile time (kForcingGuo
+// is instantiated for the 64x6 FP32 tile only).
+template <int TX, int TY, int S, class St = float, int FORCING = kForcingShift>
 __global__ void __launch_bounds__(TX* TY, 1)
     sc_step_tma_kernel(const __grid_constant__ TmaMaps maps, const LatticeArgs<St> a, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     TmaSmem<TX, TY, S, St> sm(smem_raw);
     sm.init_barriers();
-    tma_item<TX, TY, S, St>(&maps.pop, &maps.rho, a, blockIdx.x * TX, blockIdx.y * TY, blockIdx.z * a.zchunk, 0u, sm,
-                            err);
+    tma_item<TX, TY, S, St, TmaNoHook, FORCING>(&maps.pop, &maps.rho, a, blockIdx.x * TX, blockIdx.y * TY,
+                                                blockIdx.z * a.zchunk, 0u, sm, err);
 }
 
 }  // namespace lbmsc

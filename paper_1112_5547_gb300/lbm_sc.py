@@ -40,6 +40,10 @@ PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "bf16": LBM_F32_STORE_BF16, "f16":
               "bf16_rest": LBM_F32_STORE_BF16_REST, "f16_rest": LBM_F32_STORE_F16_REST}
 REST_PRECISIONS = (LBM_F32_STORE_BF16_REST, LBM_F32_STORE_F16_REST)
 
+LBM_FORCING_SHIFT = 0
+LBM_FORCING_GUO = 1
+FORCINGS = {"shift": LBM_FORCING_SHIFT, "guo": LBM_FORCING_GUO}
+
 # Every entry point declared in include/lbm_sc.h.
 EXPORTS = (
     "lbm_sc_workspace_bytes", "lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step",
@@ -68,7 +72,8 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
         return True
     tx, ty = BATCH_TILES[tile]
     p = lattice.params
-    return p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.nx >= tx and p.ny >= ty
+    return (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT and p.nx >= tx
+            and p.ny >= ty)
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
 # the shared-memory stages of the persistent cp.async kernel (0: register kernel).
@@ -91,12 +96,15 @@ TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2),
 TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0) + (256,) * 12
 
 
-def tile_supported(tile: int, lattice: int, precision: int) -> bool:
+def tile_supported(tile: int, lattice: int, precision: int, forcing: int = 0) -> bool:
     """Mirror of the library's rule: kinds 1 and 5 need D3Q19 with FP32 storage, kind 2 D3Q19 without
-    rest-offset storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage."""
+    rest-offset storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage; Guo forcing
+    runs on kinds 0 and 3 and on tile 34."""
     if not 0 <= tile < len(TILES):
         return False
     kind = TILE_KIND[tile]
+    if forcing == LBM_FORCING_GUO and kind not in (0, 3) and tile != 34:
+        return False
     if kind in (0, 3):
         return True
     if kind in (1, 5):
@@ -110,7 +118,7 @@ def tile_supported(tile: int, lattice: int, precision: int) -> bool:
 
 class lbm_sc_params(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32),
-                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("forcing", ctypes.c_int32),
                 ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double), ("G", ctypes.c_double),
                 ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double), ("body_A", ctypes.c_double)]
 
@@ -203,16 +211,19 @@ def _check(status: int, where: str):
 
 
 def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
-                rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, body_A: float = 0.0) -> lbm_sc_params:
+                rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, body_A: float = 0.0,
+                forcing="shift") -> lbm_sc_params:
     """Parameters for a lattice of numpy-style shape (ny, nx) or (nz, ny, nx);
-    body_A is the Kolmogorov forcing amplitude of Eq. kolmo (0: none)."""
+    body_A is the Kolmogorov forcing amplitude of Eq. kolmo (0: none); forcing
+    "shift" (the paper's velocity shift) or "guo" (lbm_forcing)."""
     shape = tuple(int(s) for s in shape)
     if len(shape) == 2:
         nz, (ny, nx) = 1, shape
     else:
         nz, ny, nx = shape
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return lbm_sc_params(int(lattice), prec, nx, ny, nz, 0, float(tau_A), float(tau_B), float(G),
+    frc = FORCINGS[forcing] if isinstance(forcing, str) else int(forcing)
+    return lbm_sc_params(int(lattice), prec, nx, ny, nz, frc, float(tau_A), float(tau_B), float(G),
                          float(rho_ref_A), float(rho_ref_B), float(body_A))
 
 
@@ -349,15 +360,17 @@ class Lattice:
 
     ``shape`` is numpy order: (ny, nx) for D2Q9, (nz, ny, nx) for D3Q19.
     ``body_A`` switches on the Kolmogorov forcing F_x = rho A sin(2 pi y / ny)
-    of Eq. kolmo (Sec. 4.2).
+    of Eq. kolmo (Sec. 4.2); ``forcing`` is "shift" (Sec. 2.1) or "guo" (Sec. 2.3).
     """
 
     def __init__(self, lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
-                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None, body_A: float = 0.0):
+                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None, body_A: float = 0.0,
+                 forcing="shift"):
         import torch
 
         self.torch = torch
-        self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B, body_A)
+        self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B, body_A,
+                                  forcing)
         self.shape = tuple(int(s) for s in shape)
         self.lattice = int(lattice)
         self.D = 2 if self.lattice == LBM_D2Q9 else 3

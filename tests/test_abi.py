@@ -269,3 +269,26 @@ def test_body_force_must_be_finite(lib):
         assert lib.lbm_sc_workspace_bytes(p) == 0
     p = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.0, "f32", body_A=-1e-6)
     assert lib.lbm_sc_workspace_bytes(p) > 0
+
+
+def test_forcing_scheme_rules(lib):
+    """lbm_forcing: 0 and 1 only; Guo forcing on the register / low-register
+    tiles and tile 34; the TMA batch tiles need the velocity shift."""
+    assert lib.lbm_sc_workspace_bytes(lib.make_params(lib.LBM_D2Q9, (8, 8), 1.0, 1.0, 2.0, "f32", forcing=2)) == 0
+    for lat, shape, prec in ((lib.LBM_D3Q19, (8, 8, 8), "f32"), (lib.LBM_D2Q9, (8, 8), "f64"),
+                             (lib.LBM_D3Q19, (8, 8, 8), "bf16_rest")):
+        p = lib.make_params(lat, shape, 1.0, 1.0, 2.0, prec, forcing="guo")
+        assert lib.lbm_sc_workspace_bytes(p) > 0
+        h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+        try:
+            for t in range(len(lib.TILES)):
+                kind = lib.TILE_KIND[t]
+                ok = lib.tile_supported(t, lat, p.precision, lib.LBM_FORCING_GUO)
+                assert ok == (kind in (0, 3) or (t == 34 and lat == lib.LBM_D3Q19 and prec == "f32"))
+                if ok and kind in (0, 3):
+                    lib.lbm_sc_set_tuning(h, t, 0)
+                elif not ok:
+                    with pytest.raises(lib.LbmError):
+                        lib.lbm_sc_set_tuning(h, t, 0)
+        finally:
+            lib.lbm_sc_destroy(h)

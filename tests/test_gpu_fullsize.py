@@ -79,13 +79,14 @@ def _decoded_window(sc, lat, centre, radius):
     return f
 
 
-def _oracle_window_step(oracle_mod, f_gpu, tau_A, tau_B, G, body=(0.0, 0, 0)):
+def _oracle_window_step(oracle_mod, f_gpu, tau_A, tau_B, G, body=(0.0, 0, 0), forcing="shift"):
     """One oracle step of the periodic window; moments of its centre node.
     body = (A, global y of the window's row 0, L_y) for the Kolmogorov forcing."""
     c_or, _ = oracle_mod.lattice(1)
     perm = [int(np.nonzero((GPU_C3 == c).all(1))[0][0]) for c in c_or]  # oracle i -> GPU i
     W = f_gpu.shape[-1]
-    o = oracle_mod.OracleSC(1, (W, W, W), tau_A, tau_B, G, body_A=body[0], body_y0=body[1], body_ly=body[2])
+    o = oracle_mod.OracleSC(1, (W, W, W), tau_A, tau_B, G, body_A=body[0], body_y0=body[1], body_ly=body[2],
+                            forcing=forcing)
     # oracle populations: node-major (N, 2, Q), node x + W (y + W z), oracle order
     o.f[:] = f_gpu[:, perm].transpose(2, 3, 4, 0, 1).reshape(W ** 3, 2, len(perm))
     o.step(1)
@@ -111,7 +112,8 @@ def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4, rho
     for pt in pts:
         f = _decoded_window(sc, lat, pt, 3)
         body = (lat.params.body_A, pt[1] - 3, lat.params.ny)
-        ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G, body))
+        forcing = "guo" if lat.params.forcing == sc.LBM_FORCING_GUO else "shift"
+        ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G, body, forcing))
     lat.step(1)
     rA, rB, u, _ = lat.moments()
     for pt, (oa, ob, ou) in zip(pts, ref):
@@ -124,25 +126,32 @@ def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4, rho
         assert np.abs(gu - ou).max() <= tol_u, (pt, gu, ou)
 
 
-@pytest.mark.parametrize("precision,tol_rho,tol_u,body_A", [("f32", 1e-5, 1e-6, 0.0), ("bf16_rest", 2e-4, 2e-4, 0.0),
-                                                          ("f32", 1e-5, 1e-6, 1e-4)])
-def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tol_rho, tol_u, body_A):
+@pytest.mark.parametrize("precision,tol_rho,tol_u,body_A,forcing", [("f32", 1e-5, 1e-6, 0.0, "shift"),
+                                                                  ("bf16_rest", 2e-4, 2e-4, 0.0, "shift"),
+                                                                  ("f32", 1e-5, 1e-6, 1e-4, "shift"),
+                                                                  ("f32", 1e-5, 1e-6, 1e-4, "guo")])
+def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tol_rho, tol_u, body_A, forcing):
     """The bench's 512^3 drop in the bench's launch shape (the tuning cache's
     entry, which bench.py uses), and in the previous headline shape (TMA 64x4,
     1x2 clusters, 64-plane chunks; tile 22, or 30 for the 16-bit line); also
     under the Kolmogorov forcing (the window oracle is given the window's
-    global rows and the lattice's period L_y)."""
+    global rows and the lattice's period L_y), and with Guo forcing (tile 34,
+    its one TMA instantiation)."""
     import torch
     from paper_1112_5547_gb300 import autotune
     L = 512
     rA, rB = inputs.drop((L, L, L), L / 4, seed=2, dtype=np.float32)
-    lat = sc.Lattice(1, (L, L, L), 1.0, 1.0, G0, precision, body_A=body_A).init(rA, rB)
+    lat = sc.Lattice(1, (L, L, L), 1.0, 1.0, G0, precision, body_A=body_A, forcing=forcing).init(rA, rB)
     del rA, rB
-    (tile, zc), _ = autotune.tuned(lat, store=False)
+    if forcing == "guo":  # the headline tile's Guo instantiation, then the register kernel
+        tile, zc = 34, 32
+        lat.set_tuning(tile, zc)
+    else:
+        (tile, zc), _ = autotune.tuned(lat, store=False)
     tx, ty = sc.TILES[tile]
     absolute = precision != "f32"  # 16-bit rounding of the stored offsets is an absolute error
     _check_sampled(sc, oracle_mod, lat, _samples(L, (tx, ty), zc), tol_rho, tol_u, rho_abs=absolute)
-    lat.set_tuning(22 if precision == "f32" else 30, 64)
+    lat.set_tuning(4 if forcing == "guo" else (22 if precision == "f32" else 30), 64)
     _check_sampled(sc, oracle_mod, lat, _samples(L, n_random=4, seed=8), tol_rho, tol_u, steps_before=1,
                    rho_abs=absolute)
     d = lat.diagnostics()
