@@ -7,8 +7,8 @@ code with the CUDA path (``paper_1112_5547_gb300``) and never imports it.
 The arithmetic lives in ``sc_oracle.c`` (plain C, FP64, no fused multiply-add);
 this module builds it with gcc and wraps it with ctypes + numpy.  Each function
 follows the paper's Sec. 2.1 (Eq. eq:be, the moment definitions, Eq. FORCE, the
-isotropy sums) and the F dt/2 momentum shift of Sec. 2.3; see the C file's
-header for the formulas.
+isotropy sums) and the F dt/2 momentum shift of Sec. 2.3, or, for OracleFE, the
+free-energy model of Sec. 2.2; see the C file for the formulas.
 
 Array conventions (numpy, float64):
   * scalar fields: shape (nz, ny, nx) (x fastest), or (ny, nx) for D2Q9;
@@ -50,6 +50,12 @@ class _Params(ctypes.Structure):
                 ("body_ly", ctypes.c_int), ("forcing", ctypes.c_int)]
 
 
+class _FEParams(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("tau", ctypes.c_double), ("tau_g", ctypes.c_double), ("g", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("gamma", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -66,6 +72,13 @@ def _load():
         lib.oracle_step.argtypes = [pp, dp, dp, ctypes.c_int]
         lib.oracle_moments.argtypes = [pp, dp, dp, dp, dp, dp]
         lib.oracle_total_momentum.argtypes = [pp, dp, dp]
+        fp = ctypes.POINTER(_FEParams)
+        lib.oracle_fe_equilibria.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double, dp, dp]
+        lib.oracle_fe_init.argtypes = [fp, dp, dp, dp]
+        lib.oracle_fe_step.argtypes = [fp, dp, dp, ctypes.c_int]
+        lib.oracle_fe_moments.argtypes = [fp, dp, dp, dp, dp, dp]
+        lib.oracle_fe_fields.argtypes = [fp, dp, dp, dp, dp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
         _lib = lib
@@ -195,6 +208,78 @@ class OracleSC:
         out = np.zeros(3)
         _load().oracle_total_momentum(ctypes.byref(self.p), _ptr(self.f), _ptr(out))
         return out
+
+
+def fe_equilibria(lat: int, g: float, kappa: float, gamma: float, rho: float, phi: float, u, grad_phi,
+                  lap_phi: float):
+    """(f^eq, g^eq) of one node of the free-energy model (Sec. 2.2, Eqs. EQFE1, EQFE2)."""
+    lib = _load()
+    u3 = np.zeros(3)
+    u3[: len(u)] = u
+    g3 = np.zeros(3)
+    g3[: len(grad_phi)] = grad_phi
+    feq = np.zeros(19)
+    geq = np.zeros(19)
+    q = lib.oracle_fe_equilibria(lat, float(g), float(kappa), float(gamma), float(rho), float(phi), _ptr(u3),
+                                 _ptr(g3), float(lap_phi), _ptr(feq), _ptr(geq))
+    return feq[:q].copy(), geq[:q].copy()
+
+
+class OracleFE:
+    """The free-energy two-population model of Sec. 2.2 (Eqs. FE1, FE2) with the
+    functional of Eq. FEtau: relaxation times tau (f) and tau_g (g), coupling g,
+    gradient coefficient kappa (default g cs2^2 / 4, as in Eq. FEtau) and Gamma
+    (mobility M = Gamma (tau_g - 1/2)).  Same shapes and field conventions as
+    OracleSC; moments() reports rho_A = (rho + phi)/2, rho_B = (rho - phi)/2, u
+    and the bulk pressure."""
+
+    def __init__(self, lat: int, shape, tau: float, tau_g: float, g: float, kappa: float = None,
+                 gamma: float = 1.0):
+        self.lat = int(lat)
+        shape = tuple(int(s) for s in shape)
+        if self.lat == D2Q9:
+            ny, nx = shape
+            nz = 1
+        else:
+            nz, ny, nx = shape
+        self.shape = shape
+        if kappa is None:
+            kappa = g / 9.0 / 4.0
+        self.p = _FEParams(self.lat, nx, ny, nz, float(tau), float(tau_g), float(g), float(kappa), float(gamma))
+        self.N = nx * ny * nz
+        self.Q = 9 if self.lat == D2Q9 else 19
+        self.f = np.zeros((self.N, 2, self.Q))
+        self._tmp = np.zeros_like(self.f)
+
+    def init(self, rhoA, rhoB):
+        rA = np.ascontiguousarray(rhoA, dtype=np.float64).reshape(-1)
+        rB = np.ascontiguousarray(rhoB, dtype=np.float64).reshape(-1)
+        if _load().oracle_fe_init(ctypes.byref(self.p), _ptr(rA), _ptr(rB), _ptr(self.f)) != 0:
+            raise ValueError("oracle_fe_init rejected the parameters")
+        return self
+
+    def step(self, nsteps: int = 1):
+        if _load().oracle_fe_step(ctypes.byref(self.p), _ptr(self.f), _ptr(self._tmp), int(nsteps)) != 0:
+            raise ValueError("oracle_fe_step failed")
+        return self
+
+    def fields(self):
+        """(rho, phi, u, grad phi, lap phi) of the current populations (lattice stencils)."""
+        rho, phi, lp = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
+        u, gp = np.zeros((self.N, 3)), np.zeros((self.N, 3))
+        _load().oracle_fe_fields(ctypes.byref(self.p), _ptr(self.f), _ptr(rho), _ptr(phi), _ptr(u), _ptr(gp),
+                                 _ptr(lp))
+        s = self.shape
+        return rho.reshape(s), phi.reshape(s), u.reshape(s + (3,)), gp.reshape(s + (3,)), lp.reshape(s)
+
+    def moments(self):
+        rA, rB, pr = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
+        u = np.zeros((self.N, 3))
+        if _load().oracle_fe_moments(ctypes.byref(self.p), _ptr(self.f), _ptr(rA), _ptr(rB), _ptr(u),
+                                     _ptr(pr)) != 0:
+            raise ValueError("oracle_fe_moments failed")
+        s = self.shape
+        return rA.reshape(s), rB.reshape(s), u.reshape(s + (3,)), pr.reshape(s)
 
 
 if __name__ == "__main__":  # pragma: no cover - manual build helper

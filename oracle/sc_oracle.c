@@ -368,3 +368,212 @@ int oracle_total_momentum(const oracle_params* p, const double* f, double* out3)
     for (int a = 0; a < 3; ++a) out3[a] = m[a];
     return 0;
 }
+
+/* ==== Free-energy (FE) two-population model, Sec. 2.2 ======================
+ *
+ * Populations f_i (density and momentum) and g_i (order parameter), stored like
+ * the two SC species: f[(n * 2 + 0) * Q + i] = f_i, f[(n * 2 + 1) * Q + i] = g_i.
+ *   rho = sum_i f_i, u = sum_i f_i c_i / rho, phi = sum_i g_i       (Sec. 2.2)
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq) / tau                 (Eq. FE1)
+ *   g_i(x + c_i, t + 1) = g_i - (g_i - g_i^eq) / tau_g               (Eq. FE2)
+ * Free energy: the tau-dependent SC-matching functional of Eq. FEtau with
+ * coupling g (pass g_tau to match an SC run), bulk density
+ *   V(phi, rho) = cs2 (rho+phi)/2 ln((rho+phi)/2) + cs2 (rho-phi)/2 ln((rho-phi)/2)
+ *                 + g cs2 (rho^2 - phi^2)/4,
+ * gradient coefficient kappa (g cs2^2 / 4 in Eq. FEtau), so that
+ *   mu  = dV/dphi - kappa lap(phi) = cs2/2 ln((rho+phi)/(rho-phi)) - g cs2 phi/2 - kappa lap(phi)
+ *   P   = (p_b - kappa phi lap(phi) - kappa/2 |grad phi|^2) delta + kappa grad(phi) grad(phi),
+ *   p_b = phi dV/dphi + rho dV/drho - V = cs2 rho + g cs2 (rho^2 - phi^2)/4   (Sec. 2.2)
+ * The equilibria are the second-order Hermite forms that meet the moment
+ * conditions of Eq. EQFE1 and Eq. EQFE2 exactly (the paper states only the
+ * conditions):
+ *   f_i^eq = w_i [rho + rho c.u / cs2 + (c_a c_b - cs2 d_ab)(P_ab - rho cs2 d_ab + rho u_a u_b) / (2 cs2^2)]
+ *   g_i^eq = w_i [phi + phi c.u / cs2 + (c_a c_b - cs2 d_ab)((Gamma mu - phi cs2) d_ab + phi u_a u_b) / (2 cs2^2)]
+ * Derivatives by the isotropic lattice stencils
+ *   grad(phi) = (1/cs2) sum_i w_i c_i phi(x + c_i),  lap(phi) = (2/cs2) sum_i w_i (phi(x + c_i) - phi(x)).
+ * Reported fields: rho_A = (rho + phi)/2, rho_B = (rho - phi)/2 (phi = rho_A - rho_B,
+ * Sec. 2.1), u = sum_i f_i c_i / rho, p = p_b.
+ */
+typedef struct {
+    int lattice;
+    int nx, ny, nz;
+    double tau, tau_g;  /* relaxation times of f and g (Eqs. FE1, FE2) */
+    double g;           /* coupling of the functional */
+    double kappa;       /* gradient coefficient */
+    double gamma;       /* Gamma of Eq. EQFE2: mobility M = Gamma (tau_g - 1/2) */
+} fe_params;
+
+static int fe_check(const fe_params* p)
+{
+    if (p->lattice != 0 && p->lattice != 1) return -1;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
+    if (p->lattice == 0 && p->nz != 1) return -1;
+    if (!(p->tau > 0.5) || !(p->tau_g > 0.5)) return -1;
+    return 0;
+}
+
+static long fe_neighbour(const fe_params* p, long n, const int c[3])
+{
+    long nx = p->nx, ny = p->ny, nz = p->nz;
+    long x = n % nx, y = (n / nx) % ny, z = n / (nx * ny);
+    return wrap(x + c[0], nx) + nx * (wrap(y + c[1], ny) + ny * wrap(z + c[2], nz));
+}
+
+/* Equilibria of one node from rho, phi, u (3), grad phi (3), lap phi. */
+static void fe_equilibria(const velocity_set* vs, int D, double g, double kappa, double gamma, double rho,
+                          double phi, const double u[3], const double gp[3], double lp, double* feq, double* geq)
+{
+    const double mu = 0.5 * CS2 * log((rho + phi) / (rho - phi)) - 0.5 * g * CS2 * phi - kappa * lp;
+    const double pb = CS2 * rho + 0.25 * g * CS2 * (rho * rho - phi * phi);
+    const double gg = gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2];
+    double Mf[3][3], Mg[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double d = (a == b) ? 1.0 : 0.0;
+            const double P = (pb - kappa * phi * lp - 0.5 * kappa * gg) * d + kappa * gp[a] * gp[b];
+            Mf[a][b] = P - rho * CS2 * d + rho * u[a] * u[b];
+            Mg[a][b] = (gamma * mu - phi * CS2) * d + phi * u[a] * u[b];
+        }
+    for (int i = 0; i < vs->q; ++i) {
+        double cu = 0.0, hf = 0.0, hg = 0.0;
+        for (int a = 0; a < D; ++a) cu += vs->c[i][a] * u[a];
+        for (int a = 0; a < D; ++a)
+            for (int b = 0; b < D; ++b) {
+                const double h = vs->c[i][a] * vs->c[i][b] - ((a == b) ? CS2 : 0.0);
+                hf += h * Mf[a][b];
+                hg += h * Mg[a][b];
+            }
+        feq[i] = vs->w[i] * (rho + rho * cu / CS2 + hf / (2.0 * CS2 * CS2));
+        geq[i] = vs->w[i] * (phi + phi * cu / CS2 + hg / (2.0 * CS2 * CS2));
+    }
+}
+
+/* Both equilibria of one node (for the moment pins of Eqs. EQFE1, EQFE2). */
+int oracle_fe_equilibria(int lattice, double g, double kappa, double gamma, double rho, double phi,
+                         const double* u3, const double* gp3, double lp, double* feq, double* geq)
+{
+    velocity_set vs;
+    make_velocity_set(lattice, &vs);
+    fe_equilibria(&vs, lattice == 0 ? 2 : 3, g, kappa, gamma, rho, phi, u3, gp3, lp, feq, geq);
+    return vs.q;
+}
+
+/* The t = 0 state from rho_A, rho_B: f_i = w_i rho, g_i = w_i phi with rho = rho_A + rho_B,
+ * phi = rho_A - rho_B (the rest populations; the first collision relaxes them to the
+ * equilibria above). */
+int oracle_fe_init(const fe_params* p, const double* rhoA, const double* rhoB, double* f)
+{
+    if (fe_check(p)) return -1;
+    velocity_set vs;
+    make_velocity_set(p->lattice, &vs);
+    const int Q = vs.q;
+    const long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n)
+        for (int i = 0; i < Q; ++i) {
+            f[(n * 2 + 0) * Q + i] = vs.w[i] * (rhoA[n] + rhoB[n]);
+            f[(n * 2 + 1) * Q + i] = vs.w[i] * (rhoA[n] - rhoB[n]);
+        }
+    return 0;
+}
+
+/* rho, phi, u (N x 3), grad phi (N x 3) and lap phi of the current populations. */
+static void fe_fields(const fe_params* p, const velocity_set* vs, const double* f, double* rho, double* phi,
+                      double* u, double* gp, double* lp)
+{
+    const int Q = vs->q;
+    const long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        double r = 0.0, ph = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; ++i) {
+            const double fi = f[(n * 2 + 0) * Q + i];
+            r += fi;
+            ph += f[(n * 2 + 1) * Q + i];
+            for (int a = 0; a < 3; ++a) j[a] += fi * vs->c[i][a];
+        }
+        rho[n] = r;
+        phi[n] = ph;
+        for (int a = 0; a < 3; ++a) u[n * 3 + a] = j[a] / r;
+    }
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        double g3[3] = {0.0, 0.0, 0.0}, l = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            const double pn = phi[fe_neighbour(p, n, vs->c[i])];
+            for (int a = 0; a < 3; ++a) g3[a] += vs->w[i] * vs->c[i][a] * pn;
+            l += vs->w[i] * (pn - phi[n]);
+        }
+        for (int a = 0; a < 3; ++a) gp[n * 3 + a] = g3[a] / CS2;
+        lp[n] = 2.0 * l / CS2;
+    }
+}
+
+/* nsteps of collide-then-push-stream of Eqs. FE1, FE2. */
+int oracle_fe_step(const fe_params* p, double* f, double* f_tmp, int nsteps)
+{
+    if (fe_check(p) || nsteps < 0) return -1;
+    velocity_set vs;
+    make_velocity_set(p->lattice, &vs);
+    const int Q = vs.q, D = p->lattice == 0 ? 2 : 3;
+    const long N = (long)p->nx * p->ny * p->nz;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* phi = (double*)malloc(sizeof(double) * N);
+    double* u = (double*)malloc(sizeof(double) * N * 3);
+    double* gp = (double*)malloc(sizeof(double) * N * 3);
+    double* lp = (double*)malloc(sizeof(double) * N);
+    if (!rho || !phi || !u || !gp || !lp) { free(rho); free(phi); free(u); free(gp); free(lp); return -2; }
+    const double tau[2] = {p->tau, p->tau_g};
+    for (int t = 0; t < nsteps; ++t) {
+        fe_fields(p, &vs, f, rho, phi, u, gp, lp);
+#pragma omp parallel for schedule(static)
+        for (long n = 0; n < N; ++n) {
+            double eq[2][MAXQ];
+            fe_equilibria(&vs, D, p->g, p->kappa, p->gamma, rho[n], phi[n], u + n * 3, gp + n * 3, lp[n], eq[0],
+                          eq[1]);
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < Q; ++i) {
+                    const double fi = f[(n * 2 + s) * Q + i];
+                    f_tmp[(fe_neighbour(p, n, vs.c[i]) * 2 + s) * Q + i] = fi - (fi - eq[s][i]) / tau[s];
+                }
+        }
+        memcpy(f, f_tmp, sizeof(double) * 2 * N * Q);
+    }
+    free(rho); free(phi); free(u); free(gp); free(lp);
+    return 0;
+}
+
+/* rho_A = (rho + phi)/2, rho_B = (rho - phi)/2, u (N x 3), p_b; any output may be NULL. */
+int oracle_fe_moments(const fe_params* p, const double* f, double* rhoA, double* rhoB, double* u, double* pres)
+{
+    if (fe_check(p)) return -1;
+    velocity_set vs;
+    make_velocity_set(p->lattice, &vs);
+    const long N = (long)p->nx * p->ny * p->nz;
+    double* rho = (double*)malloc(sizeof(double) * N);
+    double* phi = (double*)malloc(sizeof(double) * N);
+    double* uu = (double*)malloc(sizeof(double) * N * 3);
+    double* gp = (double*)malloc(sizeof(double) * N * 3);
+    double* lp = (double*)malloc(sizeof(double) * N);
+    if (!rho || !phi || !uu || !gp || !lp) { free(rho); free(phi); free(uu); free(gp); free(lp); return -2; }
+    fe_fields(p, &vs, f, rho, phi, uu, gp, lp);
+    for (long n = 0; n < N; ++n) {
+        if (rhoA) rhoA[n] = 0.5 * (rho[n] + phi[n]);
+        if (rhoB) rhoB[n] = 0.5 * (rho[n] - phi[n]);
+        if (u) for (int a = 0; a < 3; ++a) u[n * 3 + a] = uu[n * 3 + a];
+        if (pres) pres[n] = CS2 * rho[n] + 0.25 * p->g * CS2 * (rho[n] * rho[n] - phi[n] * phi[n]);
+    }
+    free(rho); free(phi); free(uu); free(gp); free(lp);
+    return 0;
+}
+
+/* rho, phi (N each), u, grad phi (N x 3 each) and lap phi (N) of the current populations. */
+int oracle_fe_fields(const fe_params* p, const double* f, double* rho, double* phi, double* u, double* gp,
+                     double* lp)
+{
+    if (fe_check(p)) return -1;
+    velocity_set vs;
+    make_velocity_set(p->lattice, &vs);
+    fe_fields(p, &vs, f, rho, phi, u, gp, lp);
+    return 0;
+}

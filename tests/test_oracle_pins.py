@@ -556,3 +556,122 @@ def test_guo_conserves_mass_and_momentum(oracle_mod):
     a, b, _, _ = o.moments()
     assert abs(a.sum() / f[0].sum() - 1) < 1e-13 and abs(b.sum() / f[1].sum() - 1) < 1e-13
     assert np.abs(o.total_momentum() - m0).max() < 1e-12
+
+
+# --- free-energy (FE) model, Sec. 2.2 ------------------------------------------
+@pytest.mark.parametrize("lat,D", [(0, 2), (1, 3)])
+def test_fe_equilibria_meet_eqfe1_eqfe2(oracle_mod, lat, D):
+    """The moments the paper imposes on the FE equilibria (Eqs. EQFE1, EQFE2 and the
+    conserved moments): sum f^eq = rho, sum f^eq c = rho u, sum f^eq cc = P + rho uu
+    with P of Sec. 2.2; sum g^eq = phi, sum g^eq c = phi u, sum g^eq cc = Gamma mu delta
+    + phi uu, mu = dV/dphi - kappa lap(phi) of the Eq. FEtau functional."""
+    c, _ = oracle_mod.lattice(lat)
+    cc = c[:, :D].astype(float)
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        rho = 1 + rng.random()
+        phi = (rng.random() - 0.5) * rho
+        u, gp = rng.normal(size=D) * 0.05, rng.normal(size=D) * 0.1
+        lp, g, kappa, gamma = rng.normal() * 0.1, 1.8, 0.05, 0.7
+        fe, ge = oracle_mod.fe_equilibria(lat, g, kappa, gamma, rho, phi, u, gp, lp)
+        mu = 0.5 * CS2 * np.log((rho + phi) / (rho - phi)) - 0.5 * g * CS2 * phi - kappa * lp
+        pb = CS2 * rho + 0.25 * g * CS2 * (rho * rho - phi * phi)
+        P = (pb - kappa * phi * lp - 0.5 * kappa * (gp @ gp)) * np.eye(D) + kappa * np.outer(gp, gp)
+        np.testing.assert_allclose([fe.sum(), ge.sum()], [rho, phi], rtol=0, atol=1e-15)
+        np.testing.assert_allclose(fe @ cc, rho * u, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(ge @ cc, phi * u, rtol=0, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", fe, cc, cc), P + rho * np.outer(u, u), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", ge, cc, cc), gamma * mu * np.eye(D) + phi * np.outer(u, u),
+                                   rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lat,shape", [(0, (12, 10)), (1, (6, 12, 10))])
+def test_fe_lattice_derivatives_of_sines(oracle_mod, lat, shape):
+    """The isotropic stencils on phi = sin(k x) sin(k' y): d/dx carries the factor
+    sin(k) (2 + cos k') / 3 in place of k (the c_y = 0 neighbours weigh 2/3, the
+    diagonals 1/6 each side), d/dy likewise; the Laplacian of the product is
+    6 [(1/9)(2 cos k + 2 cos k' - 4) + (1/36)(4 cos k cos k' - 4)] phi for D2Q9 and
+    6 [(1/18)(2 cos k + 2 cos k' - 4) + (1/36)(4 cos k cos k' - 4 + 2 (2 cos k - 2)
+    + 2 (2 cos k' - 2))] phi for D3Q19 (neighbour sums in x, y and diagonals)."""
+    ny, nx = shape[-2], shape[-1]
+    k, kp = 2 * np.pi / nx, 2 * np.pi / ny
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    phi = 0.05 * np.sin(k * x) * np.sin(kp * y)
+    phi = np.broadcast_to(phi, shape)
+    rho = np.ones(shape)
+    o = oracle_mod.OracleFE(lat, shape, 1.0, 1.0, 1.0).init((rho + phi) / 2, (rho - phi) / 2)
+    _, ph, _, gp, lp = o.fields()
+    np.testing.assert_allclose(ph, phi, atol=1e-16)
+    gx = 0.05 * np.sin(k) * (2 + np.cos(kp)) / 3 * np.cos(k * x) * np.sin(kp * y)
+    gy = 0.05 * np.sin(kp) * (2 + np.cos(k)) / 3 * np.sin(k * x) * np.cos(kp * y)
+    np.testing.assert_allclose(gp[..., 0], np.broadcast_to(gx, shape), atol=1e-15)
+    np.testing.assert_allclose(gp[..., 1], np.broadcast_to(gy, shape), atol=1e-15)
+    np.testing.assert_allclose(gp[..., 2], 0.0, atol=1e-15)
+    ck, ckp = np.cos(k), np.cos(kp)
+    if lat == 0:
+        lam = 6 * ((2 * ck + 2 * ckp - 4) / 9 + (4 * ck * ckp - 4) / 36)
+    else:
+        lam = 6 * ((2 * ck + 2 * ckp - 4) / 18 + (4 * ck * ckp - 4 + 2 * (2 * ck - 2) + 2 * (2 * ckp - 2)) / 36)
+    np.testing.assert_allclose(lp, lam * phi, atol=1e-15)
+
+
+def test_fe_uniform_state_and_conservation(oracle_mod):
+    """A uniform state at rest stays (rho, phi, u) for any g; a drop conserves
+    sum rho, sum phi and the total momentum (collisions keep rho u, streaming
+    permutes) to round-off."""
+    shape = (10, 12)
+    o = oracle_mod.OracleFE(0, shape, 0.9, 1.1, 2.2, gamma=0.6).init(np.full(shape, 0.9), np.full(shape, 0.3)).step(50)
+    a, b, u, _ = o.moments()
+    np.testing.assert_allclose(a, 0.9, atol=1e-14)
+    np.testing.assert_allclose(b, 0.3, atol=1e-14)
+    assert np.abs(u).max() < 1e-15
+    rA, rB = inputs.drop((40, 48), 10, rho_hi=1.2, rho_lo=0.2, seed=3)
+    o = oracle_mod.OracleFE(0, (40, 48), 0.8, 1.2, 1.804, gamma=0.5).init(rA, rB)
+    o.step(300)
+    rho, phi, u, _, _ = o.fields()
+    assert abs(rho.sum() / (rA + rB).sum() - 1) < 1e-13
+    assert abs(phi.sum() - (rA - rB).sum()) < 1e-10 * np.abs(rA - rB).sum()
+    assert np.abs((rho[..., None] * u).sum((0, 1))).max() < 1e-12
+
+
+@pytest.mark.parametrize("tau,tau_g,gamma", [(1.0, 1.0, 1.0), (0.8, 1.2, 0.5)])
+def test_fe_coexistence_matches_the_sc_example(oracle_mod, tau, tau_g, gamma):
+    """Sec. 2.3 / Sec. 4: the FE model with the Eq. FEtau functional at g = g_tau
+    reproduces the SC coexistence of the paper's example (rho = 1.4, g_tau = 1.804
+    -> phi = +-1): the bulk phases obey ln(rho_A/rho_B) = g phi (mu = 0) and sit
+    within 5 % of phi = 1, whatever tau, tau_g and Gamma (they set only the
+    dynamics)."""
+    with open(os.path.join(GOLDEN, "paper_sec4_coexistence.json")) as fh:
+        gold = json.load(fh)
+    L = 128
+    rho, phi0 = gold["rho"], gold["phi_bulk"]
+    g = gold["tau"] * gold["g_AB"] / (gold["tau"] - 0.5)
+    rA, rB = inputs.slab((4, L), L / 4, rho_hi=(rho + phi0) / 2, rho_lo=(rho - phi0) / 2, noise=0.0)
+    o = oracle_mod.OracleFE(0, (4, L), tau, tau_g, g, gamma=gamma).init(rA, rB).step(20000)
+    a, b, u, _ = o.moments()
+    ra, rb = a[0, L // 2], b[0, L // 2]
+    assert abs((ra - rb) - phi0) < 0.05 * phi0 and abs((a - b)[0, 0] + phi0) < 0.05 * phi0
+    assert abs(np.log(ra / rb) / (g * (ra - rb)) - 1) < 2e-3
+    assert np.abs(u).max() < 1e-5
+
+
+@pytest.mark.parametrize("tau,tau_g,gt", [(1.0, 1.0, 1.0), (0.7, 1.0, 1.5), (1.0, 0.8, 1.5)])
+def test_fe_spinodal_rate_matches_the_sc_theory(oracle_mod, tau, tau_g, gt):
+    """The matching of Sec. 2.3: with Gamma (tau_g - 1/2) = rho (tau - 1/2) (the
+    mobility M of Eq. EQcontmatching) and g = g_tau, a small phi mode decays at
+    the rate the SC linear theory gives (test_linear_spinodal_rate_with_g_tau),
+    omega = M [cs2 (1/rho - g/2) k^2 + g cs2^2 k^4 / 4]."""
+    L, rho = 64, 1.0
+    gamma = rho * (tau - 0.5) / (tau_g - 0.5)
+    rA, rB = inputs.phi_mode((4, L), rho, 1e-4)
+    o = oracle_mod.OracleFE(0, (4, L), tau, tau_g, gt, gamma=gamma).init(rA, rB)
+    o.step(100)
+    m = o.moments()
+    a1 = _mode_amp(m[0] - m[1], 1)
+    o.step(1000)
+    m = o.moments()
+    a2 = _mode_amp(m[0] - m[1], 1)
+    k = 2 * np.pi / L
+    rate = np.log(a1 / a2) / 1000.0
+    theory = rho * (tau - 0.5) * (CS2 * (1 / rho - gt / 2) * k * k + gt / 4 * CS2 * CS2 * k ** 4)
+    assert abs(rate / theory - 1) < 1e-2
