@@ -9,12 +9,13 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
                     [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
-                    [--no-storage16] [--no-kolmogorov] [--no-guo]
+                    [--no-storage16] [--no-kolmogorov] [--no-guo] [--no-fe]
 
 Prints one JSON line (rank 0).  Beside the headline step it carries
 "storage16" (the same step with 16-bit rest-offset storage), "kolmogorov"
 (the same drop under the Kolmogorov forcing of Sec. 4.2), "guo" (the same
-drop with Guo forcing, Sec. 2.3), "batch"
+drop with Guo forcing, Sec. 2.3), "fe" (the free-energy model of Sec. 2.2 on
+the same lattice), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
 lattices stepped one at a time) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
@@ -77,6 +78,7 @@ def parse():
     ap.add_argument("--no-storage16", action="store_true", help="skip the 16-bit rest-offset storage line")
     ap.add_argument("--no-kolmogorov", action="store_true", help="skip the Kolmogorov-forced drop line")
     ap.add_argument("--no-guo", action="store_true", help="skip the Guo-forcing line")
+    ap.add_argument("--no-fe", action="store_true", help="skip the free-energy model line")
     return ap.parse_args()
 
 
@@ -241,21 +243,29 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
 
 
 def _drop_leg(L: int, steps: int, warmup: int, peak: float, precision: str, body_A: float = 0.0,
-              forcing: str = "shift", tile=None):
+              forcing: str = "shift", tile=None, fe=None):
     """One D3Q19 L^3 drop (the headline's lattice and fields) timed like the
     headline step: CUDA events on the lattice's stream over `steps` steps after
     `warmup`, inputs far larger than L2.  Launch shape from the tuning cache
     (autotuned on GB300), else autotuned here, unless `tile` = (tile, zchunk)
     fixes it.  Returns the timing, the launch shape and the diagnostics before
-    and after."""
+    and after.  fe = (g, Gamma, rho_hi, rho_lo): the free-energy model of Sec. 2.2
+    (tau = tau_g = 1) on a drop of those densities instead."""
     import torch
-    from paper_1112_5547_gb300 import autotune, lbm_sc
+    from paper_1112_5547_gb300 import autotune, inputs, lbm_sc
     st = torch.cuda.Stream()
     G = G_RHO / (RHO_HI + RHO_LO)
-    rA, rB = drop_fields(L, np.float32, seed=2)
+    if fe is not None:
+        rA, rB = inputs.drop((L, L, L), L / 4.0, rho_hi=fe[2], rho_lo=fe[3], seed=2, dtype=np.float32)
+    else:
+        rA, rB = drop_fields(L, np.float32, seed=2)
     with torch.cuda.stream(st):
-        lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st,
-                             body_A=body_A, forcing=forcing).init(rA, rB)
+        if fe is not None:
+            lat = lbm_sc.FELattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, fe[0], precision, gamma=fe[1],
+                                   stream=st).init(rA, rB)
+        else:
+            lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, stream=st,
+                                 body_A=body_A, forcing=forcing).init(rA, rB)
         del rA, rB
         d0 = lat.diagnostics(check=False)
         if tile is not None:
@@ -306,6 +316,19 @@ def guo_compare(L: int, steps: int, warmup: int, peak: float):
     out, _, d = _drop_leg(L, steps, warmup, peak, "f32", forcing="guo", tile=(34, 32))
     out.update({"workload": "D3Q19 %d^3 drop, Guo forcing" % L, "forcing": "guo", "diag_status": d["status"],
                 "parity": "tests/test_gpu_guo.py (FP64 1e-12, FP32 1e-5 vs the oracle; sampled nodes at 512^3)"})
+    return out
+
+
+def fe_compare(L: int, steps: int, warmup: int, peak: float):
+    """The free-energy two-population model of Sec. 2.2 (Eqs. FE1, FE2, the Eq.
+    FEtau functional with g = 2.5, Gamma = 0.5, tau = tau_g = 1) on an L^3 drop of
+    rho_A = 0.9 in rho_B = 0.14 (phi = +-0.76, its coexistence at rho = 1.04): the
+    same storage and 304 algorithmic bytes per LU as the SC step, on tile 34
+    (its FE instance)."""
+    out, _, d = _drop_leg(L, steps, warmup, peak, "f32", tile=(34, 32), fe=(2.5, 0.5, 0.9, 0.14))
+    out.update({"workload": "D3Q19 %d^3 drop, free-energy model (g 2.5, Gamma 0.5, rho 0.9 / 0.14)" % L,
+                "model": "fe", "diag_status": d["status"],
+                "parity": "tests/test_gpu_fe.py (FP64 1e-12, FP32 1e-5 vs the FE oracle; sampled nodes at 512^3)"})
     return out
 
 
@@ -519,6 +542,9 @@ def main():
     gf = None
     if not args.no_guo and rank == 0 and prec == "f32":
         gf = guo_compare(L, max(10, K // 2), args.warmup, peak)
+    ff = None
+    if not args.no_fe and rank == 0 and prec == "f32":
+        ff = fe_compare(L, max(10, K // 2), args.warmup, peak)
     if not args.no_batch and rank == 0:
         bt = batch_compare(args.batch_steps, args.warmup)
     sv = None
@@ -563,6 +589,8 @@ def main():
         line["kolmogorov"] = kf
     if gf is not None:
         line["guo"] = gf
+    if ff is not None:
+        line["fe"] = ff
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

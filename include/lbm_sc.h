@@ -87,6 +87,26 @@ typedef enum {
  * 9 (c_i.u_G)(c_i.F_s)].  The reported velocity u_phys is the same for both. */
 typedef enum { LBM_FORCING_SHIFT = 0, LBM_FORCING_GUO = 1 } lbm_forcing;
 
+/* The lattice Boltzmann model.  LBM_MODEL_SC: the two-component Shan-Chen
+ * model (Sec. 2.1), everything above.  LBM_MODEL_FE: the free-energy model of
+ * Sec. 2.2 (Eqs. FE1, FE2) on the same storage, species 0 holding f_i
+ * (rho = sum f_i, u = sum f_i c_i / rho) and species 1 holding g_i
+ * (phi = sum g_i); tau_A is tau of f, tau_B is tau_g of g, G is the coupling g
+ * of the Eq. FEtau functional
+ *   V = cs2 (rho+phi)/2 ln((rho+phi)/2) + cs2 (rho-phi)/2 ln((rho-phi)/2) + g cs2 (rho^2-phi^2)/4,
+ * with gradient coefficient kappa (g cs2^2 / 4 in Eq. FEtau) and mobility
+ * Gamma (tau_g - 1/2).  mu = dV/dphi - kappa lap(phi) and the pressure tensor
+ * P = (p_b - kappa phi lap(phi) - kappa/2 |grad phi|^2) delta + kappa grad(phi) grad(phi),
+ * p_b = cs2 rho + g cs2 (rho^2 - phi^2)/4, enter second-order Hermite
+ * equilibria that meet Eqs. EQFE1 and EQFE2 (sum f^eq cc = P + rho uu,
+ * sum g^eq cc = Gamma mu delta + phi uu); derivatives by the isotropic lattice
+ * stencils grad = 3 sum_i w_i c_i phi(x + c_i), lap = 6 sum_i w_i (phi(x + c_i) - phi(x)).
+ * lbm_sc_init_fields takes rho_A, rho_B and sets f = w_i rho (rho = rho_A + rho_B),
+ * g = w_i phi (phi = rho_A - rho_B) times the usual velocity factor; moments and
+ * diagnostics report rho_A = (rho + phi)/2, rho_B = (rho - phi)/2, u and p_b.
+ * FE needs LBM_F64 or LBM_F32, forcing 0 and body_A 0; |phi| < rho throughout. */
+typedef enum { LBM_MODEL_SC = 0, LBM_MODEL_FE = 1 } lbm_model;
+
 /* Parameters of one periodic lattice (Eq. eq:be, Eq. FORCE, and the optional
  * Kolmogorov forcing of Eq. kolmo). */
 typedef struct {
@@ -102,6 +122,10 @@ typedef struct {
                          /* (Sec. 4.2), F_x = rho A sin(2 pi y / ny), y = 0..ny-1,  */
                          /* shared by the species in proportion to their densities */
                          /* (F_s,x = rho_s A sin(2 pi y / ny)); finite; 0 = none    */
+    int32_t model;       /* lbm_model (0 = the SC model)                             */
+    int32_t reserved;    /* set to 0                                                 */
+    double kappa;        /* LBM_MODEL_FE: gradient coefficient kappa (finite)        */
+    double gamma;        /* LBM_MODEL_FE: Gamma of Eq. EQFE2 (finite)                */
 } lbm_sc_params;
 
 /* Optional spherical windows for the drop diagnostics: nodes whose periodic
@@ -158,9 +182,9 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
  * with 3 stages in 1x2 clusters (16-bit), 39 = 64x8 with 2 stages in 1x2
  * clusters (16-bit, 512 threads), 40 = 48x8 with 2 stages in 1x2 clusters,
- * 41 = the same without clusters (FP32).  With LBM_FORCING_GUO the accepted
- * tiles are those of the register and low-register kernels (0-4, 11-14) and
- * the TMA tile 34.  zchunk is the number
+ * 41 = the same without clusters (FP32).  With LBM_FORCING_GUO or
+ * LBM_MODEL_FE the accepted tiles are those of the register and low-register
+ * kernels (0-4, 11-14) and the TMA tile 34.  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).
  * The shape changes only speed: every shape computes bit-identical results. */
 typedef struct {
@@ -302,8 +326,8 @@ LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int
  *           wide, else 32x8 (same requirements as 5); 10 = 32x12 and 11 =
  *           64x6 / 32x12 per lattice, the same with 384-thread CTAs (every
  *           lattice at least 32 x 12).  The TMA-fed tiles (3-6, 9-11) need
- *           every lattice on LBM_FORCING_SHIFT; the z-marching ones take
- *           lattices of either forcing, mixed.
+ *           every lattice on LBM_MODEL_SC with LBM_FORCING_SHIFT; the
+ *           z-marching ones take lattices of any forcing and model, mixed.
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

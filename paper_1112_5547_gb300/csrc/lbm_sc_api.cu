@@ -62,6 +62,12 @@ bool valid(const lbm_sc_params* p) {
     if (!(p->G == p->G) || !(p->rho_ref_A == p->rho_ref_A) || !(p->rho_ref_B == p->rho_ref_B)) return false;
     if (!(p->body_A - p->body_A == 0.0)) return false;  // finite
     if (p->forcing != LBM_FORCING_SHIFT && p->forcing != LBM_FORCING_GUO) return false;
+    if (p->model != LBM_MODEL_SC && p->model != LBM_MODEL_FE) return false;
+    if (p->model == LBM_MODEL_FE) {
+        if (p->precision != LBM_F64 && p->precision != LBM_F32) return false;
+        if (p->forcing != LBM_FORCING_SHIFT || p->body_A != 0.0) return false;
+        if (!(p->kappa - p->kappa == 0.0) || !(p->gamma - p->gamma == 0.0)) return false;  // finite
+    }
     return true;
 }
 
@@ -99,6 +105,9 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.ref_B = p->rho_ref_B;
     pl.body_A = p->body_A;
     pl.forcing = p->forcing;
+    pl.model = p->model;
+    pl.kappa = p->kappa;
+    pl.gamma = p->gamma;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo,
                             pl.Np);
     return pl;

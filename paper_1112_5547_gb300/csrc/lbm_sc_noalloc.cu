@@ -69,6 +69,9 @@ extern "C" LBM_SC_API lbm_status lbm_sc_diagnostics_noalloc(const lbm_sc_params*
     pl.ref_B = p->rho_ref_B;
     pl.body_A = p->body_A;
     pl.forcing = p->forcing;
+    pl.model = p->model;
+    pl.kappa = p->kappa;
+    pl.gamma = p->gamma;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, elem_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo, pl.Np);
     pl.err = nullptr;
 

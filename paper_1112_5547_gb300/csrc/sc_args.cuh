@@ -32,6 +32,9 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     a.ref_B = Codec<S>::kOffset ? (C)p.ref_B : (C)0;
     a.body_A = (C)p.body_A;
     a.forcing = p.forcing;
+    a.model = p.model;
+    a.kappa = (C)p.kappa;
+    a.gamma = (C)p.gamma;
     return a;
 }
 

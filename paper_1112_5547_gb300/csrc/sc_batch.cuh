@@ -105,10 +105,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 const int slot = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
                 return srho[slot][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
             };
-            C gA[3], gB[3];
-            node_force<L, C>(nbr, a.G, gA, gB);
-            node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
-            node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            node_update<L, C>(a, gy, nbr, f, rA, rB);
             if (owner) store_node<L, S>(a, gx, gy, z, f);
         };
 

@@ -44,8 +44,8 @@ inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
 inline bool batch_tile_fits(int tile, const Plan& p) {
     if (tile < 0 || tile >= kNumBatchTiles) return false;
     if (!kBatchTileTma[tile]) return true;  // the z-marching batch kernel chooses the collision at run time
-    return p.lattice == 1 && p.precision == 1 && p.forcing == kForcingShift && p.nx >= kBatchTileX[tile] &&
-           p.ny >= kBatchTileY[tile];
+    return p.lattice == 1 && p.precision == 1 && p.forcing == kForcingShift && p.model == kModelSC &&
+           p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];
 }
 
 // Bytes of one lattice's descriptor, and the descriptor itself (both parities;

@@ -155,10 +155,15 @@ template <class S> struct LatticeArgs {
     C ref_A, ref_B;     // rho_ref_s of the 16-bit offsets (0 otherwise)
     C body_A;           // amplitude A of the Kolmogorov forcing (Eq. kolmo); 0 = none
     int forcing;        // kForcingShift (Sec. 2.1) or kForcingGuo (Sec. 2.3)
+    int model;          // kModelSC (Sec. 2.1) or kModelFE (Sec. 2.2: species 0 = f, 1 = g)
+    C kappa, gamma;     // FE gradient coefficient and Gamma (mobility Gamma (tau_g - 1/2))
 };
 
-// How forces enter the collision (lbm_forcing).
+// How forces enter the collision (lbm_forcing), and the model (lbm_model).
 constexpr int kForcingShift = 0, kForcingGuo = 1;
+constexpr int kModelSC = 0, kModelFE = 1;
+// Compile-time collision choice of the TMA kernel: the two forcing schemes, or the FE model.
+constexpr int kSchemeFE = 2;
 
 // Outputs of the moments kernel (any pointer may be null).
 template <class C> struct FieldArgs {

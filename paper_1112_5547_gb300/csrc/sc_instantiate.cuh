@@ -151,7 +151,7 @@ template <> struct AsyncDispatch<D3Q19, float> {
 template <class L, class S> cudaError_t step_typed_other(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st);
 
 template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fin, void* fout, cudaStream_t st) {
-    if (!tile_supported(p.step_tile, p.lattice, p.precision, p.forcing)) return cudaErrorInvalidValue;
+    if (!tile_supported(p.step_tile, p.lattice, p.precision, p.forcing, p.model)) return cudaErrorInvalidValue;
     LatticeArgs<S> a = make_args<S>(p, fin, fout);
     a.zchunk = p.step_zchunk;
     static_assert(kTiles[0].tx == 32 && kTiles[0].ty == 8 && kTiles[1].ty == 16 && kTiles[2].tx == 64 &&
@@ -228,6 +228,7 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
             case 33: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
             case 34:
+                if (p.model == kModelFE) return TmaLaunch<L, S, 64, 6, 2, kSchemeFE>::run(p, a, st);
                 return p.forcing == kForcingGuo ? TmaLaunch<L, S, 64, 6, 2, kForcingGuo>::run(p, a, st)
                                                 : TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
             case 36:

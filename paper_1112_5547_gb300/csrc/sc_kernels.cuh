@@ -176,25 +176,32 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     };
 
     auto process = [&](C (&f)[2][Q], int sm, int sc, int sp, int z) {
-        const C rA = srho[sc][0][ty + 1][tx + 1];
-        const C rB = srho[sc][1][ty + 1][tx + 1];
+        const C r0 = srho[sc][0][ty + 1][tx + 1];
+        const C r1 = srho[sc][1][ty + 1][tx + 1];
         auto nbr = [&](int s, int i) -> C {
             const int slot = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
             return srho[slot][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
         };
-        C gA[3], gB[3];
-        node_force<L, C>(nbr, a.G, gA, gB);
-        node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
         const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
-            node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+            node_update<L, C>(a, gy, nbr, f, r0, r1);
             if (owner) store_node<L, S>(a, gx, gy, z, f);
         } else {
-            // physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2 shift, Sec. 2.3)
-            C jA[3], jB[3];
+            // SC: physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2
+            // shift, Sec. 2.3).  FE (Sec. 2.2): u = sum_i f_i c_i / rho, and the
+            // reported densities are rho_A = (rho + phi)/2, rho_B = (rho - phi)/2.
+            const bool fe = a.model == kModelFE;
+            C gA[3] = {(C)0, (C)0, (C)0}, gB[3] = {(C)0, (C)0, (C)0};
+            if (!fe) {
+                node_force<L, C>(nbr, a.G, gA, gB);
+                node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
+            }
+            const C rA = fe ? A::mul((C)0.5, A::add(r0, r1)) : r0;
+            const C rB = fe ? A::mul((C)0.5, A::sub(r0, r1)) : r1;
+            C jA[3], jB[3] = {(C)0, (C)0, (C)0};
             node_momentum<L, C>(f[0], jA);
-            node_momentum<L, C>(f[1], jB);
-            const C rho = A::add(rA, rB);
+            if (!fe) node_momentum<L, C>(f[1], jB);
+            const C rho = fe ? r0 : A::add(rA, rB);
             const C inv_rho = A::rcp(rho);
             C u[3];
 #pragma unroll
@@ -355,10 +362,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const Latt
             const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm);
             return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
         };
-        C gA[3], gB[3];
-        node_force<L, C>(nbr, a.G, gA, gB);
-        node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
-        node_collide_any<L, C>(a.forcing, f, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        node_update<L, C>(a, gy, nbr, f, rA, rB);
         if (owner) store_node<L, S>(a, gx, gy, z, f);
     };
 
@@ -448,7 +452,9 @@ __global__ void __launch_bounds__(256)
             const C shape = (C)1 - (C)1.5 * uu + cu * ((C)3 + (C)4.5 * cu);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const C rho = s == 0 ? rhoA[m] : rhoB[m];
+                // SC: species densities; FE: f from rho = rho_A + rho_B, g from phi = rho_A - rho_B
+                const C rho = a.model == kModelFE ? (s == 0 ? rhoA[m] + rhoB[m] : rhoA[m] - rhoB[m])
+                                                  : (s == 0 ? rhoA[m] : rhoB[m]);
                 const C f = (C)L::w(i) * rho * shape;
                 if constexpr (Codec<S>::kRest) {
                     fr[s][i] = f;

@@ -21,6 +21,8 @@ struct Plan {
     double tau_A, tau_B, G, ref_A, ref_B;
     double body_A;         // Kolmogorov forcing amplitude (Eq. kolmo); 0 = none
     int forcing;           // kForcingShift or kForcingGuo
+    int model;             // kModelSC or kModelFE
+    double kappa, gamma;   // FE: gradient coefficient, Gamma
     int px, py, gxo, gyo;  // ghost-padded storage geometry (see LatticeArgs)
     long long Np;          // values per population plane
     int* err;              // device error word (set by a kernel whose bounded wait expired)
@@ -77,11 +79,14 @@ constexpr TileShape kTiles[kNumTiles] = {
     {64, 6, 5, 2, 1, 2}, {64, 6, 5, 2},       {64, 6, 6, 3, 1, 2}, {32, 12, 5, 2, 1, 2}, {32, 12, 5, 2},
     {32, 12, 6, 3, 1, 2}, {64, 8, 6, 2, 1, 2}, {48, 8, 5, 2, 1, 2}, {48, 8, 5, 2}};
 
-// forcing = kForcingGuo: the kernels that choose the collision at run time
-// (kinds 0 and 3) and the 64x6 TMA tile (34), which has a Guo instantiation.
-inline bool tile_supported(int tile, int lattice, int precision, int forcing = kForcingShift) {
+// forcing = kForcingGuo or model = kModelFE: the kernels that choose the
+// collision at run time (kinds 0 and 3) and the 64x6 TMA tile (34), which has
+// a Guo and an FE instantiation.
+inline bool tile_supported(int tile, int lattice, int precision, int forcing = kForcingShift, int model = kModelSC) {
     if (tile < 0 || tile >= kNumTiles) return false;
-    if (forcing == kForcingGuo && kTiles[tile].kind != 0 && kTiles[tile].kind != 3 && tile != 34) return false;
+    if ((forcing == kForcingGuo || model == kModelFE) && kTiles[tile].kind != 0 && kTiles[tile].kind != 3 &&
+        tile != 34)
+        return false;
     switch (kTiles[tile].kind) {
         case 0: return true;
         case 1: return lattice == 1 && precision == 1;
@@ -97,7 +102,7 @@ inline bool tile_supported(int tile, int lattice, int precision, int forcing = k
 // Size rules beyond the lattice kind and precision: the TMA boxes need the
 // lattice to span at least one tile in x and y.
 inline bool tile_fits(int tile, const Plan& p) {
-    if (!tile_supported(tile, p.lattice, p.precision, p.forcing)) return false;
+    if (!tile_supported(tile, p.lattice, p.precision, p.forcing, p.model)) return false;
     const TileShape& t = kTiles[tile];
     if (t.kind == 5 || t.kind == 6) {
         const int tiles_x = (p.nx + t.tx - 1) / t.tx, tiles_y = (p.ny + t.ty - 1) / t.ty;

@@ -227,6 +227,113 @@ __device__ __forceinline__ void node_collide_guo(C (&f)[2][L::Q], C rA, C rB, co
     node_relax_guo<L, C>(f[1], rB, u, FB, omega_B);
 }
 
+// ---- Free-energy (FE) two-population model (Sec. 2.2) ----------------------
+// The storage's two "species" hold f_i (density and momentum) and g_i (order
+// parameter): rho = sum_i f_i, phi = sum_i g_i, u = sum_i f_i c_i / rho.  The
+// free energy is the Eq. FEtau functional with coupling g and gradient
+// coefficient kappa; its derivatives come from the isotropic lattice stencils
+//   grad phi = 3 sum_i w_i c_i phi(x + c_i),  lap phi = 6 sum_i w_i (phi(x + c_i) - phi(x)),
+// formed over opposite pairs like the SC force.  nbr(1, i) = phi(x + c_i).
+template <class L, class C, class Nbr>
+__device__ __forceinline__ void node_fe_derivs(const Nbr& nbr, C phi0, C (&gp)[3], C& lp) {
+    using A = Ar<C>;
+    static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
+    gp[0] = gp[1] = gp[2] = (C)0;
+    C lap = (C)0;
+    const C two_phi = A::add(phi0, phi0);
+#pragma unroll
+    for (int i = 1; i < L::Q; i += 2) {
+        const C w = (C)L::w(i);
+        const C p = nbr(1, i), m = nbr(1, i + 1);
+        const C d = A::sub(p, m);  // phi(x + c_i) - phi(x - c_i)
+#pragma unroll
+        for (int k = 0; k < L::D; ++k) {
+            if (L::c(i, k) == 1) gp[k] = A::fma(w, d, gp[k]);
+            if (L::c(i, k) == -1) gp[k] = A::fma(-w, d, gp[k]);
+        }
+        lap = A::fma(w, A::sub(A::add(p, m), two_phi), lap);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gp[k] = A::mul((C)3, gp[k]);
+    lp = A::mul((C)6, lap);
+}
+
+// ln x for the chemical potential (the library's log, FP32 or FP64).
+__device__ __forceinline__ float fe_log(float x) { return logf(x); }
+__device__ __forceinline__ double fe_log(double x) { return log(x); }
+
+// The FE collision of one node (Eqs. FE1, FE2) with the second-order Hermite
+// equilibria that meet Eqs. EQFE1 and EQFE2:
+//   mu  = cs2/2 ln((rho + phi)/(rho - phi)) - g cs2 phi/2 - kappa lap phi
+//   p_b = cs2 rho + g cs2 (rho^2 - phi^2)/4,  s = p_b - kappa phi lap - kappa/2 |grad|^2 - cs2 rho
+//   f_i^eq = w_i [rho + 3 rho c.u + 9/2 (s (c.c - D cs2) + kappa ((c.grad)^2 - cs2 |grad|^2)
+//                 + rho ((c.u)^2 - cs2 u.u))]
+//   g_i^eq = w_i [phi + 3 phi c.u + 9/2 ((Gamma mu - cs2 phi)(c.c - D cs2) + phi ((c.u)^2 - cs2 u.u))]
+// (the Hermite term (c_a c_b - cs2 d_ab) M_ab / (2 cs2^2) written out for the
+// isotropic-plus-dyadic M of each population), rest components closed as
+// rho - sum_{i>0} and phi - sum_{i>0}.  omega = 1/tau, omega_g = 1/tau_g.
+template <class L, class C>
+__device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, const C (&gp)[3], C lp, C omega,
+                                                C omega_g, C g, C kappa, C gamma) {
+    using A = Ar<C>;
+    constexpr C cs2 = (C)(1.0 / 3.0);
+    C j[3];
+    node_momentum<L, C>(f[0], j);
+    const C inv_rho = A::rcp(rho);
+    C u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = A::mul(j[d], inv_rho);
+    const C uu = L::D == 3 ? A::fma(u[0], u[0], A::fma(u[1], u[1], A::mul(u[2], u[2])))
+                           : A::fma(u[0], u[0], A::mul(u[1], u[1]));
+    const C gg = L::D == 3 ? A::fma(gp[0], gp[0], A::fma(gp[1], gp[1], A::mul(gp[2], gp[2])))
+                           : A::fma(gp[0], gp[0], A::mul(gp[1], gp[1]));
+    const C mu = A::sub(A::sub(A::mul(A::mul((C)0.5, cs2), fe_log(A::mul(A::add(rho, phi), A::rcp(A::sub(rho, phi))))),
+                               A::mul(A::mul((C)0.5, A::mul(g, cs2)), phi)),
+                        A::mul(kappa, lp));
+    const C pb = A::fma(A::mul((C)0.25, A::mul(g, cs2)), A::mul(A::sub(rho, phi), A::add(rho, phi)), A::mul(cs2, rho));
+    const C s = A::sub(A::sub(A::sub(pb, A::mul(A::mul(kappa, phi), lp)), A::mul(A::mul((C)0.5, kappa), gg)),
+                       A::mul(cs2, rho));
+    const C sg = A::sub(A::mul(gamma, mu), A::mul(cs2, phi));
+    const C ku = A::mul(cs2, uu), kg = A::mul(cs2, gg);
+    C feq[L::Q], geq[L::Q];
+    C fsum = (C)0, gsum = (C)0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        C cu = (C)0, cg = (C)0;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) {
+            if (L::c(i, d) == 1) {
+                cu = A::add(cu, u[d]);
+                cg = A::add(cg, gp[d]);
+            }
+            if (L::c(i, d) == -1) {
+                cu = A::sub(cu, u[d]);
+                cg = A::sub(cg, gp[d]);
+            }
+        }
+        int c2 = 0;
+#pragma unroll
+        for (int d = 0; d < L::D; ++d) c2 += L::c(i, d) * L::c(i, d);
+        const C iso = (C)((double)c2 - (double)L::D / 3.0);  // c.c - D cs2
+        const C quad_u = A::sub(A::mul(cu, cu), ku);       // (c.u)^2 - cs2 u.u
+        const C quad_g = A::sub(A::mul(cg, cg), kg);
+        const C w = (C)L::w(i);
+        const C hf = A::fma(s, iso, A::fma(kappa, quad_g, A::mul(rho, quad_u)));
+        feq[i] = A::mul(w, A::fma((C)4.5, hf, A::fma(A::mul((C)3, rho), cu, rho)));
+        const C hg = A::fma(sg, iso, A::mul(phi, quad_u));
+        geq[i] = A::mul(w, A::fma((C)4.5, hg, A::fma(A::mul((C)3, phi), cu, phi)));
+        fsum = A::add(fsum, feq[i]);
+        gsum = A::add(gsum, geq[i]);
+    }
+    feq[0] = A::sub(rho, fsum);
+    geq[0] = A::sub(phi, gsum);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        f[0][i] = A::fma(omega, A::sub(feq[i], f[0][i]), f[0][i]);
+        f[1][i] = A::fma(omega_g, A::sub(geq[i], f[1][i]), f[1][i]);
+    }
+}
+
 // The collision of the lattice's forcing scheme, chosen at run time (kernels
 // whose launch shapes accept either scheme).
 template <class L, class C>
@@ -236,6 +343,24 @@ __device__ __forceinline__ void node_collide_any(int forcing, C (&f)[2][L::Q], C
         node_collide_guo<L, C>(f, rA, rB, gA, gB, omega_A, omega_B);
     else
         node_collide<L, C>(f, rA, rB, gA, gB, omega_A, omega_B, tau_A, tau_B);
+}
+
+// The whole node update after the pulls: the SC force (and body force) with
+// the lattice's forcing scheme, or the FE derivatives and collision, chosen at
+// run time.  r0, r1: the two population sums of the node (rho_A, rho_B for SC;
+// rho, phi for FE); nbr(s, i) returns the neighbour's sum s at x + c_i.
+template <class L, class C, class Args, class Nbr>
+__device__ __forceinline__ void node_update(const Args& a, int y, const Nbr& nbr, C (&f)[2][L::Q], C r0, C r1) {
+    if (a.model == kModelFE) {
+        C gp[3], lp;
+        node_fe_derivs<L, C>(nbr, r1, gp, lp);
+        node_collide_fe<L, C>(f, r0, r1, gp, lp, a.omega_A, a.omega_B, a.G, a.kappa, a.gamma);
+        return;
+    }
+    C gA[3], gB[3];
+    node_force<L, C>(nbr, a.G, gA, gB);
+    node_body_force<C>(a.body_A, y, a.ny, gA, gB);
+    node_collide_any<L, C>(a.forcing, f, r0, r1, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
 }
 
 }  // namespace lbmsc

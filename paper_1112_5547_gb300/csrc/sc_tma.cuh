@@ -304,13 +304,19 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
             const int sl = L::c(i, 2) == 0 ? sc : (L::c(i, 2) > 0 ? sp : sm_);
             return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
         };
-        C gA[3], gB[3];
-        node_force<L, C>(nbr, a.G, gA, gB);
-        node_add_body<C>(a.body_A, kolmo, gA, gB);
-        if constexpr (FORCING == kForcingGuo)
-            node_collide_guo<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B);
-        else
-            node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        if constexpr (FORCING == kSchemeFE) {
+            C gp[3], lp;
+            node_fe_derivs<L, C>(nbr, rB, gp, lp);
+            node_collide_fe<L, C>(X, rA, rB, gp, lp, a.omega_A, a.omega_B, a.G, a.kappa, a.gamma);
+        } else {
+            C gA[3], gB[3];
+            node_force<L, C>(nbr, a.G, gA, gB);
+            node_add_body<C>(a.body_A, kolmo, gA, gB);
+            if constexpr (FORCING == kForcingGuo)
+                node_collide_guo<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B);
+            else
+                node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
+        }
         if (owner) store_node<L, St>(a, gx, gy, zof(q), X);
     };
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
@@ -365,8 +371,9 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     return r < 0 ? -1 : nplanes;
 }
 
-// FORCING: the collision's forcing scheme, fixed at compile time (kForcingGuo
-// is instantiated for the 64x6 FP32 tile only).
+// FORCING: the collision, fixed at compile time: kForcingShift, kForcingGuo or
+// kSchemeFE (the FE model); the last two are instantiated for the 64x6 FP32
+// tile only.
 template <int TX, int TY, int S, class St = float, int FORCING = kForcingShift>
 __global__ void __launch_bounds__(TX* TY, 1)
     sc_step_tma_kernel(const __grid_constant__ TmaMaps maps, const LatticeArgs<St> a, int* __restrict__ err) {

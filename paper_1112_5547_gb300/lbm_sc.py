@@ -43,6 +43,8 @@ REST_PRECISIONS = (LBM_F32_STORE_BF16_REST, LBM_F32_STORE_F16_REST)
 LBM_FORCING_SHIFT = 0
 LBM_FORCING_GUO = 1
 FORCINGS = {"shift": LBM_FORCING_SHIFT, "guo": LBM_FORCING_GUO}
+LBM_MODEL_SC = 0
+LBM_MODEL_FE = 1
 
 # Every entry point declared in include/lbm_sc.h.
 EXPORTS = (
@@ -72,8 +74,8 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
         return True
     tx, ty = BATCH_TILES[tile]
     p = lattice.params
-    return (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT and p.nx >= tx
-            and p.ny >= ty)
+    return (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT
+            and p.model == LBM_MODEL_SC and p.nx >= tx and p.ny >= ty)
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
 # the shared-memory stages of the persistent cp.async kernel (0: register kernel).
@@ -96,14 +98,14 @@ TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2),
 TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0) + (256,) * 12
 
 
-def tile_supported(tile: int, lattice: int, precision: int, forcing: int = 0) -> bool:
+def tile_supported(tile: int, lattice: int, precision: int, forcing: int = 0, model: int = 0) -> bool:
     """Mirror of the library's rule: kinds 1 and 5 need D3Q19 with FP32 storage, kind 2 D3Q19 without
     rest-offset storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage; Guo forcing
-    runs on kinds 0 and 3 and on tile 34."""
+    and the FE model run on kinds 0 and 3 and on tile 34."""
     if not 0 <= tile < len(TILES):
         return False
     kind = TILE_KIND[tile]
-    if forcing == LBM_FORCING_GUO and kind not in (0, 3) and tile != 34:
+    if (forcing == LBM_FORCING_GUO or model == LBM_MODEL_FE) and kind not in (0, 3) and tile != 34:
         return False
     if kind in (0, 3):
         return True
@@ -120,7 +122,9 @@ class lbm_sc_params(ctypes.Structure):
     _fields_ = [("lattice", ctypes.c_int32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("forcing", ctypes.c_int32),
                 ("tau_A", ctypes.c_double), ("tau_B", ctypes.c_double), ("G", ctypes.c_double),
-                ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double), ("body_A", ctypes.c_double)]
+                ("rho_ref_A", ctypes.c_double), ("rho_ref_B", ctypes.c_double), ("body_A", ctypes.c_double),
+                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("kappa", ctypes.c_double),
+                ("gamma", ctypes.c_double)]
 
 
 class lbm_sc_window(ctypes.Structure):
@@ -212,7 +216,7 @@ def _check(status: int, where: str):
 
 def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
                 rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, body_A: float = 0.0,
-                forcing="shift") -> lbm_sc_params:
+                forcing="shift", model=LBM_MODEL_SC, kappa: float = 0.0, gamma: float = 0.0) -> lbm_sc_params:
     """Parameters for a lattice of numpy-style shape (ny, nx) or (nz, ny, nx);
     body_A is the Kolmogorov forcing amplitude of Eq. kolmo (0: none); forcing
     "shift" (the paper's velocity shift) or "guo" (lbm_forcing)."""
@@ -224,7 +228,7 @@ def make_params(lattice: int, shape, tau_A: float, tau_B: float, G: float, preci
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     frc = FORCINGS[forcing] if isinstance(forcing, str) else int(forcing)
     return lbm_sc_params(int(lattice), prec, nx, ny, nz, frc, float(tau_A), float(tau_B), float(G),
-                         float(rho_ref_A), float(rho_ref_B), float(body_A))
+                         float(rho_ref_A), float(rho_ref_B), float(body_A), int(model), 0, float(kappa), float(gamma))
 
 
 # ---- one Python function per C entry point ----------------------------------
@@ -355,6 +359,17 @@ class Window:
         return lbm_sc_window(float(c[0]), float(c[1]), float(c[2]), float(self.r_in), float(self.r_out))
 
 
+def FELattice(lattice: int, shape, tau: float, tau_g: float, g: float, precision="f32", kappa: float = None,
+              gamma: float = 1.0, device="cuda", stream=None) -> "Lattice":
+    """A lattice of the free-energy model of Sec. 2.2 (lbm_model LBM_MODEL_FE):
+    relaxation times tau (f) and tau_g (g), coupling g of the Eq. FEtau functional,
+    gradient coefficient kappa (default g cs2^2 / 4, as in Eq. FEtau) and Gamma."""
+    if kappa is None:
+        kappa = g / 36.0
+    return Lattice(lattice, shape, tau, tau_g, g, precision, device=device, stream=stream, model=LBM_MODEL_FE,
+                   kappa=kappa, gamma=gamma)
+
+
 class Lattice:
     """A lattice whose workspace is a torch uint8 tensor on ``device``.
 
@@ -365,12 +380,12 @@ class Lattice:
 
     def __init__(self, lattice: int, shape, tau_A: float, tau_B: float, G: float, precision="f32",
                  rho_ref_A: float = 0.0, rho_ref_B: float = 0.0, device="cuda", stream=None, body_A: float = 0.0,
-                 forcing="shift"):
+                 forcing="shift", model=LBM_MODEL_SC, kappa: float = 0.0, gamma: float = 0.0):
         import torch
 
         self.torch = torch
         self.params = make_params(lattice, shape, tau_A, tau_B, G, precision, rho_ref_A, rho_ref_B, body_A,
-                                  forcing)
+                                  forcing, model, kappa, gamma)
         self.shape = tuple(int(s) for s in shape)
         self.lattice = int(lattice)
         self.D = 2 if self.lattice == LBM_D2Q9 else 3

@@ -292,3 +292,30 @@ def test_forcing_scheme_rules(lib):
                         lib.lbm_sc_set_tuning(h, t, 0)
         finally:
             lib.lbm_sc_destroy(h)
+
+
+def test_fe_model_rules(lib):
+    """lbm_model: the FE model takes FP64 / FP32 storage only, no body force and
+    the shift forcing value; its tiles are those of Guo forcing."""
+    fe = dict(model=lib.LBM_MODEL_FE, kappa=0.05, gamma=0.5)
+    ok = lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "f32", **fe)
+    assert lib.lbm_sc_workspace_bytes(ok) > 0
+    for bad in (lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "bf16", **fe),
+                lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "f32", body_A=1e-5, **fe),
+                lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "f32", forcing="guo", **fe),
+                lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "f32", model=2),
+                lib.make_params(lib.LBM_D3Q19, (8, 8, 8), 1.0, 1.0, 2.5, "f32", model=lib.LBM_MODEL_FE,
+                                kappa=float("nan"), gamma=0.5)):
+        assert lib.lbm_sc_workspace_bytes(bad) == 0
+    h = lib.lbm_sc_create(ok, 256 * 1024, lib.lbm_sc_workspace_bytes(ok), 0)
+    try:
+        for t in range(len(lib.TILES)):
+            good = lib.tile_supported(t, lib.LBM_D3Q19, lib.LBM_F32, 0, lib.LBM_MODEL_FE)
+            assert good == (lib.TILE_KIND[t] in (0, 3) or t == 34)
+            if good and lib.TILE_KIND[t] in (0, 3):
+                lib.lbm_sc_set_tuning(h, t, 0)
+            elif not good:
+                with pytest.raises(lib.LbmError):
+                    lib.lbm_sc_set_tuning(h, t, 0)
+    finally:
+        lib.lbm_sc_destroy(h)

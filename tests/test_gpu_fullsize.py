@@ -79,14 +79,18 @@ def _decoded_window(sc, lat, centre, radius):
     return f
 
 
-def _oracle_window_step(oracle_mod, f_gpu, tau_A, tau_B, G, body=(0.0, 0, 0), forcing="shift"):
+def _oracle_window_step(oracle_mod, f_gpu, tau_A, tau_B, G, body=(0.0, 0, 0), forcing="shift", fe=None):
     """One oracle step of the periodic window; moments of its centre node.
-    body = (A, global y of the window's row 0, L_y) for the Kolmogorov forcing."""
+    body = (A, global y of the window's row 0, L_y) for the Kolmogorov forcing;
+    fe = (kappa, Gamma) for the free-energy model (tau_A, tau_B, G = tau, tau_g, g)."""
     c_or, _ = oracle_mod.lattice(1)
     perm = [int(np.nonzero((GPU_C3 == c).all(1))[0][0]) for c in c_or]  # oracle i -> GPU i
     W = f_gpu.shape[-1]
-    o = oracle_mod.OracleSC(1, (W, W, W), tau_A, tau_B, G, body_A=body[0], body_y0=body[1], body_ly=body[2],
-                            forcing=forcing)
+    if fe is not None:
+        o = oracle_mod.OracleFE(1, (W, W, W), tau_A, tau_B, G, kappa=fe[0], gamma=fe[1])
+    else:
+        o = oracle_mod.OracleSC(1, (W, W, W), tau_A, tau_B, G, body_A=body[0], body_y0=body[1], body_ly=body[2],
+                                forcing=forcing)
     # oracle populations: node-major (N, 2, Q), node x + W (y + W z), oracle order
     o.f[:] = f_gpu[:, perm].transpose(2, 3, 4, 0, 1).reshape(W ** 3, 2, len(perm))
     o.step(1)
@@ -113,7 +117,8 @@ def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4, rho
         f = _decoded_window(sc, lat, pt, 3)
         body = (lat.params.body_A, pt[1] - 3, lat.params.ny)
         forcing = "guo" if lat.params.forcing == sc.LBM_FORCING_GUO else "shift"
-        ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G, body, forcing))
+        fe = (lat.params.kappa, lat.params.gamma) if lat.params.model == sc.LBM_MODEL_FE else None
+        ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G, body, forcing, fe))
     lat.step(1)
     rA, rB, u, _ = lat.moments()
     for pt, (oa, ob, ou) in zip(pts, ref):
@@ -156,6 +161,24 @@ def test_512_sampled_nodes_vs_oracle(sc, oracle_mod, precision, tol_rho, tol_u, 
                    rho_abs=absolute)
     d = lat.diagnostics()
     assert d["status"] == sc.LBM_OK
+    del lat
+    torch.cuda.empty_cache()
+
+
+def test_512_fe_sampled_nodes_vs_oracle(sc, oracle_mod):
+    """The free-energy model (Sec. 2.2) on the bench's 512^3 lattice in its TMA
+    launch shape (tile 34, its FE instance) and in the register kernel (tile
+    4): sampled nodes one by one against the FE oracle's window step (a node
+    after one step depends on populations within distance 2)."""
+    import torch
+    L = 512
+    rA, rB = inputs.drop((L, L, L), L / 4, rho_hi=0.9, rho_lo=0.14, seed=2, dtype=np.float32)
+    lat = sc.FELattice(1, (L, L, L), 1.0, 1.0, 2.5, "f32", gamma=0.5).init(rA, rB)
+    del rA, rB
+    lat.set_tuning(34, 32)
+    _check_sampled(sc, oracle_mod, lat, _samples(L, (64, 6), 32), 1e-5, 1e-6)
+    lat.set_tuning(4, 64)
+    _check_sampled(sc, oracle_mod, lat, _samples(L, n_random=4, seed=8), 1e-5, 1e-6, steps_before=1)
     del lat
     torch.cuda.empty_cache()
 
