@@ -284,3 +284,6 @@ class OracleFE:
 
 if __name__ == "__main__":  # pragma: no cover - manual build helper
     print(build(force="--force" in sys.argv))
+
+
+from .pfm import OraclePFM  # noqa: E402  (the phase-field oracle of Sec. 3)

@@ -675,3 +675,88 @@ def test_fe_spinodal_rate_matches_the_sc_theory(oracle_mod, tau, tau_g, gt):
     rate = np.log(a1 / a2) / 1000.0
     theory = rho * (tau - 0.5) * (CS2 * (1 / rho - gt / 2) * k * k + gt / 4 * CS2 * CS2 * k ** 4)
     assert abs(rate / theory - 1) < 1e-2
+
+
+# --- phase-field model (PFM), Sec. 3 --------------------------------------------
+def test_pfm_linear_mode_follows_the_ab2_cn_recurrence_and_the_sc_rate(oracle_mod):
+    """u = 0, a small phi mode: the scheme of Eqs. eq11-eq13 is linear in it, so the
+    mode amplitude must follow the two-level recurrence
+    a_{n+1} (1 + dt lam/2) = a_n (1 - dt lam/2) + dt (3 sig a_n - sig a_{n-1})/2
+    with lam = D (2 k^2 + (dt D/2) k^4) (implicit part) and sig = -D k^2 (2/(g_tau rho)
+    - 3) - D (xi^2 - dt D/2) k^4 (explicit part), a_{-1} = a_0; and its rate must be
+    the continuum omega = D k^2 (2/(g_tau rho) - 1 + xi^2 k^2), which is the SC linear
+    theory rho (tau - 1/2)[cs2 (1/rho - g_tau/2) k^2 + g_tau cs2^2 k^4/4] (the matching
+    of Sec. 3)."""
+    L, rho, tau, g, dt, eps = 64, 1.0, 0.8, 1.0, 1.0, 1e-6
+    x = np.arange(L)
+    s = np.sin(2 * np.pi * x / L)
+    o = oracle_mod.OraclePFM((4, L), rho, tau, g, dt).init(eps * np.broadcast_to(s, (4, L)))
+    amps = []
+    for _ in range(60):
+        p, _ = o.step(1).fields()
+        amps.append(2 * (p * s).mean())
+    k2 = (2 * np.pi / L) ** 2
+    D, xi2, gt = o.Dc, o.xi2, o.g_tau
+    lam = D * (2 * k2 + dt * D / 2 * k2 * k2)
+    sig = -D * k2 * (2 / (gt * rho) - 3) - D * (xi2 - dt * D / 2) * k2 * k2
+    a_prev = a = eps
+    rec = []
+    for _ in range(60):
+        a_prev, a = a, (a * (1 - dt * lam / 2) + dt * (3 * sig * a - sig * a_prev) / 2) / (1 + dt * lam / 2)
+        rec.append(a)
+    assert np.abs(np.array(amps) - rec).max() < 1e-11 * eps
+    omega = rho * (tau - 0.5) * (CS2 * (1 / rho - gt / 2) * k2 + gt / 4 * CS2 * CS2 * k2 * k2)
+    rate = np.log(amps[20] / amps[50]) / (30 * dt)
+    assert abs(rate / omega - 1) < 1e-4
+
+
+def test_pfm_shear_wave_decays_by_the_crank_nicolson_factor(oracle_mod):
+    """u_x = U sin(k y), phi = 0: the nonlinear and capillary terms vanish, so every
+    step multiplies the mode by (1 - dt nu k^2/2)/(1 + dt nu k^2/2), nu = cs2 (tau - 1/2)."""
+    L = 48
+    o = oracle_mod.OraclePFM((L, 4), 1.0, 0.9, 1.0, 0.7)
+    u = np.zeros((L, 4, 2))
+    u[..., 0] = 1e-3 * np.sin(2 * np.pi * np.arange(L) / L)[:, None]
+    o.init(np.zeros((L, 4)), u).step(25)
+    k2 = (2 * np.pi / L) ** 2
+    f = (1 - 0.7 * o.nu * k2 / 2) / (1 + 0.7 * o.nu * k2 / 2)
+    np.testing.assert_allclose(o.fields()[1][..., 0], u[..., 0] * f ** 25, rtol=0, atol=1e-17)
+    assert abs(o.nu - CS2 * 0.4) < 1e-15
+
+
+def test_pfm_drop_keeps_div_u_mass_and_momentum(oracle_mod):
+    """A 3D drop with a divergence-free random start: div u stays zero (projected
+    right-hand sides, component-wise implicit viscosity), sum phi and sum u stay."""
+    shape = (16, 20, 24)
+    rA, rB = inputs.drop(shape, 5, rho_hi=1.2, rho_lo=0.2, seed=2)
+    rng = np.random.default_rng(1)
+    o = oracle_mod.OraclePFM(shape, 1.4, 0.6, 0.3, 0.1)  # explicit log term: dt small on a width-2 interface
+    uh = [np.fft.fftn(rng.normal(size=shape) * 1e-3) for _ in range(3)]
+    k = [o._kx(a) for a in range(3)]  # first-derivative wavenumbers (Nyquist zeroed)
+    k2 = np.where(o.kd2 == 0, 1, o.kd2)
+    kU = sum(k[a] * uh[a] for a in range(3))
+    u0 = np.stack([np.real(np.fft.ifftn(np.where(o.k2 == 0, 0, uh[a] - k[a] * kU / k2))) for a in range(3)], -1)
+    o.init(rA - rB, u0).step(40)
+    phi, u = o.fields()
+    div = sum(np.real(np.fft.ifftn(1j * k[a] * np.fft.fftn(u[..., a]))) for a in range(3))
+    assert np.abs(div).max() < 1e-15
+    assert abs(phi.sum() - (rA - rB).sum()) < 1e-11
+    assert np.abs(u.sum((0, 1, 2))).max() < 1e-13
+    rest = oracle_mod.OraclePFM(shape, 1.4, 0.6, 0.3, 0.1).init(rA - rB).step(40)
+    assert np.abs(rest.fields()[1]).max() > 1e-6  # the capillary force moves a fluid at rest
+
+
+def test_pfm_coexistence_matches_the_paper_example(oracle_mod):
+    """The paper's Sec. 4 example (rho = 1.4, g_tau = 1.804 -> phi = +-1) in the PFM:
+    a slab relaxes to bulk phases with mu_tau = 0, ln((rho+phi)/(rho-phi)) = g_tau phi,
+    within 5 % of phi = 1 (the same coexistence as the SC and FE models)."""
+    with open(os.path.join(GOLDEN, "paper_sec4_coexistence.json")) as fh:
+        gold = json.load(fh)
+    L, tau, rho, phi0 = 64, 0.6, gold["rho"], gold["phi_bulk"]
+    gt = gold["tau"] * gold["g_AB"] / (gold["tau"] - 0.5)
+    rA, rB = inputs.slab((4, L), L / 4, rho_hi=(rho + phi0) / 2, rho_lo=(rho - phi0) / 2, noise=0.0)
+    o = oracle_mod.OraclePFM((4, L), rho, tau, gt * (tau - 0.5) / tau, 0.5).init(rA - rB).step(8000)
+    phi, _ = o.fields()
+    pi = phi[0, L // 2]
+    assert abs(pi - phi0) < 0.05 and abs(phi[0, 0] + phi0) < 0.05
+    assert abs(np.log((rho + pi) / (rho - pi)) / (gt * pi) - 1) < 1e-2
