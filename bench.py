@@ -9,13 +9,14 @@ One timed "step" is one lattice time step (one fused-kernel launch) over all
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--L 512] [--precision f32|bf16|f16|bf16_rest|f16_rest|f64]
                     [--no-e2e] [--no-cpu-baseline] [--no-batch] [--serve-requests 24]
-                    [--no-storage16] [--no-kolmogorov] [--no-guo] [--no-fe]
+                    [--no-storage16] [--no-kolmogorov] [--no-guo] [--no-fe] [--no-pfm]
 
 Prints one JSON line (rank 0).  Beside the headline step it carries
 "storage16" (the same step with 16-bit rest-offset storage), "kolmogorov"
 (the same drop under the Kolmogorov forcing of Sec. 4.2), "guo" (the same
 drop with Guo forcing, Sec. 2.3), "fe" (the free-energy model of Sec. 2.2 on
-the same lattice), "batch"
+the same lattice), "pfm" (the phase-field model of Sec. 3 against the SC step
+on a 256^3 grid), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
 lattices stepped one at a time) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
@@ -79,6 +80,7 @@ def parse():
     ap.add_argument("--no-kolmogorov", action="store_true", help="skip the Kolmogorov-forced drop line")
     ap.add_argument("--no-guo", action="store_true", help="skip the Guo-forcing line")
     ap.add_argument("--no-fe", action="store_true", help="skip the free-energy model line")
+    ap.add_argument("--no-pfm", action="store_true", help="skip the phase-field model line")
     return ap.parse_args()
 
 
@@ -332,6 +334,47 @@ def fe_compare(L: int, steps: int, warmup: int, peak: float):
     return out
 
 
+def pfm_compare(L: int, steps: int, warmup: int):
+    """The pseudo-spectral phase-field model of Sec. 3 (libpfm.so: cuFFT plus the
+    library's kernels) against the SC step on the same L^3 grid and drop
+    (rho_A 1.2 / rho_B 0.2, tau = 0.6, g = 0.3, FP32): milliseconds per step of
+    each, CUDA events on one stream, and their ratio per step and per unit of
+    physical time (the PFM runs at dt = 0.1 here, the LBM at 1; the paper reports
+    T_PFM / T_SC = 2.9 for its 2D runs on CPUs, Fig. 6)."""
+    import torch
+    from paper_1112_5547_gb300 import inputs, lbm_sc, phase_field
+    st = torch.cuda.Stream()
+    rA, rB = inputs.drop((L, L, L), L / 4.0, rho_hi=1.2, rho_lo=0.2, seed=2, dtype=np.float32)
+    dt = 0.1
+
+    def timed(obj):
+        obj.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        obj.step(steps)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+    with torch.cuda.stream(st):
+        s = phase_field.PFM((L, L, L), 1.4, 0.6, 0.3, dt, "f32", stream=st).init(rA - rB)
+        ms_pfm = timed(s)
+        phi, _ = s.fields()
+        finite = bool(torch.isfinite(phi).all())
+        del s, phi
+        torch.cuda.empty_cache()
+        lat = lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 0.6, 0.6, 0.3, "f32", stream=st).init(rA, rB)
+        lat.set_tuning(34, 32)
+        ms_sc = timed(lat)
+        del lat
+        torch.cuda.empty_cache()
+    N = L ** 3
+    return {"workload": "3D %d^3 drop, rho 1.2 / 0.2, tau 0.6, g 0.3, FP32; PFM dt = %g" % (L, dt),
+            "ms_per_step_pfm": ms_pfm, "ms_per_step_sc": ms_sc, "ratio_per_step": ms_pfm / ms_sc,
+            "ratio_per_time_unit": ms_pfm / dt / ms_sc, "pfm_mnodes_per_s": N / ms_pfm / 1e3,
+            "transforms_per_step": 19, "steps": steps, "finite": finite,
+            "parity": "tests/test_gpu_pfm.py (FP64 1e-10, FP32 1e-5 vs the numpy oracle; 128^3 whole field)"}
+
+
 def kolmogorov_compare(L: int, steps: int, warmup: int, peak: float, A: float = 1e-6):
     """The headline drop under the Kolmogorov forcing of Eq. kolmo (Sec. 4.2),
     F_x = rho A sin(2 pi y / L), A = 1e-6 as in the paper: the same fused step
@@ -545,6 +588,9 @@ def main():
     ff = None
     if not args.no_fe and rank == 0 and prec == "f32":
         ff = fe_compare(L, max(10, K // 2), args.warmup, peak)
+    pm = None
+    if not args.no_pfm and rank == 0 and prec == "f32":
+        pm = pfm_compare(256, max(10, K // 2), args.warmup)
     if not args.no_batch and rank == 0:
         bt = batch_compare(args.batch_steps, args.warmup)
     sv = None
@@ -591,6 +637,8 @@ def main():
         line["guo"] = gf
     if ff is not None:
         line["fe"] = ff
+    if pm is not None:
+        line["pfm"] = pm
     if cb is not None:
         line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -1,8 +1,10 @@
-"""Build liblbm_sc.so in-tree with nvcc for sm_103a (GB300).
+"""Build liblbm_sc.so and libpfm.so in-tree with nvcc for sm_103a (GB300).
 
 Each .cu file under csrc/ compiles to an object in parallel; the objects link
 into a shared library with the CUDA runtime linked statically, so the library
 exports only the C ABI of include/lbm_sc.h and needs no torch at link time.
+csrc_pfm/ (the phase-field solver, include/pfm.h) links the same way into
+libpfm.so, which also links cuFFT.
 """
 from __future__ import annotations
 
@@ -19,6 +21,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblbm_sc.so")
+PFM_CSRC = os.path.join(PKG, "csrc_pfm")
+PFM_LIB = os.path.join(PKG, "libpfm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -42,10 +46,11 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PFM_LIB):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PFM_LIB))
+    deps = _deps() + sorted(glob.glob(os.path.join(PFM_CSRC, "*.cu"))) + [os.path.join(ROOT, "include", "pfm.h")]
+    return all(os.path.getmtime(d) <= t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
@@ -70,15 +75,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     # edited while it compiles is newer and triggers the next build
     t_start = time.time()
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    os.utime(LIB, (t_start, t_start))
+    pfm_srcs = sorted(glob.glob(os.path.join(PFM_CSRC, "*.cu")))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs) + len(pfm_srcs), os.cpu_count() or 1))) as ex:
+        futs = [ex.submit(compile_one, s) for s in srcs + pfm_srcs]
+        objs = [f.result() for f in futs]
+    for lib, lib_objs, extra in ((LIB, objs[:len(srcs)], []), (PFM_LIB, objs[len(srcs):], ["-lcufft"])):
+        tmp = lib + ".tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-cudart", "static", "-o", tmp, *lib_objs, *extra]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        os.replace(tmp, lib)
+        os.utime(lib, (t_start, t_start))
     return LIB
 
 

@@ -319,3 +319,37 @@ def test_fe_model_rules(lib):
                     lib.lbm_sc_set_tuning(h, t, 0)
     finally:
         lib.lbm_sc_destroy(h)
+
+
+def test_pfm_library_exports_and_layout(lib, tmp_path):
+    """libpfm.so loads without a GPU, exports every pfm_ entry point of
+    include/pfm.h, its parameter struct has the C layout, and the workspace size
+    validates the parameters."""
+    import subprocess
+    from paper_1112_5547_gb300 import phase_field as pf
+    src = open(os.path.join(ROOT, "include", "pfm.h")).read()
+    declared = set(re.findall(r"\b(pfm_\w+)\s*\(", re.sub(r"/\*.*?\*/", "", src, flags=re.S)))
+    assert declared == set(pf.EXPORTS)
+    so = ctypes.CDLL(pf.PFM_LIB)
+    for name in declared:
+        assert hasattr(so, name), name
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pfm.h"', "int main(void) {",
+             'printf("size %zu\\n", sizeof(pfm_params));']
+    for field, _ in pf.pfm_params._fields_:
+        lines.append('printf("%s %%zu\\n", offsetof(pfm_params, %s));' % (field, field))
+    lines.append("return 0; }")
+    (tmp_path / "l.c").write_text("\n".join(lines))
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(tmp_path / "l"), str(tmp_path / "l.c")],
+                   check=True)
+    got = dict(x.split() for x in subprocess.run([str(tmp_path / "l")], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(pf.pfm_params)
+    for field, _ in pf.pfm_params._fields_:
+        assert int(got[field]) == getattr(pf.pfm_params, field).offset, field
+    ok = pf.make_params((16, 20, 24), 1.4, 0.6, 0.3, 0.1, "f32")
+    n = pf.workspace_bytes(ok)
+    R, C = 16 * 20 * 24, 16 * 20 * 13
+    assert n >= (8 * C * 2 + 8 * C * 2 + 8 * R + 11 * R + 11 * C * 2) * 4  # state, transform batches
+    for bad in (pf.make_params((16, 20, 24), 1.4, 0.5, 0.3, 0.1), pf.make_params((16, 20, 24), 1.4, 0.6, 0.3, 0.0),
+                pf.make_params((16, 20, 24), -1.0, 0.6, 0.3, 0.1), pf.make_params((1, 20), 1.4, 0.6, 0.3, 0.1)):
+        assert pf.workspace_bytes(bad) == 0
