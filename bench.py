@@ -182,8 +182,25 @@ def cpu_baseline(seconds: float, L: int = 128):
         if el >= seconds and n >= 2:
             break
     mlups = L ** 3 * n / el / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d steps in %.1f s" % (L, n, el)}
+    cores = oracle.num_threads()
+    # the same oracle on one core, on a 64^3 sample of the recipe (a few seconds)
+    oracle.set_num_threads(1)
+    try:
+        Ls = 64
+        rA, rB = drop_fields(Ls, np.float64)
+        o1 = oracle.OracleSC(1, (Ls, Ls, Ls), 1.0, 1.0, G).init(rA, rB)
+        t0 = time.perf_counter()
+        n1 = 0
+        while time.perf_counter() - t0 < seconds / 4 or n1 < 2:
+            o1.step(1)
+            n1 += 1
+        el1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d steps in %.1f s" % (L, n, el),
+            "single_core": {"value": Ls ** 3 * n1 / el1 / 1e6, "unit": "MLUPS",
+                            "sample": "D3Q19 %d^3 drop, 1 thread, %d steps in %.1f s" % (Ls, n1, el1)}}
 
 
 def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
