@@ -353,3 +353,17 @@ def test_pfm_library_exports_and_layout(lib, tmp_path):
     for bad in (pf.make_params((16, 20, 24), 1.4, 0.5, 0.3, 0.1), pf.make_params((16, 20, 24), 1.4, 0.6, 0.3, 0.0),
                 pf.make_params((16, 20, 24), -1.0, 0.6, 0.3, 0.1), pf.make_params((1, 20), 1.4, 0.6, 0.3, 0.1)):
         assert pf.workspace_bytes(bad) == 0
+
+
+def test_missing_libraries_fail_loudly(tmp_path):
+    """The product path has no CPU fallback: loading a library that is not there
+    raises instead of degrading."""
+    from paper_1112_5547_gb300 import lbm_sc, phase_field
+    for mod, name in ((lbm_sc, "liblbm_sc.so"), (phase_field, "libpfm.so")):
+        saved = mod._lib
+        mod._lib = None
+        try:
+            with pytest.raises(ImportError):
+                mod.load(str(tmp_path / name))
+        finally:
+            mod._lib = saved
