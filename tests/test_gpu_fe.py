@@ -145,3 +145,37 @@ def test_fe_matches_the_sc_spinodal_rate_on_gpu(sc):
         m = _fields(lat.step(1000))
         a2 = _mode_amp(m[0] - m[1], 1)
         assert abs(np.log(a1 / a2) / 1000.0 / theory - 1) < 1e-2, name
+
+
+def test_d2q9_batch_mixes_every_model_and_forcing(sc):
+    """One D2Q9 batch (z-marching batch tiles) holding an SC lattice, a
+    Kolmogorov-forced one, a Guo-forced one and an FE one, FP32 and FP64:
+    bitwise equal to stepping each alone."""
+    shapes = [(48, 64), (37, 50), (64, 40), (30, 72)]
+
+    def make(prec):
+        out = []
+        for k, shape in enumerate(shapes):
+            if k == 3:
+                rA, rB = _drop(shape, k)
+                out.append(sc.FELattice(0, shape, 0.9, 1.1, G_FE, prec, gamma=0.5).init(rA, rB))
+                continue
+            rA, rB = inputs.drop(shape, min(shape) / 4.0, seed=k)
+            kw = [{}, {"body_A": 2e-5}, {"forcing": "guo", "body_A": -1e-5}][k]
+            out.append(sc.Lattice(0, shape, 1.0, 0.8, 2.3, prec, **kw).init(rA, rB))
+        return out
+    for prec in ("f32", "f64"):
+        solo = make(prec)
+        for lat in solo:
+            lat.step(17)
+        ref = [_fields(lat) for lat in solo]
+        tiles = [t for t in range(len(sc.BATCH_TILES)) if all(sc.batch_tile_fits(t, lat) for lat in solo)]
+        assert tiles == [t for t in range(len(sc.BATCH_TILES)) if not sc.BATCH_TILE_TMA[t]]
+        for tile in tiles:
+            lats = make(prec)
+            b = sc.Batch(lats, tile=tile)
+            b.step(9).step(8)
+            for k, lat in enumerate(lats):
+                for x, y in zip(_fields(lat), ref[k]):
+                    assert np.array_equal(x, y), (prec, tile, k)
+            b.close()
