@@ -10,7 +10,11 @@
  *   F_s(x) = -G rho_s(x) sum_i w_i rho_s'(x + c_i) c_i             (Eq. FORCE)
  *
  * with the second-order equilibrium f^eq_i = w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u]
- * and fully periodic boundaries (Sec. 4).
+ * and fully periodic boundaries (Sec. 4).  Options of the same step (see
+ * lbm_sc_params): the Kolmogorov body force of Eq. kolmo (Sec. 4.2), Guo forcing
+ * in place of the velocity shift (lbm_forcing, Sec. 2.3), and the free-energy
+ * two-population model of Sec. 2.2 on the same storage (lbm_model).  The
+ * pseudo-spectral phase-field model of Sec. 3 has its own ABI (pfm.h).
  *
  * Conventions for every entry point:
  *   - The caller owns all device memory and the CUDA stream.  The library never
