@@ -760,3 +760,41 @@ def test_pfm_coexistence_matches_the_paper_example(oracle_mod):
     pi = phi[0, L // 2]
     assert abs(pi - phi0) < 0.05 and abs(phi[0, 0] + phi0) < 0.05
     assert abs(np.log((rho + pi) / (rho - pi)) / (gt * pi) - 1) < 1e-2
+
+
+def test_pfm_is_second_order_in_time(oracle_mod):
+    """Eq. eq11 is second order (AB2 for the explicit terms, CN for the implicit
+    ones): on a 2D drop, halving dt divides the error at a fixed time by about 4
+    (a first-order slip, such as a wrong AB2 weight, would give 2)."""
+    shape = (32, 32)
+    rA, rB = inputs.drop(shape, 8, rho_hi=1.2, rho_lo=0.2, seed=1, noise=0.0)
+
+    def run(dt):
+        o = oracle_mod.OraclePFM(shape, 1.4, 0.6, 0.3, dt).init(rA - rB)
+        return o.step(int(round(2.0 / dt))).fields()
+    ref = run(0.1 / 16)
+    e = [np.abs(run(dt)[0] - ref[0]).max() for dt in (0.1, 0.05, 0.025)]
+    assert 3.5 < e[0] / e[1] < 4.6 and 3.5 < e[1] / e[2] < 4.6, e
+
+
+def test_fe_laplace_law(oracle_mod):
+    """The FE model's pressure tensor (Eq. EQFE1 with the gradient terms) gives
+    drops whose bulk pressure jump follows Laplace's law dP = sigma / R in 2D
+    (Sec. 4.1): linear in 1/R (R^2 > 0.999) through the origin (intercept below
+    5 % of sigma / 8, the bar of the SC Laplace pin)."""
+    L, g = 64, 2.5
+    inv, dps = [], []
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    r = np.hypot(x - L / 2, y - L / 2)
+    for R in (10, 14, 18):
+        rA, rB = inputs.drop((L, L), R, rho_hi=0.9, rho_lo=0.14, seed=0, noise=0.0)
+        a, _, _, p = oracle_mod.OracleFE(0, (L, L), 1.0, 1.0, g, gamma=1.0).init(rA, rB).step(3000).moments()
+        rin, rout = a[r < R / 4].mean(), a[r > R + 8].mean()
+        Req = np.sqrt((a - rout).sum() / (rin - rout) / np.pi)
+        inv.append(1 / Req)
+        dps.append(p[r < Req / 4].mean() - p[r > Req + 8].mean())
+    A = np.vstack([inv, np.ones(3)]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, np.array(dps), rcond=None)
+    pred = A @ [slope, icpt]
+    r2 = 1 - ((np.array(dps) - pred) ** 2).sum() / ((np.array(dps) - np.mean(dps)) ** 2).sum()
+    assert slope > 0 and r2 > 0.999 and abs(icpt) < 0.05 * slope / 8, (slope, icpt, r2)
