@@ -179,3 +179,31 @@ def test_d2q9_batch_mixes_every_model_and_forcing(sc):
                 for x, y in zip(_fields(lat), ref[k]):
                     assert np.array_equal(x, y), (prec, tile, k)
             b.close()
+
+
+def test_fe_laplace_batch_on_gpu(sc):
+    """Five FE drops (R = 12..32 on 128^2, FP32) advanced as one ragged batch for
+    6000 steps: the bulk pressure jump follows Laplace's law dP = sigma / R
+    (R^2 > 0.999, intercept below 5 % of sigma / 8), as the oracle's FE model does."""
+    L, radii = 128, (12, 16, 20, 26, 32)
+    lats, fields = [], []
+    for R in radii:
+        rA, rB = inputs.drop((L, L), R, rho_hi=0.9, rho_lo=0.14, seed=0, noise=0.0)
+        lats.append(sc.FELattice(0, (L, L), 1.0, 1.0, G_FE, "f32", gamma=1.0).init(rA, rB))
+    b = sc.Batch(lats, tile=1)
+    b.step(6000)
+    y, x = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    r = np.hypot(x - L / 2, y - L / 2)
+    inv, dps = [], []
+    for R, lat in zip(radii, lats):
+        a, _, _, p = _fields(lat)
+        rin, rout = a[r < R / 4].mean(), a[r > R + 8].mean()
+        Req = np.sqrt((a - rout).sum() / (rin - rout) / np.pi)
+        inv.append(1 / Req)
+        dps.append(p[r < Req / 4].mean() - p[r > Req + 8].mean())
+    b.close()
+    A = np.vstack([inv, np.ones(len(inv))]).T
+    (slope, icpt), *_ = np.linalg.lstsq(A, np.array(dps), rcond=None)
+    pred = A @ [slope, icpt]
+    r2 = 1 - ((np.array(dps) - pred) ** 2).sum() / ((np.array(dps) - np.mean(dps)) ** 2).sum()
+    assert slope > 0 and r2 > 0.999 and abs(icpt) < 0.05 * slope / 8, (slope, icpt, r2)
