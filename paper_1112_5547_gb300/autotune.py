@@ -120,6 +120,9 @@ def cache_key(lattice: "lbm_sc.Lattice") -> str:
     prec = {v: k for k, v in lbm_sc.PRECISIONS.items()}[lattice.params.precision]
     kind = "D2Q9" if lattice.lattice == lbm_sc.LBM_D2Q9 else "D3Q19"
     key = "%s/%s/%s" % (kind, prec, "x".join(str(s) for s in reversed(lattice.shape)))
+    # the collision changes the best shape: separate entries for Guo forcing and the FE model
+    if lattice.params.model == lbm_sc.LBM_MODEL_FE:
+        return key + "/fe"
     return key + "/guo" if lattice.params.forcing == lbm_sc.LBM_FORCING_GUO else key
 
 

@@ -367,3 +367,18 @@ def test_missing_libraries_fail_loudly(tmp_path):
                 mod.load(str(tmp_path / name))
         finally:
             mod._lib = saved
+
+
+def test_tuning_cache_keys_separate_the_collisions(lib):
+    """The autotuner's cache keeps the SC shift, Guo and FE entries of one size apart
+    (a shape tuned for one collision must not overwrite another's)."""
+    from paper_1112_5547_gb300 import autotune
+
+    class Fake:
+        def __init__(self, **kw):
+            self.params = lib.make_params(lib.LBM_D3Q19, (64, 64, 64), 1.0, 1.0, 2.0, "f32", **kw)
+            self.lattice = lib.LBM_D3Q19
+            self.shape = (64, 64, 64)
+    keys = {autotune.cache_key(Fake()), autotune.cache_key(Fake(forcing="guo")),
+            autotune.cache_key(Fake(model=lib.LBM_MODEL_FE, kappa=0.05, gamma=1.0))}
+    assert keys == {"D3Q19/f32/64x64x64", "D3Q19/f32/64x64x64/guo", "D3Q19/f32/64x64x64/fe"}
