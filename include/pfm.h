@@ -20,6 +20,8 @@
  * advanced by Crank-Nicolson; the velocity likewise, with -div(u u) + mu grad phi / rho
  * explicit (projected onto divergence-free fields) and nu lap u implicit.  The
  * first step takes the previous explicit term equal to the current one.
+ * Optional Kolmogorov forcing of Eq. kolmo (Sec. 4.2): A sin(2 pi y / ny) along x
+ * added to the explicit momentum right-hand side (per unit mass; divergence-free).
  * Spectral derivatives: i k for first derivatives (the Nyquist wavenumber of
  * an even axis zeroed), -|k|^2 for the Laplacian; products in physical space,
  * no dealiasing.  Transforms: cuFFT (real-to-complex and back, batched); the
@@ -54,6 +56,7 @@ typedef struct {
     double tau;          /* LBM relaxation time the PFM is matched to (> 1/2)        */
     double g;            /* SC coupling g (g_tau = tau g / (tau - 1/2))              */
     double dt;           /* time step (> 0)                                          */
+    double body_A;       /* Kolmogorov forcing amplitude A (finite); 0 = none        */
 } pfm_params;
 
 typedef struct pfm_handle pfm_handle;

@@ -12,7 +12,9 @@ viscosity-matched incompressible binary fluid on a periodic box (Sec. 3):
   mu     = the same with g in place of g_tau                        (Eq. eq45.2)
   M = rho (tau - 1/2), nu = cs2 (tau - 1/2), g_tau = tau g / (tau - 1/2).
 The paper writes the momentum equation per unit mass; its capillary term is
-read here as mu grad phi / rho (rho uniform).
+read here as mu grad phi / rho (rho uniform).  Optional Kolmogorov forcing of
+Eq. kolmo (Sec. 4.2): F_x / rho = A sin(2 pi y / L_y) added to the explicit
+momentum right-hand side (it is divergence-free, the projection keeps it).
 
 Time stepping (Sec. 3.1, Eqs. eq10-eq13), pseudo-spectral: with
 beta = g_tau cs2 / 2, D = M beta and xi^2 = cs2 / 2 the Cahn-Hilliard equation
@@ -46,8 +48,9 @@ class OraclePFM:
     """Phase-field model of Sec. 3 on a periodic box of ``shape`` (numpy order),
     uniform density rho, LBM relaxation time tau and SC coupling g, time step dt."""
 
-    def __init__(self, shape, rho: float, tau: float, g: float, dt: float = 1.0):
+    def __init__(self, shape, rho: float, tau: float, g: float, dt: float = 1.0, body_A: float = 0.0):
         self.shape = tuple(int(s) for s in shape)
+        self.body_A = float(body_A)
         self.D = len(self.shape)
         self.rho, self.tau, self.g, self.dt = float(rho), float(tau), float(g), float(dt)
         self.M = self.rho * (self.tau - 0.5)
@@ -103,9 +106,13 @@ class OraclePFM:
         mu = 0.5 * CS2 * np.log((rho + phi) / (rho - phi)) - 0.5 * self.g * CS2 * phi - 0.25 * self.g * CS2 * CS2 * lap
         N = []
         for a in range(self.D):
-            # -d_b (u_a u_b) + mu d_a phi / rho
+            # -d_b (u_a u_b) + mu d_a phi / rho (+ the Kolmogorov force along x)
             div = sum(1j * self._kx(b) * np.fft.fftn(u[a] * u[b]) for b in range(self.D))
             N.append(-div + np.fft.fftn(mu * grad[a]) / rho)
+        if self.body_A != 0.0:
+            ny = self.shape[-2]
+            y = np.arange(ny).reshape([ny if ax == self.D - 2 else 1 for ax in range(self.D)])
+            N[0] = N[0] + np.fft.fftn(np.broadcast_to(self.body_A * np.sin(2 * np.pi * y / ny), self.shape))
         # projection onto divergence-free fields: N - k (k.N) / k^2 (first-derivative k);
         # the mean (k = 0) of the right-hand side is dropped: no net force on a periodic box
         kd2 = np.where(self.kd2 == 0, 1.0, self.kd2)

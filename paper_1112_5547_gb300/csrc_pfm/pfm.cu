@@ -72,6 +72,7 @@ template <class T> __device__ __forceinline__ Wave<T> wave_of(const Geometry& g,
 
 struct Coeffs {
     double rho, g, g_tau, Dc, xi2, nu, dt, inv_n;
+    double body_half_n;  // A N / 2: the Fourier coefficient (times -+i) of A sin(2 pi y/ny) at ky = +-1
 };
 
 template <class C, class T> __device__ __forceinline__ C cmul_i(C a, T k) {  // (i k) a
@@ -182,6 +183,12 @@ __global__ void pfm_update_kernel(Geometry g, Coeffs c, int first, const typenam
             nx_[a] = re;
             ny_[a] = im;
         }
+        // Kolmogorov forcing A sin(2 pi y/ny) e_x: -i A N/2 at ky = +1, +i A N/2 at ky = -1 (kx = kz = 0)
+        if (c.body_half_n != 0.0 && g.ny > 2) {
+            const int ix = (int)(i % g.nxh), iy = (int)((i / g.nxh) % g.ny), iz = (int)(i / ((long long)g.nxh * g.ny));
+            if (ix == 0 && iz == 0 && iy == 1) ny_[0] -= (T)c.body_half_n;
+            if (ix == 0 && iz == 0 && iy == g.ny - 1) ny_[0] += (T)c.body_half_n;
+        }
         const T kd2 = w.kd[0] * w.kd[0] + w.kd[1] * w.kd[1] + w.kd[2] * w.kd[2];
         T kre = 0, kim = 0;
         for (int a = 0; a < D; ++a) {
@@ -216,6 +223,7 @@ bool valid(const pfm_params* p) {
     if (p->dim == 3 && p->nz < 2) return false;
     if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return false;
     if (!(p->rho > 0) || !(p->tau > 0.5) || !(p->dt > 0) || !(p->g - p->g == 0.0)) return false;
+    if (!(p->body_A - p->body_A == 0.0)) return false;
     return true;
 }
 
@@ -286,6 +294,7 @@ Coeffs coeffs(const pfm_params* p, const Geometry& g) {
     c.nu = kCs2 * (p->tau - 0.5);
     c.dt = p->dt;
     c.inv_n = 1.0 / (double)g.nreal;
+    c.body_half_n = p->body_A * (double)g.nreal / 2.0;
     return c;
 }
 

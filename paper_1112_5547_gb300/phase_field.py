@@ -26,7 +26,8 @@ EXPORTS = ("pfm_workspace_bytes", "pfm_create", "pfm_init", "pfm_step", "pfm_fie
 class pfm_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("precision", ctypes.c_int32), ("nx", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("rho", ctypes.c_double), ("tau", ctypes.c_double), ("g", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("rho", ctypes.c_double), ("tau", ctypes.c_double), ("g", ctypes.c_double), ("dt", ctypes.c_double),
+                ("body_A", ctypes.c_double)]
 
 
 _lib = None
@@ -57,14 +58,15 @@ def load(path: str = PFM_LIB):
     return lib
 
 
-def make_params(shape, rho: float, tau: float, g: float, dt: float, precision="f64") -> pfm_params:
+def make_params(shape, rho: float, tau: float, g: float, dt: float, precision="f64",
+                body_A: float = 0.0) -> pfm_params:
     shape = tuple(int(s) for s in shape)
     if len(shape) == 2:
         dim, nz, (ny, nx) = 2, 1, shape
     else:
         dim, (nz, ny, nx) = 3, shape
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return pfm_params(dim, prec, nx, ny, nz, 0, float(rho), float(tau), float(g), float(dt))
+    return pfm_params(dim, prec, nx, ny, nz, 0, float(rho), float(tau), float(g), float(dt), float(body_A))
 
 
 def workspace_bytes(params: pfm_params) -> int:
@@ -81,12 +83,12 @@ class PFM:
     spectral state in a torch-owned workspace (see include/pfm.h)."""
 
     def __init__(self, shape, rho: float, tau: float, g: float, dt: float = 1.0, precision="f64", device="cuda",
-                 stream=None):
+                 stream=None, body_A: float = 0.0):
         import torch
         self.torch = torch
         self.shape = tuple(int(s) for s in shape)
         self.D = len(self.shape)
-        self.params = make_params(shape, rho, tau, g, dt, precision)
+        self.params = make_params(shape, rho, tau, g, dt, precision, body_A)
         self.dtype = torch.float64 if self.params.precision == PFM_F64 else torch.float32
         nbytes = workspace_bytes(self.params)
         if nbytes == 0:

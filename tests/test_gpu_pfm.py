@@ -128,3 +128,22 @@ def test_pfm_128_whole_field_and_256_invariants(pf, oracle_mod):
     assert float(div.abs().max()) < 2e-4 * float(u.abs().max())
     del s, u, uh, div
     torch.cuda.empty_cache()
+
+
+def test_pfm_kolmogorov_forcing_on_gpu(pf, oracle_mod):
+    """The forcing of Eq. kolmo in the PFM (FP64): a forced drop matches the oracle
+    (1e-10), and a forced uniform fluid reaches the exact steady profile
+    u_x = A sin(k y) / (nu k^2)."""
+    shape = (24, 32)
+    phi0 = _phi(shape, 7)
+    s = pf.PFM(shape, RHO, TAU, G, DT, "f64", body_A=1e-4).init(phi0).step(50)
+    o = oracle_mod.OraclePFM(shape, RHO, TAU, G, DT, body_A=1e-4).init(phi0).step(50)
+    gp, gu = _gpu(s)
+    op, ou = o.fields()
+    assert _rel(gp, op) < 1e-10 and _rel(gu, ou) < 1e-9
+    A, tau, ny = 1e-6, 0.8, 32
+    k, nu = 2 * np.pi / ny, (tau - 0.5) / 3
+    s = pf.PFM((ny, 8), 1.4, tau, 0.3, 1.0, "f64", body_A=A).init(np.zeros((ny, 8))).step(int(30 / (nu * k * k)))
+    u = _gpu(s)[1]
+    expect = A * np.sin(k * np.arange(ny)) / (nu * k * k)
+    np.testing.assert_allclose(u[..., 0], np.broadcast_to(expect[:, None], (ny, 8)), rtol=0, atol=1e-9 * expect.max())

@@ -798,3 +798,20 @@ def test_fe_laplace_law(oracle_mod):
     pred = A @ [slope, icpt]
     r2 = 1 - ((np.array(dps) - pred) ** 2).sum() / ((np.array(dps) - np.mean(dps)) ** 2).sum()
     assert slope > 0 and r2 > 0.999 and abs(icpt) < 0.05 * slope / 8, (slope, icpt, r2)
+
+
+@pytest.mark.parametrize("shape", [(32, 8), (4, 24, 6)])
+def test_pfm_steady_kolmogorov_flow_is_exact(oracle_mod, shape):
+    """The PFM with the forcing of Eq. kolmo on a uniform phi: spectral derivatives
+    and the CN steady state make u_x = A sin(k y) / (nu k^2) exact (no lattice
+    correction, unlike the LBM), u_y = u_z = 0."""
+    A, tau = 1e-6, 0.8
+    ny = shape[-2]
+    k, nu = 2 * np.pi / ny, CS2 * (tau - 0.5)
+    o = oracle_mod.OraclePFM(shape, 1.4, tau, 0.3, 1.0, body_A=A).init(np.zeros(shape))
+    o.step(int(30 / (nu * k * k)))
+    _, u = o.fields()
+    y = np.arange(ny).reshape([ny if ax == len(shape) - 2 else 1 for ax in range(len(shape))])
+    np.testing.assert_allclose(u[..., 0], np.broadcast_to(A * np.sin(k * y) / (nu * k * k), shape), rtol=0,
+                               atol=1e-10 * A / (nu * k * k))
+    assert np.abs(u[..., 1:]).max() < 1e-18
