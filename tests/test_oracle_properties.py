@@ -1,0 +1,56 @@
+"""Randomised checks of the FP64 oracle (hypothesis): over random small lattices,
+relaxation times, couplings, forcing schemes and densities, one oracle step
+equals the independent exact rational trace (tests/exact_sc.py), and several
+steps conserve each species' mass and the total momentum.  They widen the
+fixed-parameter pins of test_oracle_pins.py to the whole parameter range."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings  # noqa: E402
+from hypothesis import strategies as st  # noqa: E402
+
+from tests import exact_sc  # noqa: E402
+
+taus = st.sampled_from([Fraction(11, 20), Fraction(3, 5), Fraction(4, 5), Fraction(1), Fraction(3, 2), Fraction(2)])
+couplings = st.sampled_from([Fraction(0), Fraction(1, 2), Fraction(3, 2), Fraction(5, 2), Fraction(-1, 2)])
+
+
+@settings(max_examples=25, deadline=None)
+@given(nx=st.integers(1, 4), ny=st.sampled_from([1, 2, 4]), tau_A=taus, tau_B=taus, G=couplings,
+       A=st.sampled_from([Fraction(0), Fraction(1, 40), Fraction(-1, 25)]), guo=st.booleans(),
+       seed=st.integers(0, 10 ** 6))
+def test_one_step_equals_the_exact_trace(oracle_mod, nx, ny, tau_A, tau_B, G, A, guo, seed):
+    rng = np.random.default_rng(seed)
+    nums = rng.integers(2, 40, size=(2, ny, nx))
+    rA = [[Fraction(int(nums[0, y, x]), 20) for x in range(nx)] for y in range(ny)]
+    rB = [[Fraction(int(nums[1, y, x]), 25) for x in range(nx)] for y in range(ny)]
+    ex = exact_sc.ExactSC(nx, ny, tau_A, tau_B, G, body_A=A, guo=guo).init(rA, rB).step()
+    o = oracle_mod.OracleSC(0, (ny, nx), float(tau_A), float(tau_B), float(G), body_A=float(A),
+                            forcing="guo" if guo else "shift")
+    o.init(np.array(rA, dtype=float), np.array(rB, dtype=float)).step(1)
+    a, b, u, p = o.moments()
+    eA, eB, eux, euy, ep = (np.array([float(v) for v in arr]).reshape(ny, nx) for arr in ex.fields())
+    np.testing.assert_allclose(a, eA, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(b, eB, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(u[..., 0], eux, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(u[..., 1], euy, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(p, ep, rtol=1e-14, atol=0)
+
+
+@settings(max_examples=20, deadline=None)
+@given(lat=st.sampled_from([0, 1]), n=st.integers(3, 7), tau_A=st.floats(0.55, 2.0), tau_B=st.floats(0.55, 2.0),
+       G=st.floats(-0.5, 2.5), guo=st.booleans(), seed=st.integers(0, 10 ** 6))
+def test_mass_and_momentum_conservation(oracle_mod, lat, n, tau_A, tau_B, G, guo, seed):
+    rng = np.random.default_rng(seed)
+    shape = (n, n + 1) if lat == 0 else (n, n + 1, n + 2)
+    rA = 0.3 + rng.random(shape)
+    rB = 0.3 + rng.random(shape)
+    o = oracle_mod.OracleSC(lat, shape, tau_A, tau_B, G, forcing="guo" if guo else "shift").init(rA, rB)
+    m0 = o.total_momentum()
+    o.step(5)
+    a, b, _, _ = o.moments()
+    assert abs(a.sum() / rA.sum() - 1) < 1e-13 and abs(b.sum() / rB.sum() - 1) < 1e-13
+    assert np.abs(o.total_momentum() - m0).max() < 1e-12 * (rA.sum() + rB.sum())
