@@ -54,7 +54,7 @@ typedef struct {
     int32_t reserved;    /* set to 0                                                 */
     double rho;          /* uniform density (> 0)                                    */
     double tau;          /* LBM relaxation time the PFM is matched to (> 1/2)        */
-    double g;            /* SC coupling g (g_tau = tau g / (tau - 1/2))              */
+    double g;            /* SC coupling g > 0 (g_tau = tau g / (tau - 1/2))          */
     double dt;           /* time step (> 0)                                          */
     double body_A;       /* Kolmogorov forcing amplitude A (finite); 0 = none        */
 } pfm_params;

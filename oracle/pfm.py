@@ -49,6 +49,8 @@ class OraclePFM:
     uniform density rho, LBM relaxation time tau and SC coupling g, time step dt."""
 
     def __init__(self, shape, rho: float, tau: float, g: float, dt: float = 1.0, body_A: float = 0.0):
+        if not g > 0:
+            raise ValueError("the PFM needs g > 0 (its explicit bracket carries 1/g_tau)")
         self.shape = tuple(int(s) for s in shape)
         self.body_A = float(body_A)
         self.D = len(self.shape)

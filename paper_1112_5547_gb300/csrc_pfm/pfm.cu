@@ -222,7 +222,8 @@ bool valid(const pfm_params* p) {
     if (p->dim == 2 && p->nz != 1) return false;
     if (p->dim == 3 && p->nz < 2) return false;
     if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return false;
-    if (!(p->rho > 0) || !(p->tau > 0.5) || !(p->dt > 0) || !(p->g - p->g == 0.0)) return false;
+    // g > 0: the explicit bracket carries 1/g_tau and the mobility D = M g_tau cs2/2
+    if (!(p->rho > 0) || !(p->tau > 0.5) || !(p->dt > 0) || !(p->g > 0) || !(p->g - p->g == 0.0)) return false;
     if (!(p->body_A - p->body_A == 0.0)) return false;
     return true;
 }

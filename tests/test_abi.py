@@ -351,7 +351,8 @@ def test_pfm_library_exports_and_layout(lib, tmp_path):
     R, C = 16 * 20 * 24, 16 * 20 * 13
     assert n >= (8 * C * 2 + 8 * C * 2 + 8 * R + 11 * R + 11 * C * 2) * 4  # state, transform batches
     for bad in (pf.make_params((16, 20, 24), 1.4, 0.5, 0.3, 0.1), pf.make_params((16, 20, 24), 1.4, 0.6, 0.3, 0.0),
-                pf.make_params((16, 20, 24), -1.0, 0.6, 0.3, 0.1), pf.make_params((1, 20), 1.4, 0.6, 0.3, 0.1)):
+                pf.make_params((16, 20, 24), -1.0, 0.6, 0.3, 0.1), pf.make_params((1, 20), 1.4, 0.6, 0.3, 0.1),
+                pf.make_params((16, 20, 24), 1.4, 0.6, 0.0, 0.1)):
         assert pf.workspace_bytes(bad) == 0
 
 

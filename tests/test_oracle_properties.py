@@ -54,3 +54,27 @@ def test_mass_and_momentum_conservation(oracle_mod, lat, n, tau_A, tau_B, G, guo
     a, b, _, _ = o.moments()
     assert abs(a.sum() / rA.sum() - 1) < 1e-13 and abs(b.sum() / rB.sum() - 1) < 1e-13
     assert np.abs(o.total_momentum() - m0).max() < 1e-12 * (rA.sum() + rB.sum())
+
+
+@settings(max_examples=15, deadline=None)
+@given(L=st.sampled_from([8, 12, 16, 24, 32]), mode=st.integers(1, 3), tau=st.floats(0.55, 1.5),
+       g=st.floats(0.05, 1.5), dt=st.sampled_from([0.05, 0.2, 0.5, 1.0]))
+def test_pfm_linear_modes_follow_the_scheme_recurrence(L, mode, tau, g, dt):
+    """Any small phi mode of the PFM at rest follows the two-level recurrence of
+    Eqs. eq11-eq13 (see test_pfm_linear_mode_follows_the_ab2_cn_recurrence_and_the_sc_rate)."""
+    import oracle
+    rho, eps, cs2 = 1.0, 1e-7, 1.0 / 3.0
+    x = np.arange(L)
+    s = np.sin(2 * np.pi * mode * x / L)
+    o = oracle.OraclePFM((2, L), rho, tau, g, dt).init(eps * np.broadcast_to(s, (2, L)))
+    k2 = (2 * np.pi * mode / L) ** 2
+    g_tau = tau * g / (tau - 0.5)
+    D, xi2 = rho * (tau - 0.5) * g_tau * cs2 / 2, cs2 / 2
+    lam = D * (2 * k2 + dt * D / 2 * k2 * k2)
+    sig = -D * k2 * (2 / (g_tau * rho) - 3) - D * (xi2 - dt * D / 2) * k2 * k2
+    a_prev = a = eps
+    for _ in range(12):
+        a_prev, a = a, (a * (1 - dt * lam / 2) + dt * (3 * sig * a - sig * a_prev) / 2) / (1 + dt * lam / 2)
+        p, _ = o.step(1).fields()
+        amp = 2 * (p * s).mean()
+        assert abs(amp - a) <= 1e-9 * max(abs(a), eps) + 1e-20, (amp, a)
