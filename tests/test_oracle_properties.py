@@ -78,3 +78,27 @@ def test_pfm_linear_modes_follow_the_scheme_recurrence(L, mode, tau, g, dt):
         p, _ = o.step(1).fields()
         amp = 2 * (p * s).mean()
         assert abs(amp - a) <= 1e-9 * max(abs(a), eps) + 1e-20, (amp, a)
+
+
+@settings(max_examples=30, deadline=None)
+@given(lat=st.sampled_from([0, 1]), rho=st.floats(0.5, 2.0), frac=st.floats(-0.9, 0.9),
+       g=st.floats(-1.0, 4.0), kappa=st.floats(0.0, 0.2), gamma=st.floats(0.1, 2.0),
+       u=st.lists(st.floats(-0.1, 0.1), min_size=3, max_size=3),
+       gp=st.lists(st.floats(-0.3, 0.3), min_size=3, max_size=3), lp=st.floats(-0.3, 0.3))
+def test_fe_equilibria_meet_the_moment_conditions_everywhere(oracle_mod, lat, rho, frac, g, kappa, gamma, u, gp, lp):
+    """Eqs. EQFE1 / EQFE2 over random states (the fixed-state pin, widened)."""
+    D = 2 if lat == 0 else 3
+    phi = frac * rho
+    u, gp = np.array(u[:D]), np.array(gp[:D])
+    c, _ = oracle_mod.lattice(lat)
+    cc = c[:, :D].astype(float)
+    fe, ge = oracle_mod.fe_equilibria(lat, g, kappa, gamma, rho, phi, u, gp, lp)
+    cs2 = 1.0 / 3.0
+    mu = 0.5 * cs2 * np.log((rho + phi) / (rho - phi)) - 0.5 * g * cs2 * phi - kappa * lp
+    pb = cs2 * rho + 0.25 * g * cs2 * (rho * rho - phi * phi)
+    P = (pb - kappa * phi * lp - 0.5 * kappa * (gp @ gp)) * np.eye(D) + kappa * np.outer(gp, gp)
+    tol = 1e-14 * max(1.0, abs(mu), abs(pb))
+    assert abs(fe.sum() - rho) < tol and abs(ge.sum() - phi) < tol
+    assert np.abs(fe @ cc - rho * u).max() < tol and np.abs(ge @ cc - phi * u).max() < tol
+    assert np.abs(np.einsum("i,ia,ib->ab", fe, cc, cc) - P - rho * np.outer(u, u)).max() < tol
+    assert np.abs(np.einsum("i,ia,ib->ab", ge, cc, cc) - gamma * mu * np.eye(D) - phi * np.outer(u, u)).max() < tol
