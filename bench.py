@@ -407,7 +407,8 @@ def kolmogorov_compare(L: int, steps: int, warmup: int, peak: float, A: float = 
 
 def serve_compare(n: int, rate: float, seed: int = 4):
     """Continuous batching against serial solves on a seeded Poisson stream of
-    n drop-relaxation requests (mean rate per second): D2Q9 lattices 64^2 ..
+    n drop- and interface-relaxation requests (a quarter are flat interfaces;
+    mean rate per second): D2Q9 lattices 64^2 ..
     1024^2 and D3Q19 32^3 .. 192^3 (sizes 32, 48, 64, 96, 128, 160, 192), per-request G, tau, R as in the ragged
     batch; each runs until max|u_phys| changes by < 1% over 500 steps or 10000
     steps; 80 GB HBM admission budget, smallest lattices admitted first while
@@ -415,17 +416,19 @@ def serve_compare(n: int, rate: float, seed: int = 4):
     result (rho_A) in host memory.  Serial: the same requests one at a time
     (plain lbm_sc_step, same convergence rule), input generation not timed."""
     from paper_1112_5547_gb300 import serving
-    reqs = serving.poisson_requests(n, rate, seed)
+    reqs = serving.poisson_requests(n, rate, seed, interface_fraction=0.25)
     # smallest lattices admitted first while the resident set holds < 48 M nodes
     # (256-request sweep: p50 45 -> 12 s at 1 % less throughput, p99 unchanged)
     res, st = serving.Server(hbm_budget=80e9, order="size", max_active_nodes=48_000_000).run(reqs)
     sres, stot, smlups = serving.serial_baseline(reqs)
-    return {"workload": "%d Poisson requests at %.0f/s (seed %d): D2Q9 64^2..1024^2, D3Q19 32^3..192^3, "
+    return {"workload": "%d Poisson requests at %.0f/s (seed %d): drops and (1 in 4) flat interfaces, "
+                        "D2Q9 64^2..1024^2, D3Q19 32^3..192^3, "
                         "until |d max|u|| < 1%% per 500 steps or 10000 steps, 80 GB budget, FP32" % (n, rate, seed),
             "served_mlups": st.mlups, "serial_mlups": smlups, "speedup": st.mlups / smlups,
             "p50_s": st.p50_s, "p99_s": st.p99_s, "mean_s": st.mean_s, "wall_s": st.wall_s, "serial_s": stot,
             "max_resident": st.max_resident, "admission": "fewest nodes first, resident nodes < 48 M",
             "converged": sum(r.converged for r in res),
+            "interfaces": sum(r.kind == "interface" for r in reqs),
             "same_steps_as_alone": all(a.steps == b.steps for a, b in zip(res, sres))}
 
 

@@ -43,25 +43,32 @@ class Request:
     seed: int
     arrival: float = 0.0  # seconds after the start of the run
     precision: str = "f32"
+    kind: str = "drop"    # "drop" (radius R) or "interface" (a slab of half-width R: two flat interfaces)
 
     @property
     def nodes(self) -> int:
         return int(np.prod(self.shape))
 
     def fields(self):
-        """Initial (rho_A, rho_B): the drop recipe of paper_1112_5547_gb300.inputs, in FP32."""
+        """Initial (rho_A, rho_B) in FP32: the drop recipe of paper_1112_5547_gb300.inputs,
+        or its slab recipe (interfaces normal to x, centred at the request's centre x)."""
+        if self.kind == "interface":
+            return inputs.slab(self.shape, self.R, centre_x=self.centre[0], seed=self.seed, dtype=np.float32)
         return inputs.drop(self.shape, self.R, centre=self.centre, seed=self.seed, dtype=np.float32)
 
 
 def poisson_requests(n: int, rate: float = 50.0, seed: int = 4, d3_fraction: float = 0.5,
                      sizes2=(64, 128, 256, 512, 1024), sizes3=(32, 48, 64, 96, 128, 160, 192),
-                     precision: str = "f32") -> List[Request]:
+                     precision: str = "f32", interface_fraction: float = 0.0) -> List[Request]:
     """n requests with exponential inter-arrival times of mean 1/rate (seeded).
 
     Each is D3Q19 with probability d3_fraction, else D2Q9; the edge L is drawn
     uniformly from sizes3 / sizes2, G rho_tot uniformly in [2.2, 2.8], tau_A,
     tau_B uniformly in [0.6, 1.5], the drop radius uniformly in [L/8, L/3] at a
     uniformly random centre (the ragged-batch recipe of inputs.ragged_drop_specs).
+    With probability interface_fraction a request relaxes a flat interface
+    instead (a slab of half-width R); with 0 the stream is the drops-only one
+    (no extra random draws).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out, t = [], 0.0
@@ -76,8 +83,9 @@ def poisson_requests(n: int, rate: float = 50.0, seed: int = 4, d3_fraction: flo
         tau_B = float(rng.uniform(0.6, 1.5))
         R = float(rng.uniform(L / 8.0, L / 3.0))
         centre = tuple(float(c) for c in rng.uniform(0.0, L, size=dim))
+        kind = "interface" if interface_fraction > 0 and rng.uniform() < interface_fraction else "drop"
         out.append(Request(k, lbm_sc.LBM_D3Q19 if d3 else lbm_sc.LBM_D2Q9, (L,) * dim, g_rho / inputs.RHO_TOT,
-                           tau_A, tau_B, R, centre, int(seed) * 1000003 + k, t, precision))
+                           tau_A, tau_B, R, centre, int(seed) * 1000003 + k, t, precision, kind))
     return out
 
 

@@ -35,6 +35,19 @@ def test_served_equals_alone(sv):
     assert st.p99_s >= st.p50_s > 0
 
 
+def test_drops_and_interfaces_served_equal_alone(sv):
+    """A stream with flat-interface relaxations among the drops: each result is
+    the same served in the mix as solved alone."""
+    reqs = sv.poisson_requests(8, rate=200.0, seed=11, sizes2=(64, 96), sizes3=(32, 40), interface_fraction=0.5)
+    assert {r.kind for r in reqs} == {"drop", "interface"}
+    srv = sv.Server(hbm_budget=80e9, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+    res, st = srv.run(reqs)
+    assert st.max_resident >= 2
+    for r in reqs:
+        alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+        assert res[r.rid].steps == alone.steps and np.array_equal(res[r.rid].rhoA, alone.rhoA), r.rid
+
+
 def test_admission_respects_budget(sv):
     """A budget that holds only two of these lattices: at most two are resident,
     the rest wait, and every request still finishes with its own result."""
