@@ -48,3 +48,24 @@ def test_ragged_batch_specs_seeded_and_in_range():
         assert L / 8 <= s["R"] <= L / 3
     rA, rB = inputs.spec_fields(a[0])
     assert rA.shape == a[0]["shape"] and abs((rA + rB).mean() - inputs.RHO_TOT) < 1e-3
+
+
+def test_interface_requests():
+    """interface_fraction mixes flat-interface relaxations into the stream (a slab
+    of half-width R across x), and 0 leaves the drops-only stream untouched."""
+    from paper_1112_5547_gb300 import serving
+    a = serving.poisson_requests(30, 50.0, 4)
+    b = serving.poisson_requests(30, 50.0, 4, interface_fraction=0.0)
+    assert [(r.shape, r.R, r.arrival, r.kind) for r in a] == [(r.shape, r.R, r.arrival, r.kind) for r in b]
+    c = serving.poisson_requests(40, 50.0, 4, interface_fraction=0.5)
+    kinds = [r.kind for r in c]
+    assert 5 < kinds.count("interface") < 35
+    r = next(q for q in c if q.kind == "interface")
+    rA, rB = r.fields()
+    assert rA.shape == r.shape
+    L = r.shape[-1]
+    x = np.arange(L)
+    d = np.abs((x - r.centre[0] + L / 2) % L - L / 2)  # periodic distance to the slab centre
+    prof = rA.reshape(-1, L).mean(0)
+    assert prof[d < r.R - 4].min() > 0.9 and prof[d > r.R + 4].max() < 0.1
+    assert serving.Server.footprint(r) > 0
