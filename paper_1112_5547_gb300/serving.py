@@ -20,6 +20,7 @@ Because a batched step is bit-identical to a solo step, a request's result
 from __future__ import annotations
 
 import concurrent.futures as cf
+import ctypes
 import time
 from collections import deque
 from dataclasses import dataclass, field
@@ -28,6 +29,14 @@ from typing import Dict, List, Optional
 import numpy as np
 
 from . import inputs, lbm_sc
+
+# Doubles in one lbm_sc_diag record (the rows of the device diagnostics array).
+DIAG_DOUBLES = ctypes.sizeof(lbm_sc.lbm_sc_diag) // 8
+
+
+def max_speed_of(row) -> float:
+    """max|u_phys| of one lbm_sc_diag record held as DIAG_DOUBLES doubles."""
+    return float(lbm_sc.lbm_sc_diag.from_buffer_copy(np.ascontiguousarray(row, dtype=np.float64).tobytes()).max_speed)
 
 
 @dataclass
@@ -191,14 +200,16 @@ class Server:
         """max|u_phys| of each slot's current state, one synchronisation for all."""
         torch = self.torch
         n = len(slots)
+        width = DIAG_DOUBLES
         if self._diag is None or self._diag.shape[0] < n:
-            self._diag = torch.empty((max(n, 64), 16), dtype=torch.float64, device=self.device)
+            self._diag = torch.empty((max(n, 64), width), dtype=torch.float64, device=self.device)
+        assert self._diag.shape[1] * 8 == ctypes.sizeof(lbm_sc.lbm_sc_diag)
         for k, s in enumerate(slots):
             eb, q, px, py, gx, gy, ptr = lbm_sc.lbm_sc_layout(s.lat.handle)
             lbm_sc.lbm_sc_diagnostics_noalloc(s.lat.params, ptr, None, self._diag[k].data_ptr(),
                                               self.stream.cuda_stream)
-        host = self._diag[:n].cpu()  # on the current stream, which is self.stream
-        return [float(host[k, 6]) for k in range(n)]  # slot 6: max_speed
+        host = self._diag[:n].cpu().numpy()  # on the current stream, which is self.stream
+        return [max_speed_of(host[k]) for k in range(n)]
 
     def _admit(self, req: Request, f, now: float) -> _Slot:
         with self.torch.cuda.stream(self.stream):
@@ -310,14 +321,14 @@ def solve_alone(req: Request, chunk: int = 100, check_every: int = 500, tol: flo
         lat = lbm_sc.Lattice(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision, stream=stream)
         lat.init(f[0], f[1])
         steps, last, conv, u = 0, None, False, float("nan")
-        diag = torch.empty(16, dtype=torch.float64, device="cuda")
+        diag = torch.empty(DIAG_DOUBLES, dtype=torch.float64, device="cuda")
         while True:
             lat.step(chunk)
             steps += chunk
             if steps % check_every == 0:
                 eb, q, px, py, gx, gy, ptr = lbm_sc.lbm_sc_layout(lat.handle)
                 lbm_sc.lbm_sc_diagnostics_noalloc(lat.params, ptr, None, diag.data_ptr(), stream.cuda_stream)
-                u = float(diag[6].cpu())
+                u = max_speed_of(diag.cpu().numpy())
                 conv = last is not None and abs(u - last) < tol * max(last, 1e-300)
                 if conv or steps >= max_steps:
                     break

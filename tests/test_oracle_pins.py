@@ -170,6 +170,51 @@ def test_exact_rational_steps_4x4(oracle_mod, tau_A, tau_B, G):
         assert np.abs(eux).max() > 1e-3  # the trace really exercises the force
 
 
+# --- exact rational brute force on small D3Q19 boxes -------------------------
+def _rational_fields_3d(shape, seed):
+    nz, ny, nx = shape
+    nums = np.random.default_rng(seed).integers(1, 40, size=(2, nz, ny, nx))
+    rA = [[[Fraction(int(nums[0, z, y, x]), 20) for x in range(nx)] for y in range(ny)] for z in range(nz)]
+    rB = [[[Fraction(int(nums[1, z, y, x]), 25) for x in range(nx)] for y in range(ny)] for z in range(nz)]
+    return rA, rB
+
+
+@pytest.mark.parametrize("shape,tau_A,tau_B,G,A,guo", [
+    ((3, 4, 3), 1, 1, Fraction(3, 2), 0, False),
+    ((3, 3, 4), Fraction(3, 2), Fraction(4, 5), Fraction(2, 1), 0, False),
+    ((4, 2, 3), Fraction(3, 5), Fraction(6, 5), Fraction(-1, 2), 0, False),
+    ((3, 4, 3), Fraction(3, 2), Fraction(4, 5), Fraction(2, 1), Fraction(1, 40), False),
+    ((3, 4, 3), Fraction(3, 2), Fraction(4, 5), Fraction(2, 1), Fraction(1, 40), True),
+])
+def test_exact_rational_steps_d3q19(oracle_mod, shape, tau_A, tau_B, G, A, guo):
+    """Eq. FORCE on D3Q19 with G != 0: two oracle steps equal an exact rational
+    trace (tests/exact_sc.py ExactSC3: textbook D3Q19 order, pull streaming,
+    Hermite equilibrium) on boxes at least three nodes deep in every direction
+    the force has to resolve, with random rational densities, so every one of
+    the 18 neighbour terms (the twelve off-plane diagonals included) enters with
+    its own weight and sign; a mis-signed or mis-weighted term moves u and rho
+    by ~1e-2 (checked by planting one in the trace)."""
+    nz, ny, nx = shape
+    rA, rB = _rational_fields_3d(shape, 7)
+    ex = exact_sc.ExactSC3(nx, ny, nz, tau_A, tau_B, G, body_A=A, guo=guo).init(rA, rB)
+    o = oracle_mod.OracleSC(1, shape, float(tau_A), float(tau_B), float(G), body_A=float(A),
+                            forcing="guo" if guo else "shift")
+    o.init(np.array(rA, dtype=float), np.array(rB, dtype=float))
+    for _ in range(2):
+        ex.step()
+        o.step(1)
+        a, b, u, p = o.moments()
+        eA, eB, eux, euy, euz, ep = (np.array([float(v) for v in arr]).reshape(shape) for arr in ex.fields())
+        np.testing.assert_allclose(a, eA, rtol=4e-15, atol=0)
+        np.testing.assert_allclose(b, eB, rtol=4e-15, atol=0)
+        for k, e in enumerate((eux, euy, euz)):
+            np.testing.assert_allclose(u[..., k], e, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(p, ep, rtol=4e-15, atol=0)
+        if nz >= 3 and G != 0:
+            assert np.abs(euz).max() > 1e-3  # the z (off-plane) force terms are exercised
+        assert np.abs(eux).max() > 1e-3
+
+
 # --- closed-form decay rates -------------------------------------------------
 def _mode_amp(field, axis):
     n = field.shape[axis]
