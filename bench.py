@@ -81,7 +81,74 @@ def parse():
     ap.add_argument("--no-guo", action="store_true", help="skip the Guo-forcing line")
     ap.add_argument("--no-fe", action="store_true", help="skip the free-energy model line")
     ap.add_argument("--no-pfm", action="store_true", help="skip the phase-field model line")
+    ap.add_argument("--profile", default=None, choices=list(PROFILE_CASES),
+                    help="run one small fixed workload for ncu and exit (no JSON line)")
+    ap.add_argument("--batch-tile", type=int, default=5, help="batch tile of the --profile batch cases")
     return ap.parse_args()
+
+
+PROFILE_CASES = ("step", "step2d", "solo_vs_batch", "ragged", "pfm")
+
+
+def profile_case(a):
+    """Small fixed workloads for profiling the kernels under ncu; each builds its
+    lattices, runs ``--steps`` steps with a fixed launch shape and exits.
+
+      step           one D3Q19 drop lattice (R = L/4, G rho_tot = 2.4, tau = 1)
+                     in --precision, --tile / --zchunk, solo steps
+      step2d         the same on an L^2 D2Q9 lattice
+      solo_vs_batch  the D3Q19 drop stepped twice alone, then twice as a batch of one
+      ragged         the 64-lattice ragged batch (inputs.ragged_drop_specs), --batch-tile
+      pfm            the phase-field solver (FP32) on an L^3 drop (rho_A 1.2 / rho_B 0.2,
+                     tau 0.6, g 0.3, dt 0.1)
+
+    e.g. python bench.py --profile step --L 192 --precision bf16_rest --tile 35 --zchunk 48 --steps 3
+    """
+    import torch
+    from paper_1112_5547_gb300 import inputs, lbm_sc
+    G = G_RHO / (RHO_HI + RHO_LO)
+
+    def drop_lattice(L, precision, stream):
+        rA, rB = inputs.drop((L, L, L), L / 4, seed=2, dtype=np.float32)
+        ref = (0.52, 0.52) if precision in ("bf16", "f16") else (0.0, 0.0)
+        return lbm_sc.Lattice(lbm_sc.LBM_D3Q19, (L, L, L), 1.0, 1.0, G, precision, ref[0], ref[1],
+                              stream=stream).init(rA, rB)
+
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        if a.profile == "pfm":
+            from paper_1112_5547_gb300 import phase_field
+            rA, rB = inputs.drop((a.L,) * 3, a.L / 4, rho_hi=1.2, rho_lo=0.2, seed=2, dtype=np.float32)
+            phase_field.PFM((a.L,) * 3, 1.4, 0.6, 0.3, 0.1, "f32", stream=st).init(rA - rB).step(a.steps)
+        elif a.profile == "step2d":
+            rA, rB = inputs.drop((a.L, a.L), a.L / 4, seed=0, dtype=np.float32)
+            lat = lbm_sc.Lattice(lbm_sc.LBM_D2Q9, (a.L, a.L), 1.0, 1.0, G, a.precision, stream=st).init(rA, rB)
+            lat.set_tuning(max(a.tile, 0), 0)
+            lat.step(a.steps)
+        elif a.profile == "step":
+            lat = drop_lattice(a.L, a.precision, st)
+            lat.set_tuning(max(a.tile, 0), a.zchunk)
+            lat.step(a.steps)
+        elif a.profile == "solo_vs_batch":
+            lat = drop_lattice(a.L, a.precision, st)
+            lat.set_tuning(max(a.tile, 0), a.zchunk)
+            lat.step(2)
+            b = lbm_sc.Batch([lat], tile=a.batch_tile, zchunk=a.zchunk, stream=st)
+            b.step(2)
+            st.synchronize()
+            b.close()
+        else:
+            lats = []
+            for sp in inputs.ragged_drop_specs():
+                rA, rB = inputs.spec_fields(sp, dtype=np.float32)
+                lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32",
+                                           stream=st).init(rA, rB))
+            b = lbm_sc.Batch(lats, tile=a.batch_tile, zchunk=a.zchunk, stream=st)
+            b.step(a.steps)
+            st.synchronize()
+            b.close()
+        st.synchronize()
+    print("profile case %s ok" % a.profile)
 
 
 def dist_env():
@@ -458,17 +525,39 @@ def workload_config(L: int, prec: str, world: int) -> dict:
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
+REFERENCE_SAMPLE_L = 128
+
+
 def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle (the paper has no code to install) on
+    the host cores, W untimed and exactly K timed steps of a 128^3 sample of the
+    headline drop workload (same recipe); the line states that sample as its
+    config, its own step count and its own time per step."""
     if rank != 0:
         return
-    cb = cpu_baseline(max(5.0, args.cpu_seconds))
-    line = {"impl": "reference", "metric": "2-comp SC D3Q19 MLUPS & HBM roofline %", "value": cb["value"],
-            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": args.L ** 3 / (cb["value"] * 1e6) * 1e3,  # at the oracle's sampled rate
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.L, args.precision, world),
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    import oracle
+    oracle.build()
+    L = REFERENCE_SAMPLE_L
+    G = G_RHO / (RHO_HI + RHO_LO)
+    rA, rB = drop_fields(L, np.float64)
+    o = oracle.OracleSC(1, (L, L, L), 1.0, 1.0, G).init(rA, rB)
+    o.step(max(args.warmup, 1))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    mlups = L ** 3 * args.steps / el / 1e6
+    cores = oracle.num_threads()
+    cfg = workload_config(L, "f64", 1)
+    cfg["parallelism"] = "%d host threads" % cores
+    cfg["sample_of"] = "the %d^3 headline workload (oracle FP64 on host cores; a bounded sample)" % args.L
+    cb = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+          "sample": "D3Q19 %d^3 drop (same recipe), FP64 oracle, %d timed steps after %d warm-up in %.1f s"
+                    % (L, args.steps, max(args.warmup, 1), el)}
+    line = {"impl": "reference", "metric": "2-comp SC D3Q19 MLUPS & HBM roofline %", "value": mlups,
+            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -477,6 +566,11 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.profile is not None:
+        from paper_1112_5547_gb300 import build as gb
+        gb.build()
+        profile_case(args)
         return
 
     import torch

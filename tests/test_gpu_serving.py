@@ -72,3 +72,37 @@ def test_active_node_cap(sv):
     for r in reqs[:2]:
         alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
         assert np.array_equal(res[r.rid].rhoA, alone.rhoA)
+
+
+def test_diagnostics_check_of_65_slots_stays_in_its_rows(sv):
+    """One check of 65 due slots writes exactly one lbm_sc_diag per row: a guard
+    placed right after the last row is untouched, and each row's max|u_phys|
+    equals the handle diagnostics of that lattice."""
+    import torch
+    from paper_1112_5547_gb300 import inputs, lbm_sc
+    srv = sv.Server(chunk=100, check_every=500)
+    w = sv.DIAG_DOUBLES
+    assert w * 8 == __import__("ctypes").sizeof(lbm_sc.lbm_sc_diag)
+    n = 65
+    guard = 12345.678
+    buf = torch.full((n * w + 64,), guard, dtype=torch.float64, device="cuda")
+    srv._diag = buf[:n * w].view(n, w)
+
+    class _S:
+        pass
+
+    slots = []
+    with torch.cuda.stream(srv.stream):
+        for k in range(n):
+            sh = (24, 24 + (k % 3) * 8)
+            s = _S()
+            s.lat = lbm_sc.Lattice(lbm_sc.LBM_D2Q9, sh, 1.0, 1.0, 2.4 / 1.04, "f32", stream=srv.stream).init(
+                *inputs.drop(sh, 5, seed=k, dtype=np.float32))
+            s.lat.step(3)
+            slots.append(s)
+        got = srv._check(slots)
+        srv.stream.synchronize()
+    assert np.all(buf[n * w:].cpu().numpy() == guard)
+    for s, u in zip(slots, got):
+        assert u == s.lat.diagnostics()["max_speed"]
+        s.lat.close()

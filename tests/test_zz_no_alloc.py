@@ -31,11 +31,16 @@ def _from_device(dev):
     return d.as_dict()
 
 
-@pytest.mark.parametrize("lattice,shape,precision", [(1, (24, 40, 70), "f32"), (0, (96, 130), "f64")])
+@pytest.mark.parametrize("lattice,shape,precision", [(1, (24, 40, 70), "f32"), (0, (96, 130), "f64"),
+                                                     (1, (24, 40, 70), "bf16"), (1, (24, 40, 70), "bf16_rest")])
 def test_noalloc_diagnostics_match_handle_diagnostics(sc, lattice, shape, precision):
+    """Also on 16-bit storage (reference- and rest-offset), whose buffers carry the
+    two FP32 density planes of the rest-offset mode after the populations: the
+    static-scratch variant must read them at the handle's own layout."""
     import torch
     f = inputs.drop(shape, min(shape) / 4.0, seed=21)
-    lat = sc.Lattice(lattice, shape, 1.0, 0.8, G0, precision).init(*f).step(15)
+    ref_rho = (1.0, 0.04) if precision == "bf16" else (0.0, 0.0)
+    lat = sc.Lattice(lattice, shape, 1.0, 0.8, G0, precision, *ref_rho).init(*f).step(15)
     centre = tuple(n / 2.0 for n in reversed(shape))
     win = sc.Window(centre, 3.0, min(shape) / 2.5)
     ref = lat.diagnostics(win)
