@@ -65,11 +65,14 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
  * equilibrium of a reference density, one per species) in bf16 / fp16 and
  * decode to FP32 on load.  The _REST variants store h_is(n) = f_is(n) -
  * w_i rho_s(n), the offset from the rest equilibrium of the density of the
- * node n the value is stored at, with rho_s(n) itself kept in FP32: 16-bit
- * populations plus two FP32 density planes per buffer (84 instead of 152 bytes
- * per D3Q19 node), and an error that no longer grows with |rho_s - rho_ref_s|,
- * which in a two-phase lattice is large in one of the phases whatever
- * rho_ref_s is.  The paper computes in double precision throughout; the
+ * node n the value is stored at, with rho_s(n) itself kept in FP32, the two
+ * species' offsets of one direction paired in one 32-bit word (A in the low
+ * half, B in the high half) and encoded / decoded with one fused multiply-add
+ * each (h = round16(fma(-w_i, rho_s, f)), f = fma(w_i, rho_s, h)): 16-bit
+ * populations plus one float2 density plane per buffer (84 instead of 152
+ * bytes per D3Q19 node), and an error that no longer grows with
+ * |rho_s - rho_ref_s|, which in a two-phase lattice is large in one of the
+ * phases whatever rho_ref_s is.  The paper computes in double precision throughout; the
  * 16-bit storage modes are a bandwidth option of this library. */
 typedef enum {
     LBM_F64 = 0,
@@ -128,7 +131,9 @@ typedef struct {
                          /* (F_s,x = rho_s A sin(2 pi y / ny)); finite; 0 = none    */
     int32_t model;       /* lbm_model (0 = the SC model)                             */
     int32_t reserved;    /* set to 0                                                 */
-    double kappa;        /* LBM_MODEL_FE: gradient coefficient kappa (finite)        */
+    double kappa;        /* LBM_MODEL_FE: gradient coefficient kappa (finite); a     */
+                         /* negative value selects the Eq. FEtau coefficient        */
+                         /* g cs2^2 / 4 = G / 36                                    */
     double gamma;        /* LBM_MODEL_FE: Gamma of Eq. EQFE2 (finite)                */
 } lbm_sc_params;
 
@@ -162,25 +167,22 @@ typedef struct lbm_sc_handle lbm_sc_handle;
 
 /* Launch shape of the step kernel.  tile selects the CTA tile of x by y
  * columns and the kernel: 0 = 32x8, 1 = 32x16, 2 = 64x8, 3 = 32x4, 4 = 64x4
- * (register-pipelined kernel, every lattice and precision); 5 = 32x8 with 3
- * shared-memory stages, 6 = 32x8 with 4 stages, 7 = 64x4 with 3 stages
- * (persistent cp.async kernel, D3Q19 with LBM_F32 only); 8 = 32x8, 9 = 64x4,
- * 10 = 32x4 (software-pipelined kernel with loads two planes ahead, D3Q19,
- * every precision but the _REST ones); 11 = 32x4, 12 = 32x8, 13 = 64x4, 14 = 32x4 (low-register
+ * (register-pipelined kernel, every lattice and precision); 5 to 10 are
+ * retired ids (kernels measured slower at every size and removed; rejected
+ * with LBM_ERR_INVALID_ARG); 11 = 32x4, 12 = 32x8, 13 = 64x4, 14 = 32x4 (low-register
  * kernel that pulls a plane a second time for its collision, every lattice and
  * precision; 11 and 14 differ in the register budget); 15 = 32x4, 16 = 32x8,
  * 17 = 16x8 (register-pipelined kernel holding three planes of pulls, D3Q19
  * with 32-bit storage or the reference-offset 16-bit storage); 18 = 32x8 with 3 stages, 19 = 64x4 with 3
  * stages, 20 = 32x4 with 4 stages, 21 = 32x4 with 2 stages, and the cluster
  * launches 22 = 64x4 in clusters of 1x2 tiles, 23 = 64x4 in 1x4, 24 = 64x4 in
- * 2x2, 25 = 32x8 in 2x2, and with the L2 fetch granularity of the tensor
- * copies changed from 256 bytes: 26 = 64x4 in 1x2 with 128 bytes, 27 = the
- * same with none, 28 = 32x8 with 128 bytes, 29 = 32x8 with none (TMA-fed
- * kernel, D3Q19 with LBM_F32 only, lattices at least one tile wide in x and y
- * whose tile counts divide by the cluster shape); 30 = 64x4 in 1x2 clusters
+ * 2x2, 25 = 32x8 in 2x2 (TMA-fed kernel, D3Q19 with LBM_F32 only, lattices
+ * at least one tile wide in x and y whose tile counts divide by the cluster
+ * shape); 26 to 29 are retired ids (other L2 fetch granularities of the
+ * tensor copies, no faster); 30 = 64x4 in 1x2 clusters
  * with 3 stages, 31 = the same with 4 stages, 32 = 32x8 with 3 stages (the
  * TMA-fed kernel for the four 16-bit storage precisions, same size rules; the
- * rest-offset ones also stage the FP32 densities); 33 = 64x6 with 2 stages in
+ * rest-offset ones also stage the float2 densities); 33 = 64x6 with 2 stages in
  * 1x2 clusters, 34 = the same without clusters (FP32, 384 threads: 12 warps
  * per SM), 35 = 64x6 with 3 stages in 1x2 clusters (16-bit), 36 = 32x12 with
  * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
@@ -289,11 +291,34 @@ LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t 
  * of pitch_x * pitch_y * nz values each; node (x, y, z) sits at
  * (x + ghost_x) + pitch_x * ((y + ghost_y) + pitch_y * z).  The columns
  * x = -2, -1, nx, nx + 1 and rows y = -2, -1, ny, ny + 1 hold periodic images;
- * other padding is unused.  For the _REST precisions the 2 x Q planes are
- * followed by 2 planes of FP32 densities rho_s (species s at plane s) with the
- * same pitches, node (x, y, z) at the same index.  Any output pointer may be NULL. */
+ * other padding is unused.  For the _REST precisions a stored value is one
+ * 32-bit word holding both species (elem_bytes = 4): Q planes (index i) of
+ * such words, followed by one plane of float2 densities (rho_A, rho_B) with the
+ * same pitches, node (x, y, z) at the same index (8 bytes per node).  Any output pointer may be NULL. */
 LBM_SC_API lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y,
                                     int* ghost_x, int* ghost_y, const void** d_populations);
+
+/* ---- Failure detection -----------------------------------------------------
+ * The paper has no counterpart: these two calls test the library's bounded
+ * device waits (every mbarrier wait of the TMA-fed kernels, tile kinds 5 and 6,
+ * gives up after a fixed number of tries, raises the device error word, waits
+ * with the same bound for its own copies still in flight and returns, so the
+ * CUDA context stays usable and lbm_sc_diagnostics reports LBM_ERR_TIMEOUT).
+ *
+ * lbm_sc_set_wait_probe: tries > 0 makes the first CTA of every later step of
+ * this handle (tile (0, 0), first z chunk) wait `tries` tries on a barrier
+ * that nothing ever arrives on before its first plane, so that wait runs out
+ * and the error path runs; that CTA then stores nothing for that step (the
+ * handle's state is no longer a solution: re-initialise it).  tries = 0 turns
+ * the hook off.  Other tile kinds ignore it.  The error word stays set until
+ * lbm_sc_init_fields clears it.  Returns LBM_ERR_INVALID_ARG for tries < 0. */
+LBM_SC_API lbm_status lbm_sc_set_wait_probe(lbm_sc_handle* h, int tries);
+
+/* The device error word of the handle, after synchronising its stream: 0 = no
+ * wait expired; bit 0 set = a bounded wait expired; bit 1 set as well = a CTA
+ * could not confirm, within the same bound, that the copies into its shared
+ * memory had landed before it left (the device state is then suspect). */
+LBM_SC_API lbm_status lbm_sc_error_word(lbm_sc_handle* h, int* host_out);
 
 /* ---- Ragged batch ---------------------------------------------------------
  * Many independent lattices of different sizes and parameters advanced

@@ -34,19 +34,9 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 int q_of(int lattice) { return lattice == LBM_D2Q9 ? 9 : 19; }
 int d_of(int lattice) { return lattice == LBM_D2Q9 ? 2 : 3; }
 
-size_t store_bytes(int precision) {
-    switch (precision) {
-        case LBM_F64: return 8;
-        case LBM_F32: return 4;
-        case LBM_F32_STORE_BF16:
-        case LBM_F32_STORE_F16:
-        case LBM_F32_STORE_BF16_REST:
-        case LBM_F32_STORE_F16_REST: return 2;
-    }
-    return 0;
-}
+size_t store_bytes(int precision) { return (size_t)lbmsc::storage_elem_bytes(precision); }
 
-bool rest_offsets(int precision) { return precision == LBM_F32_STORE_BF16_REST || precision == LBM_F32_STORE_F16_REST; }
+bool rest_offsets(int precision) { return lbmsc::rest_precision(precision); }
 
 size_t compute_bytes(int precision) { return precision == LBM_F64 ? 8 : 4; }
 
@@ -106,21 +96,22 @@ Plan make_plan(const lbm_sc_params* p) {
     pl.body_A = p->body_A;
     pl.forcing = p->forcing;
     pl.model = p->model;
-    pl.kappa = p->kappa;
+    // a negative kappa selects the gradient coefficient of Eq. FEtau, g cs2^2 / 4
+    pl.kappa = p->kappa < 0.0 ? p->G / 36.0 : p->kappa;
     pl.gamma = p->gamma;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo,
                             pl.Np);
     return pl;
 }
 
-// One population buffer: 2 species x Q ghost-padded planes.
+// One population buffer: 2 species x Q ghost-padded planes (Q paired planes
+// and one float2 density plane for the rest-offset precisions).
 size_t population_bytes(const lbm_sc_params* p) {
     int px, py, gxo, gyo;
     long long Np;
     lbmsc::storage_geometry(p->nx, p->ny, p->nz, (int)store_bytes(p->precision), px, py, gxo, gyo, Np);
-    // rest-offset storage keeps the two FP32 density planes after the populations
-    return (size_t)2 * q_of(p->lattice) * (size_t)Np * store_bytes(p->precision) +
-           (rest_offsets(p->precision) ? (size_t)2 * (size_t)Np * 4 : 0);
+    return (size_t)lbmsc::population_planes(p->lattice, p->precision) * (size_t)Np * store_bytes(p->precision) +
+           (rest_offsets(p->precision) ? (size_t)Np * 8 : 0);
 }
 
 size_t partial_bytes(const Plan& pl) {
@@ -198,10 +189,7 @@ lbm_status lbm_sc_set_tuning(lbm_sc_handle* h, const lbm_sc_tuning* t) {
     if (!lbmsc::tile_fits(t->tile, h->plan)) return LBM_ERR_INVALID_ARG;
     const lbmsc::TileShape ts = lbmsc::kTiles[t->tile];
     h->plan.step_tile = t->tile;
-    // persistent kernels: ~8 items per SM, chunks of at least 32 planes
-    int zc = t->zchunk != 0 ? t->zchunk
-             : ts.kind == 1 ? pick_zchunk(&h->params, ts.tx, ts.ty, 8LL * h->plan.sm_count, 32)
-                            : pick_zchunk(&h->params, ts.tx, ts.ty);
+    int zc = t->zchunk != 0 ? t->zchunk : pick_zchunk(&h->params, ts.tx, ts.ty);
     if (h->params.lattice == LBM_D2Q9 || zc > h->params.nz) zc = h->params.lattice == LBM_D2Q9 ? 1 : h->params.nz;
     h->plan.step_zchunk = zc;
     return LBM_OK;
@@ -211,6 +199,22 @@ lbm_status lbm_sc_get_tuning(const lbm_sc_handle* h, lbm_sc_tuning* t) {
     if (!h || !t) return LBM_ERR_INVALID_ARG;
     t->tile = h->plan.step_tile;
     t->zchunk = h->plan.step_zchunk;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_set_wait_probe(lbm_sc_handle* h, int tries) {
+    if (!h || tries < 0) return LBM_ERR_INVALID_ARG;
+    h->plan.wait_probe = tries;
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_error_word(lbm_sc_handle* h, int* host_out) {
+    if (!h || !host_out) return LBM_ERR_INVALID_ARG;
+    int w = 0;
+    if (cudaMemcpyAsync(&w, h->plan.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    *host_out = w;
     return LBM_OK;
 }
 

@@ -41,8 +41,6 @@ cudaError_t device_scratch(double** out) {
     return cudaSuccess;
 }
 
-int elem_bytes(int precision) { return precision == LBM_F64 ? 8 : precision == LBM_F32 ? 4 : 2; }
-
 }  // namespace
 
 extern "C" LBM_SC_API lbm_status lbm_sc_diagnostics_noalloc(const lbm_sc_params* p, const void* d_populations,
@@ -72,7 +70,7 @@ extern "C" LBM_SC_API lbm_status lbm_sc_diagnostics_noalloc(const lbm_sc_params*
     pl.model = p->model;
     pl.kappa = p->kappa;
     pl.gamma = p->gamma;
-    lbmsc::storage_geometry(p->nx, p->ny, p->nz, elem_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo, pl.Np);
+    lbmsc::storage_geometry(p->nx, p->ny, p->nz, lbmsc::storage_elem_bytes(p->precision), pl.px, pl.py, pl.gxo, pl.gyo, pl.Np);
     pl.err = nullptr;
 
     const long long parts = lbmsc::fused_blocks(pl);

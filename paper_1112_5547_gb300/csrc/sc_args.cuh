@@ -35,6 +35,7 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     a.model = p.model;
     a.kappa = (C)p.kappa;
     a.gamma = (C)p.gamma;
+    a.wait_probe = p.wait_probe;
     return a;
 }
 
@@ -57,21 +58,22 @@ constexpr CUtensorMapL2promotion kPromotion[4] = {CU_TENSOR_MAP_L2_PROMOTION_NON
                                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B};
 
 // Tensor map of the population planes of one buffer as a 4-D array: x and y
-// of the ghost-padded plane, z, and the plane index s*Q + i; boxes of
-// bx x by x 1 x 1 values of elem_bytes (4: FP32, 2: 16-bit storage copied as
-// raw 16-bit words).  The box x start of a tile at x0 is x0 + gxo - 16 bytes
+// of the ghost-padded plane, z, and the plane index (s*Q + i, or i for the
+// paired rest-offset words; planes = 0 means 2 Q); boxes of bx x by x 1 x 1
+// values of elem_bytes (4: FP32 or a paired rest-offset word, 2: 16-bit
+// storage copied as raw 16-bit words).  The box x start of a tile at x0 is x0 + gxo - 16 bytes
 // of values, so gxo and the row pitch must be whole 16-byte units for it to be
 // 16-byte aligned, as tensor copies require.  promo indexes kPromotion (the
 // L2 fetch granularity on a miss).
 inline cudaError_t encode_population_map(const Plan& p, const void* fin, int bx, int by, CUtensorMap* map,
-                                         int promo = 3, int elem_bytes = 4) {
+                                         int promo = 3, int elem_bytes = 4, int planes = 0) {
     const int e = elem_bytes;
     if ((e != 4 && e != 2) || p.gxo * e < 16 || (p.gxo * e) % 16 != 0 || ((long long)p.px * e) % 16 != 0 ||
         (bx * e) % 16 != 0)
         return cudaErrorInvalidValue;
     auto enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    const int q2 = 2 * (p.lattice == 0 ? 9 : 19);
+    const int q2 = planes > 0 ? planes : 2 * (p.lattice == 0 ? 9 : 19);
     const cuuint64_t dims[4] = {(cuuint64_t)p.px, (cuuint64_t)p.py, (cuuint64_t)p.nz, (cuuint64_t)q2};
     const cuuint64_t strides[3] = {(cuuint64_t)p.px * e, (cuuint64_t)p.px * p.py * e, (cuuint64_t)p.Np * e};
     const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
@@ -83,19 +85,21 @@ inline cudaError_t encode_population_map(const Plan& p, const void* fin, int bx,
     return cudaSuccess;
 }
 
-// Tensor map of the two FP32 density planes of a rest-offset buffer (rho_base
-// = the first of them): x, y, z, species; boxes of bx x by x 1 x 1.
-inline cudaError_t encode_rho_map(const Plan& p, const float* rho_base, int bx, int by, CUtensorMap* map,
+// Tensor map of the float2 density plane of a rest-offset buffer (rho_base =
+// its first pair) as floats: x (two floats per node), y, z, and a unit fourth
+// dimension; boxes of 2 bx floats (bx nodes) x by x 1 x 1.  A box starting at
+// node x0 - 2 of a tile is 16-byte aligned when gxo and x0 are even.
+inline cudaError_t encode_rho_map(const Plan& p, const float2* rho_base, int bx, int by, CUtensorMap* map,
                                   int promo = 3) {
-    if ((p.px * 4) % 16 != 0 || (bx * 4) % 16 != 0 || (p.gxo - 4) * 4 % 16 != 0 || p.gxo < 4)
+    if ((p.px * 8) % 16 != 0 || (bx * 8) % 16 != 0 || p.gxo < 2 || (p.gxo - 2) % 2 != 0)
         return cudaErrorInvalidValue;
     auto enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    const cuuint64_t dims[4] = {(cuuint64_t)p.px, (cuuint64_t)p.py, (cuuint64_t)p.nz, 2};
-    const cuuint64_t strides[3] = {(cuuint64_t)p.px * 4, (cuuint64_t)p.px * p.py * 4, (cuuint64_t)p.Np * 4};
-    const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+    const cuuint64_t dims[4] = {(cuuint64_t)p.px * 2, (cuuint64_t)p.py, (cuuint64_t)p.nz, 1};
+    const cuuint64_t strides[3] = {(cuuint64_t)p.px * 8, (cuuint64_t)p.px * p.py * 8, (cuuint64_t)p.Np * 8};
+    const cuuint32_t box[4] = {(cuuint32_t)(2 * bx), (cuuint32_t)by, 1, 1};
     const cuuint32_t es[4] = {1, 1, 1, 1};
-    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(rho_base), dims, strides, box, es,
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(rho_base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, kPromotion[promo & 3],
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;

@@ -48,9 +48,8 @@ struct D3Q19 {
 
 // Storage codecs: load/store one population value.  16-bit types hold the
 // offset h = f - w_i rho_ref (the caller passes the offset w_i rho_ref).
-// The rest-offset types (kRest) hold h = f - w_i rho_s(n), rho_s(n) the density
-// of the node n the value was stored at, kept in FP32 beside the populations
-// (see rest_rho); the caller passes w_i rho_s(n) as the offset.
+// The rest-offset types (kRest) pair the two species in one word per
+// direction and offset from the storing node's own density (see bf16_rest).
 template <class S> struct Codec;
 
 template <> struct Codec<double> {
@@ -91,24 +90,35 @@ template <> struct Codec<__half> {
     }
 };
 
-// 16-bit values offset from the rest equilibrium of their own node.
+// Species-paired 16-bit rest-offset storage.  One 32-bit word per node and
+// direction holds the offsets of both species, species A in the low 16 bits
+// and species B in the high 16 bits (bf16 or fp16):
+//   h_is(n) = f_is(n) - w_i rho_s(n),
+// rho_s(n) the density of the node n the word is stored at, which is kept in
+// FP32 beside the populations (rest_rho: one float2 (rho_A, rho_B) per node).
+// Encoding and decoding take one fused multiply-add per value,
+//   h = round16(fma(-w_i, rho_s(n), f)),   f = fma(w_i, rho_s(n), h),
+// so a value pulled from n gets back exactly the product it was offset by.
+// Pairing the species halves the load, store and conversion instructions of
+// the unpaired 16-bit layout (one word, one pack, one density pair per
+// direction instead of two of each).
 struct bf16_rest {
-    __nv_bfloat16 v;
+    uint32_t v;
 };
 struct f16_rest {
-    __half v;
+    uint32_t v;
 };
 
 template <> struct Codec<bf16_rest> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = true;
-    __device__ __forceinline__ static C decode(bf16_rest v, C off) { return __fadd_rn(__bfloat162float(v.v), off); }
-    __device__ __forceinline__ static C load(const bf16_rest* p, C off) {
-        return __fadd_rn(__bfloat162float(__ldg(&p->v)), off);
-    }
-    __device__ __forceinline__ static void store(bf16_rest* p, C v, C off) {
-        p->v = __float2bfloat16_rn(__fsub_rn(v, off));
+    __device__ __forceinline__ static C lo(uint32_t v) { return __uint_as_float(v << 16); }
+    __device__ __forceinline__ static C hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
+    // (a, b) -> one word, a in the low half (round to nearest even)
+    __device__ __forceinline__ static uint32_t pack(C a, C b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return (uint32_t)__bfloat16_as_ushort(h.x) | ((uint32_t)__bfloat16_as_ushort(h.y) << 16);
     }
 };
 
@@ -116,23 +126,32 @@ template <> struct Codec<f16_rest> {
     using C = float;
     static constexpr bool kOffset = true;
     static constexpr bool kRest = true;
-    __device__ __forceinline__ static C decode(f16_rest v, C off) { return __fadd_rn(__half2float(v.v), off); }
-    __device__ __forceinline__ static C load(const f16_rest* p, C off) {
-        return __fadd_rn(__half2float(__ldg(&p->v)), off);
-    }
-    __device__ __forceinline__ static void store(f16_rest* p, C v, C off) {
-        p->v = __float2half_rn(__fsub_rn(v, off));
+    __device__ __forceinline__ static C lo(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu))); }
+    __device__ __forceinline__ static C hi(uint32_t v) { return __half2float(__ushort_as_half((unsigned short)(v >> 16))); }
+    __device__ __forceinline__ static uint32_t pack(C a, C b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return (uint32_t)__half_as_ushort(h.x) | ((uint32_t)__half_as_ushort(h.y) << 16);
     }
 };
 
-// FP32 density planes of a rest-offset population buffer: they follow its
-// 2 Q population planes, species s at plane s, same ghost-padded geometry
-// (node index cell(), values of 4 bytes).
-template <class L, class S> __host__ __device__ __forceinline__ float* rest_rho(S* buf, long long Np) {
-    return reinterpret_cast<float*>(buf + (size_t)2 * L::Q * (size_t)Np);
+// Decode and encode of one paired rest-offset word (the species' densities r.x, r.y of the storing node).
+template <class S>
+__device__ __forceinline__ void rest_decode(uint32_t v, float w, float2 r, float& fA, float& fB) {
+    fA = __fmaf_rn(w, r.x, Codec<S>::lo(v));
+    fB = __fmaf_rn(w, r.y, Codec<S>::hi(v));
 }
-template <class L, class S> __host__ __device__ __forceinline__ const float* rest_rho(const S* buf, long long Np) {
-    return reinterpret_cast<const float*>(buf + (size_t)2 * L::Q * (size_t)Np);
+template <class S> __device__ __forceinline__ uint32_t rest_encode(float fA, float fB, float w, float2 r) {
+    return Codec<S>::pack(__fmaf_rn(-w, r.x, fA), __fmaf_rn(-w, r.y, fB));
+}
+
+// Density plane of a rest-offset population buffer: it follows the Q paired
+// population planes, one float2 (rho_A, rho_B) per node, same ghost-padded
+// geometry (node index cell()).
+template <class L, class S> __host__ __device__ __forceinline__ float2* rest_rho(S* buf, long long Np) {
+    return reinterpret_cast<float2*>(buf + (size_t)L::Q * (size_t)Np);
+}
+template <class L, class S> __host__ __device__ __forceinline__ const float2* rest_rho(const S* buf, long long Np) {
+    return reinterpret_cast<const float2*>(buf + (size_t)L::Q * (size_t)Np);
 }
 
 // Per-lattice arguments of the step / moments kernels (compute type C).
@@ -157,6 +176,8 @@ template <class S> struct LatticeArgs {
     int forcing;        // kForcingShift (Sec. 2.1) or kForcingGuo (Sec. 2.3)
     int model;          // kModelSC (Sec. 2.1) or kModelFE (Sec. 2.2: species 0 = f, 1 = g)
     C kappa, gamma;     // FE gradient coefficient and Gamma (mobility Gamma (tau_g - 1/2))
+    int wait_probe;     // > 0: the TMA kernels' first CTA waits this many tries on a barrier
+                        // nothing arrives on (failure-detection test hook); 0 = off
 };
 
 // How forces enter the collision (lbm_forcing), and the model (lbm_model).

@@ -3,10 +3,8 @@
 
 #include <cstring>
 
-#include "sc_async.cuh"
 #include "sc_tma.cuh"
 #include "sc_kernels.cuh"
-#include "sc_pipe.cuh"
 #include "sc_regpipe.cuh"
 #include "sc_launch.cuh"
 #include "sc_args.cuh"
@@ -20,26 +18,6 @@ cudaError_t step_tiled(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) 
     // register budget: 65536 / (threads * CTAs per SM)
     constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 4 : (TX * TY <= 256 ? 2 : 1));
     sc_fused_kernel<L, S, TX, TY, kModeStep, kMin><<<step_grid(p), dim3(TX, TY), 0, st>>>(a, fo);
-    return cudaGetLastError();
-}
-
-template <int TX, int TY, int STAGES>
-cudaError_t step_async(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
-    using T = AsyncTile<TX, TY, STAGES>;
-    auto kern = sc_step_async_kernel<TX, TY, STAGES>;
-    // the attribute is per function and device: set it on every launch (a cheap host call)
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, T::smem_bytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int tiles_x = (p.nx + TX - 1) / TX, tiles_y = (p.ny + TY - 1) / TY;
-    const int nchunks = (p.nz + p.step_zchunk - 1) / p.step_zchunk;
-    const long long items = (long long)tiles_x * tiles_y * nchunks;
-    long long grid = (long long)p.sm_count * per_sm;
-    if (grid > items) grid = items;
-    kern<<<(unsigned)grid, dim3(TX, TY), T::smem_bytes, st>>>(a, tiles_x, tiles_y, nchunks);
     return cudaGetLastError();
 }
 
@@ -64,9 +42,10 @@ template <class S, int TX, int TY, int ST, int FORCING> struct TmaLaunch<D3Q19, 
             if (p.nx < TX || p.ny < TY) return cudaErrorInvalidValue;
             TmaMaps maps;
             memset(&maps, 0, sizeof(maps));
-            cudaError_t e = encode_population_map(p, a.fin, T::BX, T::BY, &maps.pop, ts.promo, T::E);
-            if (e == cudaSuccess && T::REST)
-                e = encode_rho_map(p, rest_rho<D3Q19>(a.fin, p.Np), T::RBX, T::RBY, &maps.rho, ts.promo);
+            cudaError_t e = encode_population_map(p, a.fin, T::BX, T::BY, &maps.pop, ts.promo, T::E, T::Q2);
+            if constexpr (T::REST)
+                if (e == cudaSuccess)
+                    e = encode_rho_map(p, rest_rho<D3Q19>(a.fin, p.Np), T::RBX, T::RBY, &maps.rho, ts.promo);
             if (e != cudaSuccess) return e;
             auto kern = sc_step_tma_kernel<TX, TY, ST, S, FORCING>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
@@ -106,48 +85,6 @@ template <class S, int TX, int TY, int MINB> struct RegPipeLaunch<D3Q19, S, TX, 
     }
 };
 
-template <class S, int TX, int TY>
-cudaError_t step_pipe(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
-    using T = PipeTile<S, TX, TY>;
-    using C = typename Codec<S>::C;
-    constexpr int kMin = sizeof(C) == 8 ? 1 : (TX * TY <= 128 ? 3 : 2);
-    auto kern = sc_step_pipe_kernel<S, TX, TY, kMin>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((p.nx + TX - 1) / TX), (unsigned)((p.ny + TY - 1) / TY),
-                    (unsigned)((p.nz + p.step_zchunk - 1) / p.step_zchunk));
-    kern<<<grid, dim3(TX, TY), T::smem_bytes, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <class L, class S> struct PipeDispatch {
-    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
-};
-template <class S> struct PipeDispatch<D3Q19, S> {
-    static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
-        switch (p.step_tile) {
-            case 8: return step_pipe<S, 32, 8>(p, a, st);
-            case 9: return step_pipe<S, 64, 4>(p, a, st);
-            case 10: return step_pipe<S, 32, 4>(p, a, st);
-        }
-        return cudaErrorInvalidValue;
-    }
-};
-
-template <class L, class S> struct AsyncDispatch {
-    static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
-};
-template <> struct AsyncDispatch<D3Q19, float> {
-    static cudaError_t run(const Plan& p, const LatticeArgs<float>& a, cudaStream_t st) {
-        switch (p.step_tile) {
-            case 5: return step_async<32, 8, 3>(p, a, st);
-            case 6: return step_async<32, 8, 4>(p, a, st);
-            case 7: return step_async<64, 4, 3>(p, a, st);
-        }
-        return cudaErrorInvalidValue;
-    }
-};
-
 template <class L, class S> cudaError_t step_typed_other(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st);
 
 template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fin, void* fout, cudaStream_t st) {
@@ -155,13 +92,12 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
     LatticeArgs<S> a = make_args<S>(p, fin, fout);
     a.zchunk = p.step_zchunk;
     static_assert(kTiles[0].tx == 32 && kTiles[0].ty == 8 && kTiles[1].ty == 16 && kTiles[2].tx == 64 &&
-                      kTiles[3].ty == 4 && kTiles[4].tx == 64 && kTiles[5].stages == 3 && kTiles[6].stages == 4 &&
-                      kTiles[7].tx == 64 && kTiles[8].kind == 2 && kTiles[9].tx == 64 && kTiles[10].ty == 4 &&
-                      kTiles[11].stages == 6 && kTiles[12].ty == 8 && kTiles[13].tx == 64 && kTiles[14].stages == 4 &&
+                      kTiles[3].ty == 4 && kTiles[4].tx == 64 && kTiles[5].kind == kRetired &&
+                      kTiles[10].kind == kRetired && kTiles[11].stages == 6 && kTiles[12].ty == 8 && kTiles[13].tx == 64 && kTiles[14].stages == 4 &&
                       kTiles[15].kind == 4 && kTiles[16].ty == 8 && kTiles[17].tx == 16 && kTiles[18].kind == 5 &&
                       kTiles[19].tx == 64 && kTiles[20].stages == 4 && kTiles[21].stages == 2 && kTiles[22].cy == 2 &&
-                      kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kTiles[26].promo == 2 &&
-                      kTiles[27].promo == 0 && kTiles[28].tx == 32 && kTiles[29].promo == 0 && kTiles[30].kind == 6 &&
+                      kTiles[23].cy == 4 && kTiles[24].cx == 2 && kTiles[25].tx == 32 && kTiles[26].kind == kRetired &&
+                      kTiles[29].kind == kRetired && kTiles[30].kind == 6 &&
                       kTiles[31].stages == 4 && kTiles[32].tx == 32 && kTiles[33].ty == 6 && kTiles[34].stages == 2 &&
                       kTiles[35].kind == 6 && kTiles[36].ty == 12 && kTiles[37].cy == 1 && kTiles[38].kind == 6 &&
                       kTiles[39].ty == 8 && kTiles[40].tx == 48 && kTiles[41].cy == 1 && kNumTiles == 42,
@@ -198,12 +134,6 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
         case 2: return step_tiled<L, S, 64, 8>(p, a, st);
         case 3: return step_tiled<L, S, 32, 4>(p, a, st);
         case 4: return step_tiled<L, S, 64, 4>(p, a, st);
-        case 5:
-        case 6:
-        case 7: return AsyncDispatch<L, S>::run(p, a, st);
-        case 8:
-        case 9:
-        case 10: return PipeDispatch<L, S>::run(p, a, st);
         case 11: return step_reload<L, S, 32, 4, 6>(p, a, st);
         case 12: return step_reload<L, S, 32, 8, 3>(p, a, st);
         case 13: return step_reload<L, S, 64, 4, 3>(p, a, st);
@@ -222,10 +152,6 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 23:
             case 24: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
             case 25: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
-            case 26:
-            case 27: return TmaLaunch<L, S, 64, 4, 3>::run(p, a, st);
-            case 28:
-            case 29: return TmaLaunch<L, S, 32, 8, 3>::run(p, a, st);
             case 33: return TmaLaunch<L, S, 64, 6, 2>::run(p, a, st);
             case 34:
                 if (p.model == kModelFE) return TmaLaunch<L, S, 64, 6, 2, kSchemeFE>::run(p, a, st);

@@ -44,14 +44,15 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
     for (int i = 0; i < L::Q; ++i) {
         // x - c_x and y - c_y lie in [-1, n]: the ghost images make them valid
         const size_t node = cell(a, x - L::c(i, 0), y - L::c(i, 1), zs[L::c(i, 2) + 1]);
+        if constexpr (Codec<S>::kRest) {
+            const uint32_t v = __ldg(&(a.fin + (size_t)i * (size_t)a.Np + node)->v);
+            rest_decode<S>(v, (C)L::w(i), __ldg(rest_rho<L>(a.fin, a.Np) + node), f[0][i], f[1][i]);
+        } else {
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            C off;
-            if constexpr (Codec<S>::kRest)
-                off = __fmul_rn((C)L::w(i), __ldg(rest_rho<L>(a.fin, a.Np) + (size_t)s * (size_t)a.Np + node));
-            else
-                off = Codec<S>::kOffset ? (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B)) : (C)0;
-            f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.Np + node, off);
+            for (int s = 0; s < 2; ++s) {
+                const C off = Codec<S>::kOffset ? (C)__fmul_rn((float)L::w(i), (float)(s == 0 ? a.ref_A : a.ref_B)) : (C)0;
+                f[s][i] = Codec<S>::load(a.fin + (size_t)(s * L::Q + i) * (size_t)a.Np + node, off);
+            }
         }
     }
 }
@@ -61,18 +62,20 @@ __device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
                                            const typename Codec<S>::C (&f)[2][L::Q]) {
     using C = typename Codec<S>::C;
     if constexpr (Codec<S>::kRest) {
-        // the cell's own density (sum of what it stores, in a fixed order) is the
-        // offset base, kept in FP32 for the nodes that pull from this cell
+        // the cell's own densities (sums of what it stores, in a fixed order) are
+        // the offset bases, kept in FP32 for the nodes that pull from this cell
+        float2 r;
+        r.x = f[0][0];
+        r.y = f[1][0];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            C r = f[s][0];
-#pragma unroll
-            for (int i = 1; i < L::Q; ++i) r = __fadd_rn(r, f[s][i]);
-            rest_rho<L>(a.fout, a.Np)[(size_t)s * (size_t)a.Np + c] = r;
-#pragma unroll
-            for (int i = 0; i < L::Q; ++i)
-                Codec<S>::store(a.fout + (size_t)(s * L::Q + i) * (size_t)a.Np + c, f[s][i], __fmul_rn((C)L::w(i), r));
+        for (int i = 1; i < L::Q; ++i) {
+            r.x = __fadd_rn(r.x, f[0][i]);
+            r.y = __fadd_rn(r.y, f[1][i]);
         }
+        __stcs(rest_rho<L>(a.fout, a.Np) + c, r);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            __stcs(&(a.fout + (size_t)i * (size_t)a.Np + c)->v, rest_encode<S>(f[0][i], f[1][i], (C)L::w(i), r));
     } else {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {

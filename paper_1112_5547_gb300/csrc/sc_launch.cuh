@@ -26,7 +26,31 @@ struct Plan {
     int px, py, gxo, gyo;  // ghost-padded storage geometry (see LatticeArgs)
     long long Np;          // values per population plane
     int* err;              // device error word (set by a kernel whose bounded wait expired)
+    int wait_probe;        // failure-detection test hook (lbm_sc_set_wait_probe); 0 = off
 };
+
+// Bytes of one stored element for a precision (lbm_precision): FP64 8, FP32 4,
+// reference-offset 16-bit 2, paired rest-offset 16-bit 4 (both species of one
+// direction in one word); 0 for an unknown precision.
+inline int storage_elem_bytes(int precision) {
+    switch (precision) {
+        case 0: return 8;
+        case 1: return 4;
+        case 2:
+        case 3: return 2;
+        case 4:
+        case 5: return 4;
+    }
+    return 0;
+}
+inline bool rest_precision(int precision) { return precision == 4 || precision == 5; }
+// Population planes of one buffer: 2 Q (a plane per species and direction), or
+// Q paired planes for the rest-offset precisions (which add one plane of float2
+// densities after them).
+inline int population_planes(int lattice, int precision) {
+    const int q = lattice == 0 ? 9 : 19;
+    return rest_precision(precision) ? q : 2 * q;
+}
 
 // Ghost-padded storage geometry for a lattice.  Node x = 0 sits 128 bytes into
 // each row and the row pitch is a multiple of 128 bytes, so every warp's row
@@ -52,9 +76,6 @@ inline void storage_geometry(int nx, int ny, int nz, int elem_bytes, int& px, in
 constexpr int kTX = 32;
 constexpr int kTY = 8;
 // kind 0: register-pipelined kernel (every lattice and precision);
-// kind 1: persistent cp.async kernel with `stages` shared-memory stages
-//         (D3Q19 with FP32 storage only);
-// kind 2: software-pipelined kernel, loads two planes ahead (D3Q19 only);
 // kind 3: low-register kernel that re-pulls a plane for its collision, with
 //         `stages` = CTAs per SM requested from the register allocator;
 // kind 4: register-pipelined kernel with three planes of pulls in registers
@@ -65,17 +86,25 @@ constexpr int kTY = 8;
 //         the halo lines the tiles share are fetched into one die's L2);
 // kind 6: the TMA-fed kernel for 16-bit storage (D3Q19; the rest-offset
 //         modes also stage boxes of the FP32 node densities).
-//         promo: L2 promotion of the tensor copies (0 none, 1 64 B, 2 128 B, 3 256 B).
+// Retired ids (kind kRetired) keep their slot so that the other ids stay
+// stable; every call that names one is rejected.  They were measured slower
+// than the kinds above at every size and removed: 5-7, a persistent kernel
+// copying every pull with cp.async into thread-private stages; 8-10, a
+// software-pipelined kernel holding two planes in registers and shared memory;
+// 26-29, 64x4 / 32x8 TMA tiles with 128-byte or no L2 promotion (no change
+// against the 256-byte promotion every kept tile uses).
+constexpr int kRetired = -1;
+// promo: L2 promotion of the tensor copies (3: 256 bytes fetched per L2 miss).
 struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3; };
 constexpr int kNumTiles = 42;
 constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
-    {32, 8, 1, 3},       {32, 8, 1, 4},       {64, 4, 1, 3},       {32, 8, 2, 0},       {64, 4, 2, 0},
-    {32, 4, 2, 0},       {32, 4, 3, 6},       {32, 8, 3, 3},       {64, 4, 3, 3},       {32, 4, 3, 4},
+    {32, 8, kRetired, 0}, {32, 8, kRetired, 0}, {64, 4, kRetired, 0}, {32, 8, kRetired, 0}, {64, 4, kRetired, 0},
+    {32, 4, kRetired, 0}, {32, 4, 3, 6},       {32, 8, 3, 3},       {64, 4, 3, 3},       {32, 4, 3, 4},
     {32, 4, 4, 3},       {32, 8, 4, 1},       {16, 8, 4, 3},       {32, 8, 5, 3},       {64, 4, 5, 3},
     {32, 4, 5, 4},       {32, 4, 5, 2},       {64, 4, 5, 3, 1, 2}, {64, 4, 5, 3, 1, 4}, {64, 4, 5, 3, 2, 2},
-    {32, 8, 5, 3, 2, 2}, {64, 4, 5, 3, 1, 2, 2}, {64, 4, 5, 3, 1, 2, 0}, {32, 8, 5, 3, 1, 1, 2},
-    {32, 8, 5, 3, 1, 1, 0}, {64, 4, 6, 3, 1, 2}, {64, 4, 6, 4, 1, 2}, {32, 8, 6, 3},
+    {32, 8, 5, 3, 2, 2}, {64, 4, kRetired, 0}, {64, 4, kRetired, 0}, {32, 8, kRetired, 0},
+    {32, 8, kRetired, 0}, {64, 4, 6, 3, 1, 2}, {64, 4, 6, 4, 1, 2}, {32, 8, 6, 3},
     {64, 6, 5, 2, 1, 2}, {64, 6, 5, 2},       {64, 6, 6, 3, 1, 2}, {32, 12, 5, 2, 1, 2}, {32, 12, 5, 2},
     {32, 12, 6, 3, 1, 2}, {64, 8, 6, 2, 1, 2}, {48, 8, 5, 2, 1, 2}, {48, 8, 5, 2}};
 
@@ -89,8 +118,6 @@ inline bool tile_supported(int tile, int lattice, int precision, int forcing = k
         return false;
     switch (kTiles[tile].kind) {
         case 0: return true;
-        case 1: return lattice == 1 && precision == 1;
-        case 2: return lattice == 1 && precision <= 3;
         case 3: return true;
         case 4: return lattice == 1 && precision >= 1 && precision <= 3;
         case 5: return lattice == 1 && precision == 1;

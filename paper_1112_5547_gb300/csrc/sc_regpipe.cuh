@@ -20,9 +20,24 @@
 
 #include <type_traits>
 
-#include "sc_async.cuh"
+#include "sc_kernels.cuh"
 
 namespace lbmsc {
+
+// cp.async (Ampere-style asynchronous copies into shared memory) for the halo stage.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+template <int B> __device__ __forceinline__ void cp_async_bytes(void* smem_dst, const void* gmem_src) {
+    static_assert(B == 4 || B == 8 || B == 16, "cp.async copies 4, 8 or 16 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <class S, int TX, int TY> struct RegPipeTile {
     static constexpr int FX = TX + 2, FY = TY + 2;

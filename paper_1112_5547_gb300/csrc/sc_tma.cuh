@@ -70,40 +70,46 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 // plane's copies).
 constexpr int kMbarSpinLimit = 1 << 24;
 
-// Geometry of one CTA's stages for storage type St (FP32, or 16-bit offsets).
-// Population boxes: (TX + 2 PAD) x (TY + 2) values, PAD = 16 bytes of values on
-// each side in x (TMA copies start on 16-byte boundaries).  Rest-offset
-// storage also stages, per source plane z - 1, z, z + 1 and species, a box of
-// (TX + 8) x (TY + 4) FP32 densities rho_s of the storing nodes.
+// Geometry of one CTA's stages for storage type St (FP32, 16-bit offsets, or
+// paired 16-bit rest offsets).  Population boxes: (TX + 2 PAD) x (TY + 2)
+// elements, PAD = 16 bytes of elements on each side in x (TMA copies start on
+// 16-byte boundaries); one box per species and direction (Q2 = 2 Q), or one
+// per direction for the paired rest-offset words (both species in one 32-bit
+// element).  Rest-offset storage also stages, per source plane z - 1, z, z + 1,
+// a box of (TX + 4) x (TY + 4) float2 densities (rho_A, rho_B) of the storing
+// nodes.
 template <int TX, int TY, int S, class St = float> struct TmaTile {
     static constexpr int E = (int)sizeof(St);
     static constexpr int PAD = 16 / E;
     static constexpr int BX = TX + 2 * PAD, BY = TY + 2;
     static constexpr int FX = TX + 2, FY = TY + 2;
     static constexpr int H = 2 * FX + 2 * TY;
-    static constexpr int Q2 = 2 * D3Q19::Q;
     static constexpr bool REST = Codec<St>::kRest;
-    static constexpr int RBX = TX + 8, RBY = TY + 4;
-    static constexpr int NR = REST ? 6 : 0;  // density boxes per plane
+    static constexpr int Q2 = (REST ? 1 : 2) * D3Q19::Q;  // population boxes per plane
+    static constexpr int RBX = TX + 4, RBY = TY + 4;
+    static constexpr int NR = REST ? 3 : 0;  // density boxes per plane
     static constexpr unsigned box_bytes = BX * BY * E;
     static constexpr unsigned box_stride = (box_bytes + 127) / 128 * 128;  // TMA destinations 128-byte aligned
-    static constexpr unsigned rbox_bytes = RBX * RBY * 4;
+    static constexpr unsigned rbox_bytes = RBX * RBY * 8;
     static constexpr unsigned rbox_stride = (rbox_bytes + 127) / 128 * 128;
     static constexpr unsigned stage_bytes = Q2 * box_stride + NR * rbox_stride;
     static constexpr unsigned tx_bytes = Q2 * box_bytes + NR * rbox_bytes;  // bytes landing per plane
     static constexpr size_t ring_bytes = (size_t)4 * 2 * FY * FX * 4;
-    static constexpr size_t smem_bytes = 128 + (size_t)S * stage_bytes + ring_bytes + (size_t)S * 8;
-    static_assert((BX * E) % 16 == 0 && (RBX * 4) % 16 == 0, "TMA box rows are whole 16-byte units");
+    // S stage barriers and one barrier nothing arrives on (the wait-probe test hook)
+    static constexpr size_t smem_bytes = 128 + (size_t)S * stage_bytes + ring_bytes + (size_t)(S + 1) * 8;
+    static_assert((BX * E) % 16 == 0 && (RBX * 8) % 16 == 0, "TMA box rows are whole 16-byte units");
 };
 
-// The tensor maps of one population buffer: the 2Q population planes and, for
-// rest-offset storage, the two FP32 density planes.
+// The tensor maps of one population buffer: the population planes and, for
+// rest-offset storage, its float2 density plane.
 struct TmaMaps {
     CUtensorMap pop;
     CUtensorMap rho;
 };
 
-// Shared memory of one CTA: S stages of boxes, the density ring, S mbarriers.
+// Shared memory of one CTA: S stages of boxes, the density ring, S mbarriers
+// and one mbarrier that nothing ever arrives on (bars[S]: the wait-probe test
+// hook waits on it, so that a bounded wait runs out without any fault).
 template <int TX, int TY, int S, class St = float> struct TmaSmem {
     using T = TmaTile<TX, TY, S, St>;
     unsigned char* stage;
@@ -119,7 +125,7 @@ template <int TX, int TY, int S, class St = float> struct TmaSmem {
     __device__ __forceinline__ void init_barriers() {
         if (threadIdx.x + threadIdx.y * blockDim.x == 0) {
 #pragma unroll
-            for (int k = 0; k < S; ++k) mbar_init(&bars[k], 1);
+            for (int k = 0; k <= S; ++k) mbar_init(&bars[k], 1);
             mbar_fence_init();
         }
         __syncthreads();
@@ -128,8 +134,8 @@ template <int TX, int TY, int S, class St = float> struct TmaSmem {
 
 // The copies of plane q of a work item (tile x0, y0; planes z0 - 1 .. z1 of
 // its chunk) into the stage of pipeline slot g: 38 population boxes, one per
-// species and direction (and the 6 density boxes of rest-offset storage),
-// completing on the slot's mbarrier.  Elected thread only.
+// species and direction (19 paired boxes and 3 density boxes for rest-offset
+// storage), completing on the slot's mbarrier.  Elected thread only.
 template <int TX, int TY, int S, class St>
 __device__ __forceinline__ void tma_issue_plane(const CUtensorMap* pmap, const CUtensorMap* rmap, int x0, int y0, int z0,
                                                 int gxo, int gyo, int nz, int q, unsigned g,
@@ -147,21 +153,21 @@ __device__ __forceinline__ void tma_issue_plane(const CUtensorMap* pmap, const C
         zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
         const int cy = y0 + gyo - 1 - L::c(i, 1);
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < T::Q2 / L::Q; ++s) {
             const int j = s * L::Q + i;
             tma_load_4d(sb + (size_t)j * T::box_stride, pmap, &sm.bars[st], x0 + gxo - T::PAD, cy, zs, j);
         }
     }
     if constexpr (T::REST) {
+        // float2 densities of nodes x0 - 2 .. x0 + TX + 1, y0 - 2 .. y0 + TY + 1
+        // (the map counts floats in x: 2 per node)
         unsigned char* rb = sb + (size_t)T::Q2 * T::box_stride;
 #pragma unroll
         for (int dz = -1; dz <= 1; ++dz) {
             int zs = z + dz;
             zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-                tma_load_4d(rb + (size_t)((dz + 1) * 2 + s) * T::rbox_stride, rmap, &sm.bars[st], x0 + gxo - 4,
-                            y0 + gyo - 2, zs, s);
+            tma_load_4d(rb + (size_t)(dz + 1) * T::rbox_stride, rmap, &sm.bars[st], 2 * (x0 + gxo - 2), y0 + gyo - 2,
+                        zs, 0);
         }
     }
 }
@@ -178,14 +184,23 @@ __device__ __forceinline__ float tma_pulled(const unsigned char* sb, int s, int 
     const St v = box[fy * T::BX + fx + T::PAD - 1 - L::c(i, 0)];
     if constexpr (std::is_same<St, float>::value) {
         return v;
-    } else if constexpr (T::REST) {
-        const float* rb = reinterpret_cast<const float*>(sb + (size_t)T::Q2 * T::box_stride +
-                                                         (size_t)((1 - L::c(i, 2)) * 2 + s) * T::rbox_stride);
-        const float rho = rb[(fy + 1 - L::c(i, 1)) * T::RBX + fx + 3 - L::c(i, 0)];
-        return Codec<St>::decode(v, __fmul_rn((float)L::w(i), rho));
     } else {
         return Codec<St>::decode(v, __fmul_rn((float)L::w(i), ref_s));
     }
+}
+
+// The pulled pair (f_iA, f_iB) of frame node (fx, fy) for direction i from a
+// landed stage of paired rest-offset storage, decoded with the density pair
+// of the source node x - c_i (the same operations as pull_node).
+template <int TX, int TY, int S, class St>
+__device__ __forceinline__ void tma_pulled_pair(const unsigned char* sb, int i, int fx, int fy, float& fA, float& fB) {
+    using L = D3Q19;
+    using T = TmaTile<TX, TY, S, St>;
+    const uint32_t* box = reinterpret_cast<const uint32_t*>(sb + (size_t)i * T::box_stride);
+    const uint32_t v = box[fy * T::BX + fx + T::PAD - 1 - L::c(i, 0)];
+    const float2* rb =
+        reinterpret_cast<const float2*>(sb + (size_t)T::Q2 * T::box_stride + (size_t)(1 - L::c(i, 2)) * T::rbox_stride);
+    rest_decode<St>(v, (float)L::w(i), rb[(fy + 1 - L::c(i, 1)) * T::RBX + fx + 1 - L::c(i, 0)], fA, fB);
 }
 
 // The item a CTA runs after the current one (batch kernels): the elected
@@ -241,7 +256,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     // ahead; 9.80 against 10.24 ms for the rest-offset mode), with the halo
     // ring pulled by the last H threads so that warp 0, whose first thread
     // issues the copies, carries no second pull.
-    constexpr bool kEarly = sizeof(St) == 2;
+    constexpr bool kEarly = Codec<St>::kOffset;
     const int hid = kEarly ? tid - (TX * TY - H) : tid;  // halo cell index in [0, H) for halo threads
     const bool halo = hid >= 0 && hid < H;
     int hfx, hfy;
@@ -276,22 +291,26 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
 
     bool lost = false;
     // own pulls of plane q into X; own and halo densities into ring slot q % 4
-    auto take_plane = [&](int q, C (&X)[2][Q]) {
-        const unsigned char* sb = sm.stage + (size_t)((qbase + q) % S) * T::stage_bytes;
+    auto pull_frame = [&](const unsigned char* sb, int fx, int fy, C (&X)[2][Q]) {
+        if constexpr (T::REST) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-                X[s][i] = tma_pulled<TX, TY, S, St>(sb, s, i, tx + 1, ty + 1, s == 0 ? a.ref_A : a.ref_B);
-        ring[q & 3][0][ty + 1][tx + 1] = node_density<L, C>(X[0]);
-        ring[q & 3][1][ty + 1][tx + 1] = node_density<L, C>(X[1]);
-        if (halo) {
-            C h[2][Q];
+            for (int i = 0; i < Q; ++i) tma_pulled_pair<TX, TY, S, St>(sb, i, fx, fy, X[0][i], X[1][i]);
+        } else {
 #pragma unroll
             for (int i = 0; i < Q; ++i)
 #pragma unroll
                 for (int s = 0; s < 2; ++s)
-                    h[s][i] = tma_pulled<TX, TY, S, St>(sb, s, i, hfx, hfy, s == 0 ? a.ref_A : a.ref_B);
+                    X[s][i] = tma_pulled<TX, TY, S, St>(sb, s, i, fx, fy, s == 0 ? a.ref_A : a.ref_B);
+        }
+    };
+    auto take_plane = [&](int q, C (&X)[2][Q]) {
+        const unsigned char* sb = sm.stage + (size_t)((qbase + q) % S) * T::stage_bytes;
+        pull_frame(sb, tx + 1, ty + 1, X);
+        ring[q & 3][0][ty + 1][tx + 1] = node_density<L, C>(X[0]);
+        ring[q & 3][1][ty + 1][tx + 1] = node_density<L, C>(X[1]);
+        if (halo) {
+            C h[2][Q];
+            pull_frame(sb, hfx, hfy, h);
             ring[q & 3][0][hfy][hfx] = node_density<L, C>(h[0]);
             ring[q & 3][1][hfy][hfx] = node_density<L, C>(h[1]);
         }
@@ -335,15 +354,30 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
                                                r - nplanes, qbase + r, sm);
             }
         }
+        if (q == 0 && a.wait_probe > 0 && issuer && x0 == 0 && y0 == 0 && z0 == 0) {
+            // failure-detection test hook: the first CTA of the lattice waits,
+            // a.wait_probe tries long, on the barrier nothing arrives on, so
+            // that the bounded wait expires and the error path below runs
+            int n = 0;
+            while (!mbar_try_wait(&bars[S], 0u))
+                if (++n >= a.wait_probe) {
+                    lost = true;
+                    break;
+                }
+        }
         if (!try_plane(q)) lost = true;
         take_plane(q, Xc);
         if (__syncthreads_or(lost)) {
             if (tid == 0) {
-                atomicExch(err, 1);
                 // drain: wait (bounded) for the planes issued from q on (the
-                // next item's first planes included)
+                // next item's first planes included).  Bit 0 of the error word:
+                // a wait expired; bit 1: copies into this CTA's shared memory
+                // were still outstanding after the drain's own bound, so the
+                // device state is suspect.
                 const int last = nxt && nxt->nplanes > 0 ? nplanes + min(kAhead, nxt->nplanes) : nplanes;
-                for (int r = q; r < last && r < q + S; ++r) try_plane(r);
+                bool drained = true;
+                for (int r = q; r < last && r < q + S; ++r) drained = try_plane(r) && drained;
+                atomicOr(err, drained ? 1 : 3);
             }
             return -1;
         }

@@ -52,7 +52,7 @@ EXPORTS = (
     "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
     "lbm_sc_destroy", "lbm_sc_status_string", "lbm_sc_set_tuning", "lbm_sc_get_tuning",
     "lbm_sc_diagnostics_noalloc", "lbm_sc_batch_workspace_bytes", "lbm_sc_batch_create", "lbm_sc_batch_step",
-    "lbm_sc_batch_destroy",
+    "lbm_sc_batch_destroy", "lbm_sc_set_wait_probe", "lbm_sc_error_word",
 )
 
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
@@ -78,38 +78,43 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
             and p.model == LBM_MODEL_SC and p.nx >= tx and p.ny >= ty)
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
-# the shared-memory stages of the persistent cp.async kernel (0: register kernel).
-# kind 0: register-pipelined kernel; 1: persistent cp.async kernel; 2: software-pipelined kernel;
+# their shared-memory stages or CTAs per SM.
+# kind 0: register-pipelined kernel;
 # 3: low-register re-pull kernel (stages = CTAs per SM asked of the register allocator).
 # 4: register-pipelined kernel, three planes of pulls in registers (D3Q19, 32- and 16-bit storage).
 # 5: TMA-fed kernel (D3Q19, FP32 storage, lattices at least one tile wide), stages = smem stages.
 # 6: the TMA-fed kernel for 16-bit storage (reference- or rest-offset; D3Q19, same size rule).
+# RETIRED (-1): ids 5-10 and 26-29 keep their slot so the other ids stay stable; the library
+# rejects them (kernels measured slower at every size and removed).
 TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4), (32, 8), (64, 4), (32, 4),
          (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
          (64, 4), (64, 4), (64, 4), (32, 8), (64, 4), (64, 4),
          (32, 8), (32, 8), (64, 4), (64, 4), (32, 8), (64, 6), (64, 6), (64, 6), (32, 12), (32, 12), (32, 12),
          (64, 8), (48, 8), (48, 8))
-TILE_KIND = (0, 0, 0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 5, 6, 6, 6, 5, 5, 6, 5, 5, 6, 6, 5, 5)
-TILE_STAGES = (0, 0, 0, 0, 0, 3, 4, 3, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 4, 3, 2, 2, 3, 2, 2, 3, 2, 2, 2)
+RETIRED = -1
+TILE_KIND = (0, 0, 0, 0, 0, -1, -1, -1, -1, -1, -1, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, 6, 6, 6,
+             5, 5, 6, 5, 5, 6, 6, 5, 5)
+TILE_STAGES = (0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 0, 0, 0, 0, 3, 4, 3, 2, 2, 3, 2,
+               2, 3, 2, 2, 2)
 # thread-block cluster of the TMA tiles (tiles in x, tiles in y)
 TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1), (1, 2), (1, 2),
                                    (1, 1), (1, 2), (1, 1), (1, 2), (1, 2), (1, 1), (1, 2), (1, 2), (1, 2), (1, 1))
-# L2 promotion (bytes fetched per L2 miss) of the TMA tiles' tensor copies
-TILE_L2_PROMOTION = (256,) * 26 + (128, 0, 128, 0) + (256,) * 12
 
 
 def tile_supported(tile: int, lattice: int, precision: int, forcing: int = 0, model: int = 0) -> bool:
-    """Mirror of the library's rule: kinds 1 and 5 need D3Q19 with FP32 storage, kind 2 D3Q19 without
-    rest-offset storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage; Guo forcing
-    and the FE model run on kinds 0 and 3 and on tile 34."""
+    """Mirror of the library's rule: kind 5 needs D3Q19 with FP32 storage, kind 6 D3Q19 with 16-bit
+    storage, kind 4 D3Q19 with 32-bit or reference-offset 16-bit storage; Guo forcing and the FE
+    model run on kinds 0 and 3 and on tile 34; retired ids are rejected."""
     if not 0 <= tile < len(TILES):
         return False
     kind = TILE_KIND[tile]
+    if kind == RETIRED:
+        return False
     if (forcing == LBM_FORCING_GUO or model == LBM_MODEL_FE) and kind not in (0, 3) and tile != 34:
         return False
     if kind in (0, 3):
         return True
-    if kind in (1, 5):
+    if kind == 5:
         return lattice == LBM_D3Q19 and precision == LBM_F32
     if kind == 6:
         return lattice == LBM_D3Q19 and precision in (LBM_F32_STORE_BF16, LBM_F32_STORE_F16) + REST_PRECISIONS
@@ -184,6 +189,8 @@ def load(path: str = LIB_PATH):
     ip = ctypes.POINTER(ctypes.c_int)
     lib.lbm_sc_layout.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(vp)]
     lib.lbm_sc_set_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
+    lib.lbm_sc_set_wait_probe.argtypes = [vp, ctypes.c_int]
+    lib.lbm_sc_error_word.argtypes = [vp, ip]
     lib.lbm_sc_get_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
     lib.lbm_sc_diagnostics_noalloc.argtypes = [P, vp, ctypes.POINTER(lbm_sc_window), vp, vp]
     lib.lbm_sc_diagnostics_noalloc.restype = ctypes.c_int
@@ -203,7 +210,8 @@ def load(path: str = LIB_PATH):
         getattr(lib, name)
     for name in ("lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step", "lbm_sc_moments",
                  "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout", "lbm_sc_set_tuning",
-                 "lbm_sc_get_tuning", "lbm_sc_batch_create", "lbm_sc_batch_step"):
+                 "lbm_sc_get_tuning", "lbm_sc_batch_create", "lbm_sc_batch_step", "lbm_sc_set_wait_probe",
+                 "lbm_sc_error_word"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -301,6 +309,16 @@ def lbm_sc_layout(h: int):
     return tuple(v.value for v in vals) + (ptr.value,)
 
 
+def lbm_sc_set_wait_probe(h: int, tries: int) -> None:
+    _check(load().lbm_sc_set_wait_probe(ctypes.c_void_p(h), int(tries)), "lbm_sc_set_wait_probe")
+
+
+def lbm_sc_error_word(h: int) -> int:
+    w = ctypes.c_int()
+    _check(load().lbm_sc_error_word(ctypes.c_void_p(h), ctypes.byref(w)), "lbm_sc_error_word")
+    return w.value
+
+
 def lbm_sc_set_tuning(h: int, tile: int, zchunk: int = 0) -> None:
     t = lbm_sc_tuning(int(tile), int(zchunk))
     _check(load().lbm_sc_set_tuning(ctypes.c_void_p(h), ctypes.byref(t)), "lbm_sc_set_tuning")
@@ -363,9 +381,9 @@ def FELattice(lattice: int, shape, tau: float, tau_g: float, g: float, precision
               gamma: float = 1.0, device="cuda", stream=None) -> "Lattice":
     """A lattice of the free-energy model of Sec. 2.2 (lbm_model LBM_MODEL_FE):
     relaxation times tau (f) and tau_g (g), coupling g of the Eq. FEtau functional,
-    gradient coefficient kappa (default g cs2^2 / 4, as in Eq. FEtau) and Gamma."""
+    gradient coefficient kappa (None: the library's default, g cs2^2 / 4 as in Eq. FEtau) and Gamma."""
     if kappa is None:
-        kappa = g / 36.0
+        kappa = -1.0  # a negative kappa selects the library's Eq. FEtau coefficient
     return Lattice(lattice, shape, tau, tau_g, g, precision, device=device, stream=stream, model=LBM_MODEL_FE,
                    kappa=kappa, gamma=gamma)
 
@@ -469,26 +487,33 @@ class Lattice:
         return out
 
     def state(self):
-        """The whole current population buffer as raw bytes (with the FP32 density
-        planes of the rest-offset precisions): save and restore it to rewind."""
+        """The whole current population buffer as raw bytes (with the float2 density
+        plane of the rest-offset precisions): save and restore it to rewind."""
         eb, q, px, py, gx, gy, ptr = lbm_sc_layout(self.handle)
-        n = 2 * q * self.params.nz * py * px * eb
+        planes = q if self.params.precision in REST_PRECISIONS else 2 * q
+        n = planes * self.params.nz * py * px * eb
         if self.params.precision in REST_PRECISIONS:
-            n += 2 * self.params.nz * py * px * 4
+            n += self.params.nz * py * px * 8
         off = ptr - self.workspace.data_ptr()
         return self.workspace[off: off + n]
 
     def populations(self):
         """The current population buffer as a (2, Q, nz, pitch_y, pitch_x) tensor view
-        (GPU velocity order, ghost-padded; see lbm_sc_layout)."""
+        (GPU velocity order, ghost-padded; see lbm_sc_layout).  The rest-offset
+        precisions pair the species in one word per direction: their view is
+        (Q, nz, pitch_y, pitch_x, 2), the last index the species."""
         t = self.torch
         eb, q, px, py, gx, gy, ptr = lbm_sc_layout(self.handle)
+        rest = self.params.precision in REST_PRECISIONS
+        nz = self.params.nz
+        off = ptr - self.workspace.data_ptr()
+        if rest:
+            dt = t.bfloat16 if self.params.precision == LBM_F32_STORE_BF16_REST else t.float16
+            n = q * nz * py * px * 2
+            return self.workspace[off: off + n * 2].view(dt).view(q, nz, py, px, 2)
         dt = {8: t.float64, 4: t.float32}.get(eb)
         if dt is None:
-            dt = t.bfloat16 if self.params.precision in (LBM_F32_STORE_BF16, LBM_F32_STORE_BF16_REST) else t.float16
-        nz = self.params.nz
-        base = self.workspace.data_ptr()
-        off = ptr - base
+            dt = t.bfloat16 if self.params.precision == LBM_F32_STORE_BF16 else t.float16
         n = 2 * q * nz * py * px
         return self.workspace[off: off + n * eb].view(dt).view(2, q, nz, py, px)
 

@@ -52,13 +52,14 @@ def _decoded_window(sc, lat, centre, radius):
     import torch
     eb, q, px, py, gx, gy, _ = sc.lbm_sc_layout(lat.handle)
     nz, ny, nx = lat.shape
-    pops = lat.populations()  # (2, Q, nz, py, px), stored type
     prec = lat.params.precision
     rest = prec in sc.REST_PRECISIONS
+    pops = lat.populations()  # (2, Q, nz, py, px), stored type; rest-offset: (Q, nz, py, px, 2) pairs
     if rest:
+        pops = pops.permute(4, 0, 1, 2, 3)
         st = lat.state()
-        npl = 2 * q * nz * py * px * eb
-        rho = st[npl:].view(torch.float32).view(2, nz, py, px)
+        npl = q * nz * py * px * eb
+        rho = st[npl:].view(torch.float32).view(nz, py, px, 2).permute(3, 0, 1, 2)
     r = np.arange(-radius - 1, radius + 2)
     cz, cy, cx = centre
     zi = torch.tensor((cz + r) % nz, device=pops.device)
@@ -117,7 +118,9 @@ def _check_sampled(sc, oracle_mod, lat, pts, tol_rho, tol_u, steps_before=4, rho
         f = _decoded_window(sc, lat, pt, 3)
         body = (lat.params.body_A, pt[1] - 3, lat.params.ny)
         forcing = "guo" if lat.params.forcing == sc.LBM_FORCING_GUO else "shift"
-        fe = (lat.params.kappa, lat.params.gamma) if lat.params.model == sc.LBM_MODEL_FE else None
+        # a negative kappa asks the library for the Eq. FEtau coefficient, as None asks the oracle
+        kappa = lat.params.kappa if lat.params.kappa >= 0 else None
+        fe = (kappa, lat.params.gamma) if lat.params.model == sc.LBM_MODEL_FE else None
         ref.append(_oracle_window_step(oracle_mod, f, tau_A, tau_B, G, body, forcing, fe))
     lat.step(1)
     rA, rB, u, _ = lat.moments()
