@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 return srho[slot][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
             };
             node_update<L, C>(a, gy, nbr, f, rA, rB);
-            if (owner) store_node<L, S>(a, gx, gy, z, f);
+            if (owner) store_node<L, S>(a, gx, gy, z, f, rA, rB);
         };
 
         C cur[2][Q];

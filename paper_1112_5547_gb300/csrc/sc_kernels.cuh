@@ -57,21 +57,17 @@ __device__ __forceinline__ void pull_node(const LatticeArgs<S>& a, int x, int y,
     }
 }
 
+// Store the values of one cell.  base: the offset bases of the rest-offset
+// storage (the node's densities rho_A, rho_B; any value works as long as the
+// stored one is used, and a node's own density keeps the offsets small);
+// ignored by the other storage types.
 template <class L, class S>
 __device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
-                                           const typename Codec<S>::C (&f)[2][L::Q]) {
+                                           const typename Codec<S>::C (&f)[2][L::Q], float2 base) {
     using C = typename Codec<S>::C;
     if constexpr (Codec<S>::kRest) {
-        // the cell's own densities (sums of what it stores, in a fixed order) are
-        // the offset bases, kept in FP32 for the nodes that pull from this cell
-        float2 r;
-        r.x = f[0][0];
-        r.y = f[1][0];
-#pragma unroll
-        for (int i = 1; i < L::Q; ++i) {
-            r.x = __fadd_rn(r.x, f[0][i]);
-            r.y = __fadd_rn(r.y, f[1][i]);
-        }
+        // the bases, kept in FP32 for the nodes that pull from this cell
+        const float2 r = base;
         __stcs(rest_rho<L>(a.fout, a.Np) + c, r);
 #pragma unroll
         for (int i = 0; i < L::Q; ++i)
@@ -92,10 +88,15 @@ __device__ __forceinline__ void store_cell(const LatticeArgs<S>& a, size_t c,
 // of its periodic images in the ghost columns x in {-2, -1, nx, nx + 1} and
 // rows y in {-2, -1, ny, ny + 1}.  Two ghost layers let a node of the halo
 // ring itself (x = -1 .. nx) pull without wrapping.
+// rA, rB: the node's densities (pre-collision, equal to the post-collision
+// sums in exact arithmetic), the offset bases of rest-offset storage.
 template <class L, class S>
 __device__ __forceinline__ void store_node(const LatticeArgs<S>& a, int x, int y, int z,
-                                           const typename Codec<S>::C (&f)[2][L::Q]) {
-    store_cell<L, S>(a, cell(a, x, y, z), f);
+                                           const typename Codec<S>::C (&f)[2][L::Q], typename Codec<S>::C rA,
+                                           typename Codec<S>::C rB) {
+    float2 base = make_float2(0.f, 0.f);
+    if constexpr (Codec<S>::kRest) base = make_float2(rA, rB);
+    store_cell<L, S>(a, cell(a, x, y, z), f, base);
     const int nx = a.nx, ny = a.ny;
     if (x < 2 || x >= nx - 2 || y < 2 || y >= ny - 2) {
 #pragma unroll 1
@@ -106,7 +107,7 @@ __device__ __forceinline__ void store_node(const LatticeArgs<S>& a, int x, int y
             for (int iy = -2; iy <= 2; ++iy) {
                 const int yi = y + iy * ny;
                 if ((ix | iy) == 0 || yi < -2 || yi > ny + 1) continue;
-                store_cell<L, S>(a, cell(a, xi, yi, z), f);
+                store_cell<L, S>(a, cell(a, xi, yi, z), f, base);
             }
         }
     }
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         const size_t node = (size_t)gx + (size_t)nx * ((size_t)gy + (size_t)ny * z);
         if (MODE == kModeStep) {
             node_update<L, C>(a, gy, nbr, f, r0, r1);
-            if (owner) store_node<L, S>(a, gx, gy, z, f);
+            if (owner) store_node<L, S>(a, gx, gy, z, f, r0, r1);
         } else {
             // SC: physical velocity u = (j_A + j_B + (F_A + F_B) / 2) / rho (F dt/2
             // shift, Sec. 2.3).  FE (Sec. 2.2): u = sum_i f_i c_i / rho, and the
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_reload_kernel(const Latt
             return ring[sl][s][ty + 1 + L::c(i, 1)][tx + 1 + L::c(i, 0)];
         };
         node_update<L, C>(a, gy, nbr, f, rA, rB);
-        if (owner) store_node<L, S>(a, gx, gy, z, f);
+        if (owner) store_node<L, S>(a, gx, gy, z, f, rA, rB);
     };
 
     if (L::D == 2) {
@@ -467,7 +468,16 @@ __global__ void __launch_bounds__(256)
                 }
             }
         }
-        if constexpr (Codec<S>::kRest) store_cell<L, S>(a, n, fr);
+        if constexpr (Codec<S>::kRest) {
+            // rest-offset bases: the sums of the cell's stored values, in a fixed order
+            float2 r = make_float2(fr[0][0], fr[1][0]);
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                r.x = __fadd_rn(r.x, fr[0][i]);
+                r.y = __fadd_rn(r.y, fr[1][i]);
+            }
+            store_cell<L, S>(a, n, fr, r);
+        }
     }
 }
 

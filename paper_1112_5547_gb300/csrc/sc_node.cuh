@@ -43,18 +43,37 @@ template <class L> __host__ __device__ constexpr bool opposite_pairs() {
     return L::Q % 2 == 1;
 }
 
+// Signed sums of terms in a fixed order.  The first term is taken as it is
+// (or negated) rather than added to zero: 0 + x = x for every x but -0, so
+// the values are those of the plain running sum, without its first add.
+template <class C> struct SignedSum {
+    C v;
+    bool empty = true;
+    __device__ __forceinline__ void add(C x) {
+        v = empty ? x : Ar<C>::add(v, x);
+        empty = false;
+    }
+    __device__ __forceinline__ void sub(C x) {
+        v = empty ? -x : Ar<C>::sub(v, x);
+        empty = false;
+    }
+    __device__ __forceinline__ C get() const { return empty ? (C)0 : v; }
+};
+
 template <class L, class C> __device__ __forceinline__ void node_momentum(const C (&f)[L::Q], C (&j)[3]) {
     static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
-    j[0] = j[1] = j[2] = (C)0;
+    SignedSum<C> acc[3];
 #pragma unroll
     for (int i = 1; i < L::Q; i += 2) {
         const C dlt = Ar<C>::sub(f[i], f[i + 1]);
 #pragma unroll
         for (int d = 0; d < L::D; ++d) {
-            if (L::c(i, d) == 1) j[d] = Ar<C>::add(j[d], dlt);
-            if (L::c(i, d) == -1) j[d] = Ar<C>::sub(j[d], dlt);
+            if (L::c(i, d) == 1) acc[d].add(dlt);
+            if (L::c(i, d) == -1) acc[d].sub(dlt);
         }
     }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) j[d] = acc[d].get();
 }
 
 // g_s = -G sum_i w_i rho_s'(x + c_i) c_i for both species; nbr(s, i) returns
@@ -119,28 +138,35 @@ __device__ __forceinline__ void node_body_force(C A, int y, int ny, C (&gA)[3], 
     node_add_body<C>(A, kolmogorov_accel<C>(A, y, ny), gA, gB);
 }
 
-// BGK relaxation of one species towards f^eq(rho, u).
+// c_i . u as a signed sum of u's components (in the order of d).
+template <class L, class C> __device__ __forceinline__ C node_cu(int i, const C (&u)[3]) {
+    SignedSum<C> cu;
+#pragma unroll
+    for (int d = 0; d < L::D; ++d) {
+        if (L::c(i, d) == 1) cu.add(u[d]);
+        if (L::c(i, d) == -1) cu.sub(u[d]);
+    }
+    return cu.get();
+}
+
+// BGK relaxation of one species towards f^eq(rho, u), each moving population
+// relaxed as soon as its equilibrium is formed (fewer live values), the rest
+// population last from the closure f^eq_0 = rho - sum_{i>0} f^eq_i.
 template <class L, class C> __device__ __forceinline__ void node_relax(C (&f)[L::Q], C rho, const C (&u)[3], C omega) {
     using A = Ar<C>;
     C uu = L::D == 3 ? A::fma(u[0], u[0], A::fma(u[1], u[1], A::mul(u[2], u[2]))) : A::fma(u[0], u[0], A::mul(u[1], u[1]));
     const C base = A::fma((C)-1.5, uu, (C)1);
-    C feq[L::Q];
-    C moved = (C)0;
+    SignedSum<C> moved;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        C cu = (C)0;
-#pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            if (L::c(i, d) == 1) cu = A::add(cu, u[d]);
-            if (L::c(i, d) == -1) cu = A::sub(cu, u[d]);
-        }
+        const C cu = node_cu<L, C>(i, u);
         const C wr = A::mul((C)L::w(i), rho);
-        feq[i] = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
-        moved = A::add(moved, feq[i]);
+        const C feq = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
+        moved.add(feq);
+        f[i] = A::fma(omega, A::sub(feq, f[i]), f[i]);
     }
-    feq[0] = A::sub(rho, moved);
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i] = A::fma(omega, A::sub(feq[i], f[i]), f[i]);
+    const C feq0 = A::sub(rho, moved.get());
+    f[0] = A::fma(omega, A::sub(feq0, f[0]), f[0]);
 }
 
 // Collision of both species of one node: common velocity shifted by tau_s g_s.
@@ -178,32 +204,21 @@ __device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)
     C uF = L::D == 3 ? A::fma(u[0], F[0], A::fma(u[1], F[1], A::mul(u[2], F[2]))) : A::fma(u[0], F[0], A::mul(u[1], F[1]));
     const C base = A::fma((C)-1.5, uu, (C)1);
     const C keep = A::fma((C)-0.5, omega, (C)1);  // 1 - 1 / (2 tau)
-    C feq[L::Q], src[L::Q];
-    C moved = (C)0, sources = (C)0;
+    SignedSum<C> moved, sources;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        C cu = (C)0, cF = (C)0;
-#pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            if (L::c(i, d) == 1) {
-                cu = A::add(cu, u[d]);
-                cF = A::add(cF, F[d]);
-            }
-            if (L::c(i, d) == -1) {
-                cu = A::sub(cu, u[d]);
-                cF = A::sub(cF, F[d]);
-            }
-        }
+        const C cu = node_cu<L, C>(i, u);
+        const C cF = node_cu<L, C>(i, F);
         const C wr = A::mul((C)L::w(i), rho);
-        feq[i] = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
-        moved = A::add(moved, feq[i]);
-        src[i] = A::mul((C)L::w(i), A::fma(A::mul((C)9, cu), cF, A::mul((C)3, A::sub(cF, uF))));
-        sources = A::add(sources, src[i]);
+        const C feq = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
+        moved.add(feq);
+        const C src = A::mul((C)L::w(i), A::fma(A::mul((C)9, cu), cF, A::mul((C)3, A::sub(cF, uF))));
+        sources.add(src);
+        f[i] = A::fma(keep, src, A::fma(omega, A::sub(feq, f[i]), f[i]));
     }
-    feq[0] = A::sub(rho, moved);
-    src[0] = -sources;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) f[i] = A::fma(keep, src[i], A::fma(omega, A::sub(feq[i], f[i]), f[i]));
+    const C feq0 = A::sub(rho, moved.get());
+    const C src0 = -sources.get();
+    f[0] = A::fma(keep, src0, A::fma(omega, A::sub(feq0, f[0]), f[0]));
 }
 
 template <class L, class C>
@@ -295,22 +310,11 @@ __device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, c
                        A::mul(cs2, rho));
     const C sg = A::sub(A::mul(gamma, mu), A::mul(cs2, phi));
     const C ku = A::mul(cs2, uu), kg = A::mul(cs2, gg);
-    C feq[L::Q], geq[L::Q];
-    C fsum = (C)0, gsum = (C)0;
+    SignedSum<C> fsum, gsum;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        C cu = (C)0, cg = (C)0;
-#pragma unroll
-        for (int d = 0; d < L::D; ++d) {
-            if (L::c(i, d) == 1) {
-                cu = A::add(cu, u[d]);
-                cg = A::add(cg, gp[d]);
-            }
-            if (L::c(i, d) == -1) {
-                cu = A::sub(cu, u[d]);
-                cg = A::sub(cg, gp[d]);
-            }
-        }
+        const C cu = node_cu<L, C>(i, u);
+        const C cg = node_cu<L, C>(i, gp);
         int c2 = 0;
 #pragma unroll
         for (int d = 0; d < L::D; ++d) c2 += L::c(i, d) * L::c(i, d);
@@ -319,19 +323,18 @@ __device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, c
         const C quad_g = A::sub(A::mul(cg, cg), kg);
         const C w = (C)L::w(i);
         const C hf = A::fma(s, iso, A::fma(kappa, quad_g, A::mul(rho, quad_u)));
-        feq[i] = A::mul(w, A::fma((C)4.5, hf, A::fma(A::mul((C)3, rho), cu, rho)));
+        const C feq = A::mul(w, A::fma((C)4.5, hf, A::fma(A::mul((C)3, rho), cu, rho)));
         const C hg = A::fma(sg, iso, A::mul(phi, quad_u));
-        geq[i] = A::mul(w, A::fma((C)4.5, hg, A::fma(A::mul((C)3, phi), cu, phi)));
-        fsum = A::add(fsum, feq[i]);
-        gsum = A::add(gsum, geq[i]);
+        const C geq = A::mul(w, A::fma((C)4.5, hg, A::fma(A::mul((C)3, phi), cu, phi)));
+        fsum.add(feq);
+        gsum.add(geq);
+        f[0][i] = A::fma(omega, A::sub(feq, f[0][i]), f[0][i]);
+        f[1][i] = A::fma(omega_g, A::sub(geq, f[1][i]), f[1][i]);
     }
-    feq[0] = A::sub(rho, fsum);
-    geq[0] = A::sub(phi, gsum);
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        f[0][i] = A::fma(omega, A::sub(feq[i], f[0][i]), f[0][i]);
-        f[1][i] = A::fma(omega_g, A::sub(geq[i], f[1][i]), f[1][i]);
-    }
+    const C feq0 = A::sub(rho, fsum.get());
+    const C geq0 = A::sub(phi, gsum.get());
+    f[0][0] = A::fma(omega, A::sub(feq0, f[0][0]), f[0][0]);
+    f[1][0] = A::fma(omega_g, A::sub(geq0, f[1][0]), f[1][0]);
 }
 
 // The collision of the lattice's forcing scheme, chosen at run time (kernels

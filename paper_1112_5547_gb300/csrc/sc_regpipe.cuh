@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TX* TY, MINB) sc_step_regpipe_kernel(const Lat
         node_force<L, C>(nbr, a.G, gA, gB);
         node_body_force<C>(a.body_A, gy, a.ny, gA, gB);
         node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
-        if (owner) store_node<L, S>(a, gx, gy, zof(q), X);
+        if (owner) store_node<L, S>(a, gx, gy, zof(q), X, rA, rB);
     };
     // one plane of the steady state; false once the chunk is done
     auto body = [&](int q, C (&Xq)[2][Q], C (&Xq1)[2][Q], C (&Xq2)[2][Q]) -> bool {

@@ -336,7 +336,7 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
             else
                 node_collide<L, C>(X, rA, rB, gA, gB, a.omega_A, a.omega_B, a.tau_A, a.tau_B);
         }
-        if (owner) store_node<L, St>(a, gx, gy, zof(q), X);
+        if (owner) store_node<L, St>(a, gx, gy, zof(q), X, rA, rB);
     };
     // plane q arrives; plane q - 1 collides.  0: go on; 1: chunk done; -1: a wait was lost.
     auto body = [&](int q, C (&Xc)[2][Q], C (&Xp)[2][Q]) -> int {
