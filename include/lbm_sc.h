@@ -188,7 +188,10 @@ typedef struct lbm_sc_handle lbm_sc_handle;
  * 2 stages in 1x2 clusters, 37 = the same without clusters (FP32), 38 = 32x12
  * with 3 stages in 1x2 clusters (16-bit), 39 = 64x8 with 2 stages in 1x2
  * clusters (16-bit, 512 threads), 40 = 48x8 with 2 stages in 1x2 clusters,
- * 41 = the same without clusters (FP32).  With LBM_FORCING_GUO or
+ * 41 = the same without clusters (FP32); 42 = 64x4 with 2 stages in 1x2
+ * clusters, 43 = 32x8 with 2 stages in 1x2 clusters, 44 = 64x4 with 2 stages
+ * without clusters (16-bit, two CTAs per SM: one CTA's per-plane barrier
+ * overlaps the other's work).  With LBM_FORCING_GUO or
  * LBM_MODEL_FE the accepted tiles are those of the register and low-register
  * kernels (0-4, 11-14) and the TMA tile 34.  zchunk is the number
  * of z planes each CTA marches over per work item (D3Q19 only; 0 = automatic).

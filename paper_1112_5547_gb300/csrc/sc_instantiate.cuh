@@ -29,10 +29,10 @@ cudaError_t step_reload(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <class L, class S, int TX, int TY, int ST, int FORCING = kForcingShift> struct TmaLaunch {
+template <class L, class S, int TX, int TY, int ST, int FORCING = kForcingShift, int MINB = 1> struct TmaLaunch {
     static cudaError_t run(const Plan&, const LatticeArgs<S>&, cudaStream_t) { return cudaErrorInvalidValue; }
 };
-template <class S, int TX, int TY, int ST, int FORCING> struct TmaLaunch<D3Q19, S, TX, TY, ST, FORCING> {
+template <class S, int TX, int TY, int ST, int FORCING, int MINB> struct TmaLaunch<D3Q19, S, TX, TY, ST, FORCING, MINB> {
     static cudaError_t run(const Plan& p, const LatticeArgs<S>& a, cudaStream_t st) {
         if constexpr (sizeof(S) == 8) {
             return cudaErrorInvalidValue;
@@ -47,7 +47,7 @@ template <class S, int TX, int TY, int ST, int FORCING> struct TmaLaunch<D3Q19, 
                 if (e == cudaSuccess)
                     e = encode_rho_map(p, rest_rho<D3Q19>(a.fin, p.Np), T::RBX, T::RBY, &maps.rho, ts.promo);
             if (e != cudaSuccess) return e;
-            auto kern = sc_step_tma_kernel<TX, TY, ST, S, FORCING>;
+            auto kern = sc_step_tma_kernel<TX, TY, ST, S, FORCING, MINB>;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
             if (e != cudaSuccess) return e;
             if (ts.cx == 1 && ts.cy == 1) {
@@ -100,7 +100,8 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
                       kTiles[29].kind == kRetired && kTiles[30].kind == 6 &&
                       kTiles[31].stages == 4 && kTiles[32].tx == 32 && kTiles[33].ty == 6 && kTiles[34].stages == 2 &&
                       kTiles[35].kind == 6 && kTiles[36].ty == 12 && kTiles[37].cy == 1 && kTiles[38].kind == 6 &&
-                      kTiles[39].ty == 8 && kTiles[40].tx == 48 && kTiles[41].cy == 1 && kNumTiles == 42,
+                      kTiles[39].ty == 8 && kTiles[40].tx == 48 && kTiles[41].cy == 1 && kTiles[42].minb == 2 &&
+                      kTiles[43].tx == 32 && kTiles[44].cy == 1 && kNumTiles == 45,
                   "tile table and dispatch disagree");
     if constexpr (Codec<S>::kRest) {
         // rest-offset storage: the kernels that pull through pull_node
@@ -120,6 +121,9 @@ template <class L, class S> cudaError_t step_typed(const Plan& p, const void* fi
             case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
             case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
             case 39: return TmaLaunch<L, S, 64, 8, 2>::run(p, a, st);
+            case 42:
+            case 44: return TmaLaunch<L, S, 64, 4, 2, kForcingShift, 2>::run(p, a, st);
+            case 43: return TmaLaunch<L, S, 32, 8, 2, kForcingShift, 2>::run(p, a, st);
         }
         return cudaErrorInvalidValue;
     } else {
@@ -171,6 +175,9 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
             case 35: return TmaLaunch<L, S, 64, 6, 3>::run(p, a, st);
             case 38: return TmaLaunch<L, S, 32, 12, 3>::run(p, a, st);
             case 39: return TmaLaunch<L, S, 64, 8, 2>::run(p, a, st);
+            case 42:
+            case 44: return TmaLaunch<L, S, 64, 4, 2, kForcingShift, 2>::run(p, a, st);
+            case 43: return TmaLaunch<L, S, 32, 8, 2, kForcingShift, 2>::run(p, a, st);
         }
     }
     return cudaErrorInvalidValue;

@@ -94,9 +94,11 @@ constexpr int kTY = 8;
 // 26-29, 64x4 / 32x8 TMA tiles with 128-byte or no L2 promotion (no change
 // against the 256-byte promotion every kept tile uses).
 constexpr int kRetired = -1;
-// promo: L2 promotion of the tensor copies (3: 256 bytes fetched per L2 miss).
-struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3; };
-constexpr int kNumTiles = 42;
+// promo: L2 promotion of the tensor copies (3: 256 bytes fetched per L2 miss);
+// minb: CTAs per SM the register allocation is made for (TMA kinds; two
+// CTAs per SM let one CTA's per-plane barrier overlap the other's work).
+struct TileShape { int tx, ty, kind, stages, cx = 1, cy = 1, promo = 3, minb = 1; };
+constexpr int kNumTiles = 45;
 constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 0, 0},       {32, 16, 0, 0},      {64, 8, 0, 0},       {32, 4, 0, 0},       {64, 4, 0, 0},
     {32, 8, kRetired, 0}, {32, 8, kRetired, 0}, {64, 4, kRetired, 0}, {32, 8, kRetired, 0}, {64, 4, kRetired, 0},
@@ -106,7 +108,8 @@ constexpr TileShape kTiles[kNumTiles] = {
     {32, 8, 5, 3, 2, 2}, {64, 4, kRetired, 0}, {64, 4, kRetired, 0}, {32, 8, kRetired, 0},
     {32, 8, kRetired, 0}, {64, 4, 6, 3, 1, 2}, {64, 4, 6, 4, 1, 2}, {32, 8, 6, 3},
     {64, 6, 5, 2, 1, 2}, {64, 6, 5, 2},       {64, 6, 6, 3, 1, 2}, {32, 12, 5, 2, 1, 2}, {32, 12, 5, 2},
-    {32, 12, 6, 3, 1, 2}, {64, 8, 6, 2, 1, 2}, {48, 8, 5, 2, 1, 2}, {48, 8, 5, 2}};
+    {32, 12, 6, 3, 1, 2}, {64, 8, 6, 2, 1, 2}, {48, 8, 5, 2, 1, 2}, {48, 8, 5, 2},
+    {64, 4, 6, 2, 1, 2, 3, 2}, {32, 8, 6, 2, 1, 2, 3, 2}, {64, 4, 6, 2, 1, 1, 3, 2}};
 
 // forcing = kForcingGuo or model = kModelFE: the kernels that choose the
 // collision at run time (kinds 0 and 3) and the 64x6 TMA tile (34), which has

@@ -203,6 +203,31 @@ __device__ __forceinline__ void tma_pulled_pair(const unsigned char* sb, int i, 
     rest_decode<St>(v, (float)L::w(i), rb[(fy + 1 - L::c(i, 1)) * T::RBX + fx + 1 - L::c(i, 0)], fA, fB);
 }
 
+// Density rho_s of frame node (fx, fy) for one species s (a run-time value:
+// the same instructions read the other species' planes or half-words), with
+// the values decoded and summed exactly as node_density sums a node's pulls.
+template <int TX, int TY, int S, class St>
+__device__ __forceinline__ float tma_density(const unsigned char* sb, int s, int fx, int fy, float ref_s) {
+    using L = D3Q19;
+    using T = TmaTile<TX, TY, S, St>;
+    auto pulled = [&](int i) -> float {
+        if constexpr (T::REST) {
+            const uint32_t* box = reinterpret_cast<const uint32_t*>(sb + (size_t)i * T::box_stride);
+            const uint32_t v = box[fy * T::BX + fx + T::PAD - 1 - L::c(i, 0)];
+            const float2* rb = reinterpret_cast<const float2*>(sb + (size_t)T::Q2 * T::box_stride +
+                                                               (size_t)(1 - L::c(i, 2)) * T::rbox_stride);
+            const float2 r = rb[(fy + 1 - L::c(i, 1)) * T::RBX + fx + 1 - L::c(i, 0)];
+            return __fmaf_rn((float)L::w(i), s == 0 ? r.x : r.y, s == 0 ? Codec<St>::lo(v) : Codec<St>::hi(v));
+        } else {
+            return tma_pulled<TX, TY, S, St>(sb, s, i, fx, fy, ref_s);
+        }
+    };
+    float r = pulled(0);
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) r = __fadd_rn(r, pulled(i));
+    return r;
+}
+
 // The item a CTA runs after the current one (batch kernels): the elected
 // thread issues its first planes into the stages the current item frees,
 // so the pipeline does not drain between items.
@@ -257,10 +282,18 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     // ring pulled by the last H threads so that warp 0, whose first thread
     // issues the copies, carries no second pull.
     constexpr bool kEarly = Codec<St>::kOffset;
-    const int hid = kEarly ? tid - (TX * TY - H) : tid;  // halo cell index in [0, H) for halo threads
-    const bool halo = hid >= 0 && hid < H;
+    // Halo densities: where the CTA has twice as many threads as halo cells,
+    // two threads share a cell, one species each (the same instructions on
+    // another species' planes, no divergence), which halves the extra work the
+    // halo threads bring to the per-plane barrier; otherwise one thread pulls
+    // both species of a cell.
+    constexpr bool kSplit = 2 * H <= TX * TY;
+    constexpr int HT = kSplit ? 2 * H : H;  // halo threads
+    const int hid = kEarly ? tid - (TX * TY - HT) : tid;  // halo thread index in [0, HT) for halo threads
+    const bool halo = hid >= 0 && hid < HT;
+    const int hs = kSplit ? (hid & 1) : 0;  // the species of a shared halo cell
     int hfx, hfy;
-    halo_cell<TX, TY>(halo ? hid : 0, hfx, hfy);
+    halo_cell<TX, TY>(halo ? (kSplit ? hid >> 1 : hid) : 0, hfx, hfy);
 
     auto zof = [&](int q) {
         const int z = z0 - 1 + q;
@@ -309,10 +342,14 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
         ring[q & 3][0][ty + 1][tx + 1] = node_density<L, C>(X[0]);
         ring[q & 3][1][ty + 1][tx + 1] = node_density<L, C>(X[1]);
         if (halo) {
-            C h[2][Q];
-            pull_frame(sb, hfx, hfy, h);
-            ring[q & 3][0][hfy][hfx] = node_density<L, C>(h[0]);
-            ring[q & 3][1][hfy][hfx] = node_density<L, C>(h[1]);
+            if constexpr (kSplit) {
+                ring[q & 3][hs][hfy][hfx] = tma_density<TX, TY, S, St>(sb, hs, hfx, hfy, hs == 0 ? a.ref_A : a.ref_B);
+            } else {
+                C h[2][Q];
+                pull_frame(sb, hfx, hfy, h);
+                ring[q & 3][0][hfy][hfx] = node_density<L, C>(h[0]);
+                ring[q & 3][1][hfy][hfx] = node_density<L, C>(h[1]);
+            }
         }
     };
     auto collide = [&](int q, C (&X)[2][Q]) {
@@ -408,8 +445,8 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
 // FORCING: the collision, fixed at compile time: kForcingShift, kForcingGuo or
 // kSchemeFE (the FE model); the last two are instantiated for the 64x6 FP32
 // tile only.
-template <int TX, int TY, int S, class St = float, int FORCING = kForcingShift>
-__global__ void __launch_bounds__(TX* TY, 1)
+template <int TX, int TY, int S, class St = float, int FORCING = kForcingShift, int MINB = 1>
+__global__ void __launch_bounds__(TX* TY, MINB)
     sc_step_tma_kernel(const __grid_constant__ TmaMaps maps, const LatticeArgs<St> a, int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
     TmaSmem<TX, TY, S, St> sm(smem_raw);

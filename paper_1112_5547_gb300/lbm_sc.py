@@ -90,15 +90,16 @@ TILES = ((32, 8), (32, 16), (64, 8), (32, 4), (64, 4), (32, 8), (32, 8), (64, 4)
          (32, 4), (32, 8), (64, 4), (32, 4), (32, 4), (32, 8), (16, 8), (32, 8), (64, 4), (32, 4), (32, 4),
          (64, 4), (64, 4), (64, 4), (32, 8), (64, 4), (64, 4),
          (32, 8), (32, 8), (64, 4), (64, 4), (32, 8), (64, 6), (64, 6), (64, 6), (32, 12), (32, 12), (32, 12),
-         (64, 8), (48, 8), (48, 8))
+         (64, 8), (48, 8), (48, 8), (64, 4), (32, 8), (64, 4))
 RETIRED = -1
 TILE_KIND = (0, 0, 0, 0, 0, -1, -1, -1, -1, -1, -1, 3, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5, 5, 5, 5, 5, -1, -1, -1, -1, 6, 6, 6,
-             5, 5, 6, 5, 5, 6, 6, 5, 5)
+             5, 5, 6, 5, 5, 6, 6, 5, 5, 6, 6, 6)
 TILE_STAGES = (0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 6, 3, 3, 4, 3, 1, 3, 3, 3, 4, 2, 3, 3, 3, 3, 0, 0, 0, 0, 3, 4, 3, 2, 2, 3, 2,
-               2, 3, 2, 2, 2)
+               2, 3, 2, 2, 2, 2, 2, 2)
 # thread-block cluster of the TMA tiles (tiles in x, tiles in y)
 TILE_CLUSTER = ((1, 1),) * 22 + ((1, 2), (1, 4), (2, 2), (2, 2), (1, 2), (1, 2), (1, 1), (1, 1), (1, 2), (1, 2),
-                                   (1, 1), (1, 2), (1, 1), (1, 2), (1, 2), (1, 1), (1, 2), (1, 2), (1, 2), (1, 1))
+                                   (1, 1), (1, 2), (1, 1), (1, 2), (1, 2), (1, 1), (1, 2), (1, 2), (1, 2), (1, 1),
+                                   (1, 2), (1, 2), (1, 1))
 
 
 def tile_supported(tile: int, lattice: int, precision: int, forcing: int = 0, model: int = 0) -> bool:
