@@ -196,7 +196,9 @@ __device__ __forceinline__ void node_collide(C (&f)[2][L::Q], C rA, C rB, const 
 //   f_is += (1 / tau_s) (f^eq_i(rho_s, u_G) - f_is) + (1 - 1 / (2 tau_s)) S_is
 //   S_is = w_i [3 (c_i - u_G).F_s + 9 (c_i.u_G) (c_i.F_s)]
 // The source's rest component is closed as S_0 = -sum_{i>0} S_i (its sum over
-// i vanishes in exact arithmetic), like f^eq_0.
+// i vanishes in exact arithmetic), like f^eq_0.  Opposite directions share
+// their terms: with t1 = 9 (c.u)(c.F) - 3 u.F and t2 = 3 c.F (c = c_i),
+// S_i = w_i (t1 + t2) and S_{i+1} = w_i (t1 - t2), since c_{i+1} = -c_i.
 template <class L, class C>
 __device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)[3], const C (&F)[3], C omega) {
     using A = Ar<C>;
@@ -204,17 +206,27 @@ __device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)
     C uF = L::D == 3 ? A::fma(u[0], F[0], A::fma(u[1], F[1], A::mul(u[2], F[2]))) : A::fma(u[0], F[0], A::mul(u[1], F[1]));
     const C base = A::fma((C)-1.5, uu, (C)1);
     const C keep = A::fma((C)-0.5, omega, (C)1);  // 1 - 1 / (2 tau)
+    const C m3uF = A::mul((C)-3, uF);
+    static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
     SignedSum<C> moved, sources;
 #pragma unroll
-    for (int i = 1; i < L::Q; ++i) {
-        const C cu = node_cu<L, C>(i, u);
+    for (int i = 1; i < L::Q; i += 2) {
+        const C cu = node_cu<L, C>(i, u);  // c_{i+1}.u = -cu exactly (a signed sum of the same terms)
         const C cF = node_cu<L, C>(i, F);
-        const C wr = A::mul((C)L::w(i), rho);
-        const C feq = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
-        moved.add(feq);
-        const C src = A::mul((C)L::w(i), A::fma(A::mul((C)9, cu), cF, A::mul((C)3, A::sub(cF, uF))));
-        sources.add(src);
-        f[i] = A::fma(keep, src, A::fma(omega, A::sub(feq, f[i]), f[i]));
+        const C w = (C)L::w(i);
+        const C wr = A::mul(w, rho);
+        const C feq_p = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
+        const C feq_m = A::mul(wr, A::fma(-cu, A::fma((C)4.5, -cu, (C)3), base));
+        moved.add(feq_p);
+        moved.add(feq_m);
+        const C t1 = A::fma(A::mul((C)9, cu), cF, m3uF);
+        const C t2 = A::mul((C)3, cF);
+        const C src_p = A::mul(w, A::add(t1, t2));
+        const C src_m = A::mul(w, A::sub(t1, t2));
+        sources.add(src_p);
+        sources.add(src_m);
+        f[i] = A::fma(keep, src_p, A::fma(omega, A::sub(feq_p, f[i]), f[i]));
+        f[i + 1] = A::fma(keep, src_m, A::fma(omega, A::sub(feq_m, f[i + 1]), f[i + 1]));
     }
     const C feq0 = A::sub(rho, moved.get());
     const C src0 = -sources.get();
