@@ -320,7 +320,7 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     out = {"workload": "%d ragged D3Q19 FP32 drop lattices, L in %s, %.1fM nodes, seed %d" % (n, sizes, N / 1e6, seed),
            "nodes": N, "steps": steps, "batched_mlups": N / bat_ms / 1e3, "serial_mlups": N / ser_ms / 1e3,
            "batched_ms_per_step": bat_ms, "serial_ms_per_step": ser_ms, "speedup": ser_ms / bat_ms,
-           "batch_launch": {"tile": list(lbm_sc.BATCH_TILES[tile]), "tma": lbm_sc.BATCH_TILE_TMA[tile],
+           "batch_launch": {"tile_id": tile, "tile": list(lbm_sc.BATCH_TILES[tile]), "tma": lbm_sc.BATCH_TILE_TMA[tile],
                             "zchunk": zc, "graph_steps": gs, "candidates": len(table)},
            "gpu_launches_per_step": {"batched": 1, "serial": n}}
     del lats
@@ -682,9 +682,29 @@ def main():
         if dist is not None:
             e2e_s = max_over_ranks(e2e_s, dist)
         esz = 8 if prec == "f64" else 4
+        # the link's own rate on these buffers (one field each way, CUDA events), for the floor below
+        dfield = torch.empty(N, dtype=tdt, device="cuda")
+        ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        h2d_gbs = d2h_gbs = 0.0
+        for _ in range(3):  # best of three (the first pass maps the fresh device pages)
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+                dfield.copy_(hA, non_blocking=True)
+                ev1.record(stream)
+                oA.copy_(dfield, non_blocking=True)
+                ev2.record(stream)
+            stream.synchronize()
+            h2d_gbs = max(h2d_gbs, N * esz / (ev0.elapsed_time(ev1) / 1e3) / 1e9)
+            d2h_gbs = max(d2h_gbs, N * esz / (ev1.elapsed_time(ev2) / 1e3) / 1e9)
+        del dfield
+        copy_s = 2 * N * esz / h2d_gbs / 1e9 + 6 * N * esz / d2h_gbs / 1e9
         e2e = {"value": job_mlups(world, N, K, e2e_s), "unit": "MLUPS",
                "h2d_bytes_per_step": 2 * N * esz / K, "d2h_bytes_per_step": 6 * N * esz / K,
-               "note": "one job of %d steps: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p; bytes per step = job bytes / steps" % K}
+               "seconds": e2e_s, "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs},
+               "floor_seconds": K * ms_per_step / 1e3 + copy_s,
+               "note": "one job of %d steps through lbm_sc_run_host: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p "
+                       "(copies overlapped with init and moments in z slabs); bytes per step = job bytes / steps; "
+                       "floor = the steps alone + every copy at the measured link rate, unoverlapped" % K}
         del staging, hA, hB, oA, oB, oP, oU, lat2
 
     bt = None

@@ -283,7 +283,14 @@ LBM_SC_API size_t lbm_sc_host_staging_bytes(const lbm_sc_params* params);
  * from host pointers into d_staging, initialises, advances nsteps, computes the
  * moments and copies each non-NULL output back to host pointers (same layouts as
  * lbm_sc_moments).  d_staging: >= lbm_sc_host_staging_bytes, 256-byte aligned.
- * Synchronises the handle's stream before returning. */
+ * The copies run on a second stream in slabs of z planes (up to 8 for
+ * D3Q19 lattices of 64 planes or more), so that the input copies overlap the
+ * initialisation of the slabs already landed and the output copies of one
+ * slab overlap the moments of the next; results are those of init_fields,
+ * step and moments.  The first call on a handle creates that stream and a
+ * few events (no device memory; lbm_sc_destroy releases them); make it
+ * outside any stream capture.  Synchronises the handle's stream before
+ * returning. */
 LBM_SC_API lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_bytes,
                            const void* h_rhoA, const void* h_rhoB, const void* h_u, int nsteps,
                            void* h_rhoA_out, void* h_rhoB_out, void* h_u_out, void* h_p_out);
@@ -381,7 +388,8 @@ LBM_SC_API lbm_status lbm_sc_batch_step(lbm_sc_batch* b, int nsteps);
 /* Release the batch (and its graphs).  The handles and workspace stay the caller's. */
 LBM_SC_API void lbm_sc_batch_destroy(lbm_sc_batch* b);
 
-/* Release the host handle.  The workspace stays the caller's. */
+/* Release the host handle (and the copy stream and events of lbm_sc_run_host,
+ * if it made them).  The workspace stays the caller's. */
 LBM_SC_API void lbm_sc_destroy(lbm_sc_handle* h);
 
 /* Static, human-readable name of a status code. */

@@ -13,6 +13,9 @@
 
 using lbmsc::Plan;
 
+// Slabs of z planes lbm_sc_run_host overlaps its host copies with (at most).
+constexpr int kIoSlabs = 8;
+
 struct lbm_sc_handle {
     lbm_sc_params params;
     Plan plan;
@@ -23,6 +26,10 @@ struct lbm_sc_handle {
     double* partials;     // per-CTA diagnostics partials
     double* result;       // folded diagnostics (kNumDiag doubles)
     cudaStream_t stream;
+    // lbm_sc_run_host's copy stream and events, created on its first call
+    bool io_ready;
+    cudaStream_t io_stream;
+    cudaEvent_t io_start, io_done, io_in[kIoSlabs], io_out[kIoSlabs];
 };
 
 namespace {
@@ -313,36 +320,128 @@ size_t lbm_sc_host_staging_bytes(const lbm_sc_params* p) {
     return field * (size_t)(3 + d_of(p->lattice));
 }
 
+namespace {
+
+// The copy stream and events of lbm_sc_run_host (no device memory), made once per handle.
+cudaError_t io_setup(lbm_sc_handle* h) {
+    if (h->io_ready) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking);
+    cudaEvent_t* evs[2 + 2 * kIoSlabs];
+    int n = 0;
+    evs[n++] = &h->io_start;
+    evs[n++] = &h->io_done;
+    for (int k = 0; k < kIoSlabs; ++k) {
+        evs[n++] = &h->io_in[k];
+        evs[n++] = &h->io_out[k];
+    }
+    for (int k = 0; k < n && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(evs[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) h->io_ready = true;
+    return e;
+}
+
+void io_release(lbm_sc_handle* h) {
+    if (!h->io_ready) return;
+    cudaEventDestroy(h->io_start);
+    cudaEventDestroy(h->io_done);
+    for (int k = 0; k < kIoSlabs; ++k) {
+        cudaEventDestroy(h->io_in[k]);
+        cudaEventDestroy(h->io_out[k]);
+    }
+    cudaStreamDestroy(h->io_stream);
+    h->io_ready = false;
+}
+
+}  // namespace
+
 lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_bytes, const void* h_rhoA,
                            const void* h_rhoB, const void* h_u, int nsteps, void* h_rhoA_out, void* h_rhoB_out,
                            void* h_u_out, void* h_p_out) {
     if (!h || !d_staging || !h_rhoA || !h_rhoB || nsteps < 0) return LBM_ERR_INVALID_ARG;
     if (((uintptr_t)d_staging) % kAlign != 0) return LBM_ERR_INVALID_ARG;
     if (staging_bytes < lbm_sc_host_staging_bytes(&h->params)) return LBM_ERR_OUT_OF_MEMORY;
-    const size_t fb = (size_t)h->plan.N * compute_bytes(h->params.precision);
+    if (io_setup(h) != cudaSuccess) return LBM_ERR_CUDA;
+    const size_t esz = compute_bytes(h->params.precision);
+    const size_t fb = (size_t)h->plan.N * esz;
     const size_t field = align_up(fb);
     const int D = d_of(h->params.lattice);
+    const int nz = h->params.nz;
+    const size_t plane = (size_t)h->params.nx * h->params.ny * esz;  // bytes of one z plane of a field
     char* s = static_cast<char*>(d_staging);
-    void* dA = s;
-    void* dB = s + field;
-    void* dP = s + 2 * field;
-    void* dU = s + 3 * field;  // D consecutive planes of fb bytes
+    char* dA = s;
+    char* dB = s + field;
+    char* dP = s + 2 * field;
+    char* dU = s + 3 * field;  // D consecutive planes of fb bytes
     const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
-    if (cudaMemcpyAsync(dA, h_rhoA, fb, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (cudaMemcpyAsync(dB, h_rhoB, fb, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (h_u && cudaMemcpyAsync(dU, h_u, fb * D, h2d, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    lbm_status st = lbm_sc_init_fields(h, dA, dB, h_u ? dU : nullptr);
+    const cudaStream_t ms = h->stream, cs = h->io_stream;
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    // z slabs: the host copies of one slab overlap the kernels of another.
+    // Moments slabs are whole chunks of 32 planes (their own z chunking).
+    Plan mp = h->plan;
+    if (nz >= 64) mp.zchunk = 32;
+    const int chunks = (nz + mp.zchunk - 1) / mp.zchunk;
+    const int nslab = nz >= 64 ? (chunks < kIoSlabs ? chunks : kIoSlabs) : 1;  // no empty slab
+    int zb[kIoSlabs + 1];
+    for (int k = 0; k <= nslab; ++k) zb[k] = (int)((long long)chunks * k / nslab) * mp.zchunk;
+    zb[nslab] = nz;
+    auto copy_planes = [&](char* dev, const void* host, int z0, int z1, int nfield, cudaMemcpyKind kind) {
+        // planes [z0, z1) of nfield consecutive fields of fb bytes each
+        for (int f = 0; f < nfield; ++f) {
+            const size_t off = (size_t)f * fb + (size_t)z0 * plane, n = (size_t)(z1 - z0) * plane;
+            cudaError_t e = kind == h2d ? cudaMemcpyAsync(dev + off, static_cast<const char*>(host) + off, n, kind, cs)
+                                        : cudaMemcpyAsync(static_cast<char*>(const_cast<void*>(host)) + off, dev + off,
+                                                          n, kind, cs);
+            if (e != cudaSuccess) return false;
+        }
+        return true;
+    };
+    // inputs: the copy stream starts after the work already on the handle's
+    // stream (the staging may still be in use), last plane first (slab 0's
+    // periodic neighbour), then slab by slab; the init of slab k starts once
+    // slab k + 1 (its z + 1 neighbours) has landed
+    if (!ok(cudaEventRecord(h->io_start, ms)) || !ok(cudaStreamWaitEvent(cs, h->io_start, 0))) return LBM_ERR_CUDA;
+    if (!copy_planes(dA, h_rhoA, nz - 1, nz, 1, h2d) || !copy_planes(dB, h_rhoB, nz - 1, nz, 1, h2d) ||
+        (h_u && !copy_planes(dU, h_u, nz - 1, nz, D, h2d)))
+        return LBM_ERR_CUDA;
+    for (int k = 0; k < nslab; ++k) {
+        if (!copy_planes(dA, h_rhoA, zb[k], zb[k + 1], 1, h2d) || !copy_planes(dB, h_rhoB, zb[k], zb[k + 1], 1, h2d) ||
+            (h_u && !copy_planes(dU, h_u, zb[k], zb[k + 1], D, h2d)))
+            return LBM_ERR_CUDA;
+        if (!ok(cudaEventRecord(h->io_in[k], cs))) return LBM_ERR_CUDA;
+    }
+    h->cur = 0;
+    if (!ok(cudaMemsetAsync(h->plan.err, 0, sizeof(int), ms))) return LBM_ERR_CUDA;
+    for (int k = 0; k < nslab; ++k) {
+        if (!ok(cudaStreamWaitEvent(ms, h->io_in[k + 1 < nslab ? k + 1 : nslab - 1], 0))) return LBM_ERR_CUDA;
+        const cudaError_t e = h->plan.lattice == LBM_D2Q9
+                                  ? lbmsc::d2q9_init(h->plan, dA, dB, h_u ? dU : nullptr, h->buf[0], ms, zb[k], zb[k + 1])
+                                  : lbmsc::d3q19_init(h->plan, dA, dB, h_u ? dU : nullptr, h->buf[0], ms, zb[k], zb[k + 1]);
+        if (e != cudaSuccess) return LBM_ERR_CUDA;
+    }
+    lbm_status st = lbm_sc_step(h, nsteps);
     if (st != LBM_OK) return st;
-    st = lbm_sc_step(h, nsteps);
-    if (st != LBM_OK) return st;
-    st = lbm_sc_moments(h, h_rhoA_out ? dA : nullptr, h_rhoB_out ? dB : nullptr, h_u_out ? dU : nullptr,
-                        h_p_out ? dP : nullptr);
-    if (st != LBM_OK) return st;
-    if (h_rhoA_out && cudaMemcpyAsync(h_rhoA_out, dA, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (h_rhoB_out && cudaMemcpyAsync(h_rhoB_out, dB, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (h_u_out && cudaMemcpyAsync(h_u_out, dU, fb * D, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (h_p_out && cudaMemcpyAsync(h_p_out, dP, fb, d2h, h->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    return cuda_status(cudaStreamSynchronize(h->stream));
+    // outputs: the moments of slab k, then its copies on the copy stream while slab k + 1 computes
+    for (int k = 0; k < nslab; ++k) {
+        lbmsc::MomentsOut o;
+        o.rhoA = h_rhoA_out ? dA : nullptr;
+        o.rhoB = h_rhoB_out ? dB : nullptr;
+        o.u = h_u_out ? dU : nullptr;
+        o.p = h_p_out ? dP : nullptr;
+        o.partials = nullptr;
+        o.win[0] = o.win[1] = o.win[2] = 0.0;
+        o.win[3] = -1.0;
+        o.win[4] = 1e300;
+        o.zlo = zb[k];
+        o.zhi = zb[k + 1];
+        if (launch_moments(mp, h->buf[h->cur], o, ms) != cudaSuccess) return LBM_ERR_CUDA;
+        if (!ok(cudaEventRecord(h->io_out[k], ms)) || !ok(cudaStreamWaitEvent(cs, h->io_out[k], 0))) return LBM_ERR_CUDA;
+        if ((h_rhoA_out && !copy_planes(dA, h_rhoA_out, zb[k], zb[k + 1], 1, d2h)) ||
+            (h_rhoB_out && !copy_planes(dB, h_rhoB_out, zb[k], zb[k + 1], 1, d2h)) ||
+            (h_u_out && !copy_planes(dU, h_u_out, zb[k], zb[k + 1], D, d2h)) ||
+            (h_p_out && !copy_planes(dP, h_p_out, zb[k], zb[k + 1], 1, d2h)))
+            return LBM_ERR_CUDA;
+    }
+    if (!ok(cudaEventRecord(h->io_done, cs)) || !ok(cudaStreamWaitEvent(ms, h->io_done, 0))) return LBM_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(ms));
 }
 
 lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* pitch_x, int* pitch_y, int* ghost_x,
@@ -358,7 +457,11 @@ lbm_status lbm_sc_layout(const lbm_sc_handle* h, int* elem_bytes, int* q, int* p
     return LBM_OK;
 }
 
-void lbm_sc_destroy(lbm_sc_handle* h) { free(h); }
+void lbm_sc_destroy(lbm_sc_handle* h) {
+    if (!h) return;
+    io_release(h);
+    free(h);
+}
 
 const char* lbm_sc_status_string(lbm_status s) {
     switch (s) {

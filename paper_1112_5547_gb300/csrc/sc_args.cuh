@@ -17,6 +17,8 @@ template <class S> LatticeArgs<S> make_args(const Plan& p, const void* fin, void
     a.ny = p.ny;
     a.nz = p.nz;
     a.zchunk = p.zchunk;
+    a.zbase = 0;
+    a.zend = p.nz;
     a.N = p.N;
     a.px = p.px;
     a.py = p.py;

@@ -95,12 +95,25 @@ cudaError_t launch_batch_tma_mixed(const void* lats, const BatchItem* items, int
     return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_batch_tma_shape3(const void* lats, const BatchItem* items, int nitems, int parity, cudaStream_t st) {
+    constexpr size_t a = TmaTile<64, 6, S>::smem_bytes, b = TmaTile<48, 8, S>::smem_bytes,
+                     c = TmaTile<32, 12, S>::smem_bytes;
+    constexpr size_t smem = a > b ? (a > c ? a : c) : (b > c ? b : c);
+    constexpr auto kern = sc_batch_tma_shape3_kernel<S>;
+    const cudaError_t attr = dynamic_smem_once<kern>((int)smem);
+    if (attr != cudaSuccess) return attr;
+    if (nitems < 1) return cudaSuccess;
+    kern<<<(unsigned)nitems, 384, smem, st>>>(static_cast<const BatchTmaLattice*>(lats), items, nitems, parity);
+    return cudaGetLastError();
+}
+
 template <class L, class S>
 cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
                         int* ctr, cudaStream_t st) {
-    static_assert(kNumBatchTiles == 12 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
+    static_assert(kNumBatchTiles == 13 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
                       !kBatchTileTma[7] && kBatchTileY[8] == 4 && kBatchTileMixed == 9 && kBatchTileY[10] == 12 &&
-                      kBatchTileMixed384 == 11,
+                      kBatchTileMixed384 == 11 && kBatchTileShape3 == 12,
                   "batch tile table and dispatch disagree");
     switch (tile) {
         case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, false, st);
@@ -118,6 +131,7 @@ cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int 
             case 9: return launch_batch_tma_mixed<64, 4, 32, 8, 3>(lats, items, nitems, parity, st);
             case 10: return launch_batch_tma<32, 12, 2>(lats, items, nitems, parity, sm_count, ctr, true, st);
             case 11: return launch_batch_tma_mixed<64, 6, 32, 12, 2>(lats, items, nitems, parity, st);
+            case 12: return launch_batch_tma_shape3<2>(lats, items, nitems, parity, st);
         }
     }
     return cudaErrorInvalidValue;
@@ -183,7 +197,7 @@ cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, in
         bl.err = p.err;
         int tx, ty;
         batch_item_tile(tile, p, tx, ty);
-        bl.wide = tx == 64 ? 1 : 0;
+        bl.wide = tile == kBatchTileShape3 ? batch_shape3(p) : (tx == 64 ? 1 : 0);
         memcpy(dst, &bl, sizeof(bl));
         return cudaSuccess;
     }

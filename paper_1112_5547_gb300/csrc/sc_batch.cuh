@@ -152,7 +152,8 @@ struct BatchTmaLattice {  // CUtensorMap brings its own 128-byte alignment
     CUtensorMap map[2];
     LatticeArgs<float> a[2];
     int* err;
-    int wide;  // mixed-shape batches: 1 = this lattice's items are 64x4 tiles, 0 = 32x8
+    int wide;  // mixed-shape batches: 1 = this lattice's items are the wide tiles, 0 = the narrow ones;
+               // batch tile 12: the index of the lattice's shape in kShape3X / kShape3Y
 };
 
 // TMA-fed batch step: persistent CTAs run tma_item (sc_tma.cuh) over the work
@@ -250,6 +251,38 @@ __global__ void __launch_bounds__(WX* WY, 1)
         TmaSmem<NX, NY, S> sm(smem_raw);
         sm.init_barriers();
         tma_item<NX, NY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+    }
+}
+
+// Batch tile 12, one CTA per work item: each lattice's items run in its own
+// one of three 384-thread tile shapes (batch_shape3); the shared memory holds
+// the largest of their layouts.
+template <int S>
+__global__ void __launch_bounds__(384, 1)
+    sc_batch_tma_shape3_kernel(const BatchTmaLattice* __restrict__ lats, const BatchItem* __restrict__ items,
+                               int nitems, int parity) {
+    static_assert(kShape3X[0] * kShape3Y[0] == 384 && kShape3X[1] * kShape3Y[1] == 384 &&
+                      kShape3X[2] * kShape3Y[2] == 384,
+                  "every shape uses the same block");
+    extern __shared__ unsigned char smem_raw[];
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const BatchItem w = items[it];
+    const BatchTmaLattice* l = lats + w.lat;
+    const LatticeArgs<float> a = l->a[parity];
+    if (threadIdx.x == 0) tma_prefetch_map(&l->map[parity]);
+    if (l->wide == 1) {
+        TmaSmem<64, 6, S> sm(smem_raw);
+        sm.init_barriers();
+        tma_item<64, 6, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+    } else if (l->wide == 2) {
+        TmaSmem<48, 8, S> sm(smem_raw);
+        sm.init_barriers();
+        tma_item<48, 8, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+    } else {
+        TmaSmem<32, 12, S> sm(smem_raw);
+        sm.init_barriers();
+        tma_item<32, 12, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
     }
 }
 

@@ -22,19 +22,52 @@ struct BatchItem {
 // one CTA per item, with each lattice's own tile: 64x4 for lattices at least
 // 64 wide, else 32x8 (kBatchTileX/Y give the narrow one); with 384 threads
 // (12 warps per SM, 2 stages): 10 = 32x12 TMA-fed one CTA per item, 11 = the
-// mixed form with 64x6 and 32x12.
-constexpr int kNumBatchTiles = 12;
-constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32, 32, 32};
-constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8, 12, 12};
+// mixed form with 64x6 and 32x12; 12 = each lattice in the best of 64x6, 48x8
+// and 32x12 for its size (batch_shape3).
+constexpr int kNumBatchTiles = 13;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32, 32, 32, 32};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8, 12, 12, 12};
 constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true,
-                                                false, false, true, true, true};
+                                                false, false, true, true, true, true};
 constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true,
-                                                 true, true, true, true, true};
+                                                 true, true, true, true, true, true};
 constexpr int kBatchTileMixed = 9;
 constexpr int kBatchTileMixed384 = 11;
+constexpr int kBatchTileShape3 = 12;
+
+// The 384-thread tile shapes of batch tile 12, and the one a lattice takes:
+// the shape with the fewest nodes staged per node of the lattice, counting the
+// padding of ragged edge tiles ((tiles_x TX)(tiles_y TY) / (nx ny)) times the
+// halo boxes read per tile node ((TX + 8)(TY + 2) / (TX TY)), among the shapes
+// at most as large as the lattice.  A lattice 48 or 96 wide gets 48x8 with no
+// ragged tile (32- or 64-wide tiles would leave a quarter of the threads idle
+// in every second tile), 64 wide 64x6, 32 wide 32x12.  -1: none fits.
+constexpr int kShape3X[3] = {32, 64, 48};
+constexpr int kShape3Y[3] = {12, 6, 8};
+inline int batch_shape3(const Plan& p) {
+    int best = -1;
+    double best_cost = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const int tx = kShape3X[k], ty = kShape3Y[k];
+        if (p.nx < tx || p.ny < ty) continue;
+        const double pad = (double)((p.nx + tx - 1) / tx * tx) * ((p.ny + ty - 1) / ty * ty) / ((double)p.nx * p.ny);
+        const double cost = pad * (tx + 8) * (ty + 2) / (double)(tx * ty);
+        if (best < 0 || cost < best_cost - 1e-12) {
+            best = k;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
 
 // The tile of one lattice's items in a batch of this tile kind.
 inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
+    if (tile == kBatchTileShape3) {
+        const int k = batch_shape3(p);
+        tx = kShape3X[k < 0 ? 0 : k];
+        ty = kShape3Y[k < 0 ? 0 : k];
+        return;
+    }
     const bool mixed = tile == kBatchTileMixed || tile == kBatchTileMixed384;
     const bool wide = mixed && p.nx >= 64;
     tx = wide ? 64 : kBatchTileX[tile];
@@ -44,8 +77,9 @@ inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
 inline bool batch_tile_fits(int tile, const Plan& p) {
     if (tile < 0 || tile >= kNumBatchTiles) return false;
     if (!kBatchTileTma[tile]) return true;  // the z-marching batch kernel chooses the collision at run time
-    return p.lattice == 1 && p.precision == 1 && p.forcing == kForcingShift && p.model == kModelSC &&
-           p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];
+    if (!(p.lattice == 1 && p.precision == 1 && p.forcing == kForcingShift && p.model == kModelSC)) return false;
+    if (tile == kBatchTileShape3) return batch_shape3(p) >= 0;
+    return p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];
 }
 
 // Bytes of one lattice's descriptor, and the descriptor itself (both parities;

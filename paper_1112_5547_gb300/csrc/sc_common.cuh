@@ -161,6 +161,7 @@ template <class S> struct LatticeArgs {
     S* fout;            // populations after collision (same node, not pushed)
     int nx, ny, nz;
     int zchunk;         // planes per CTA along z (D3Q19)
+    int zbase, zend;    // planes [zbase, zend) covered by a moments launch (0, nz otherwise)
     long long N;        // nx * ny * nz
     // Population storage is ghost-padded: each z plane of a population is
     // py rows of px values, node (x, y) at column x + gxo, row y + gyo.  The

@@ -15,8 +15,9 @@ cudaError_t d3q19_step(const Plan& p, const void* fin, void* fout, cudaStream_t 
     }
     return cudaErrorInvalidValue;
 }
-cudaError_t d3q19_init(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st) {
-    return init_any<D3Q19>(p, rA, rB, u, fout, st);
+cudaError_t d3q19_init(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st,
+                      int zlo, int zhi) {
+    return init_any<D3Q19>(p, rA, rB, u, fout, st, zlo, zhi);
 }
 cudaError_t d3q19_moments(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st) {
     return moments_any<D3Q19>(p, fin, o, st);

@@ -184,20 +184,24 @@ template <class L, class S> cudaError_t step_typed_other(const Plan& p, const La
 }
 
 template <class L, class S>
-cudaError_t init_typed(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st) {
+cudaError_t init_typed(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st,
+                       int zlo, int zhi) {
     using C = typename Codec<S>::C;
     const LatticeArgs<S> a = make_args<S>(p, nullptr, fout);
-    long long blocks = (p.N + 255) / 256;
+    if (zhi <= 0 || zhi > p.nz) zhi = p.nz;
+    if (zlo < 0 || zlo >= zhi) return zlo == zhi ? cudaSuccess : cudaErrorInvalidValue;
+    long long blocks = ((long long)p.nx * p.ny * (zhi - zlo) + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks < 1) blocks = 1;
     sc_init_kernel<L, S><<<(unsigned)blocks, 256, 0, st>>>(a, static_cast<const C*>(rA), static_cast<const C*>(rB),
-                                                          static_cast<const C*>(u));
+                                                          static_cast<const C*>(u), zlo, zhi);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t moments_typed(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st) {
     using C = typename Codec<S>::C;
-    const LatticeArgs<S> a = make_args<S>(p, fin, nullptr);
+    LatticeArgs<S> a = make_args<S>(p, fin, nullptr);
     FieldArgs<C> fo;
     fo.rhoA = static_cast<C*>(o.rhoA);
     fo.rhoB = static_cast<C*>(o.rhoB);
@@ -209,7 +213,15 @@ cudaError_t moments_typed(const Plan& p, const void* fin, const MomentsOut& o, c
     fo.win_c[2] = o.win[2];
     fo.r_in2 = o.win[3] < 0 ? -1.0 : o.win[3] * o.win[3];
     fo.r_out2 = o.win[4] * o.win[4];
-    sc_fused_kernel<L, S, kTX, kTY, kModeMoments, 1><<<fused_grid(p), dim3(kTX, kTY), 0, st>>>(a, fo);
+    dim3 grid = fused_grid(p);
+    if (o.zhi > 0) {
+        // planes [zlo, zhi) only (whole chunks of p.zchunk from zlo; fields only, no partials)
+        if (o.partials || o.zlo < 0 || o.zlo >= o.zhi || o.zhi > p.nz) return cudaErrorInvalidValue;
+        a.zbase = o.zlo;
+        a.zend = o.zhi;
+        grid.z = (unsigned)((o.zhi - o.zlo + p.zchunk - 1) / p.zchunk);
+    }
+    sc_fused_kernel<L, S, kTX, kTY, kModeMoments, 1><<<grid, dim3(kTX, kTY), 0, st>>>(a, fo);
     return cudaGetLastError();
 }
 
@@ -226,14 +238,15 @@ template <class L> cudaError_t step_any(const Plan& p, const void* fin, void* fo
 }
 
 template <class L>
-cudaError_t init_any(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st) {
+cudaError_t init_any(const Plan& p, const void* rA, const void* rB, const void* u, void* fout, cudaStream_t st,
+                     int zlo, int zhi) {
     switch (p.precision) {
-        case 0: return init_typed<L, double>(p, rA, rB, u, fout, st);
-        case 1: return init_typed<L, float>(p, rA, rB, u, fout, st);
-        case 2: return init_typed<L, __nv_bfloat16>(p, rA, rB, u, fout, st);
-        case 3: return init_typed<L, __half>(p, rA, rB, u, fout, st);
-        case 4: return init_typed<L, bf16_rest>(p, rA, rB, u, fout, st);
-        case 5: return init_typed<L, f16_rest>(p, rA, rB, u, fout, st);
+        case 0: return init_typed<L, double>(p, rA, rB, u, fout, st, zlo, zhi);
+        case 1: return init_typed<L, float>(p, rA, rB, u, fout, st, zlo, zhi);
+        case 2: return init_typed<L, __nv_bfloat16>(p, rA, rB, u, fout, st, zlo, zhi);
+        case 3: return init_typed<L, __half>(p, rA, rB, u, fout, st, zlo, zhi);
+        case 4: return init_typed<L, bf16_rest>(p, rA, rB, u, fout, st, zlo, zhi);
+        case 5: return init_typed<L, f16_rest>(p, rA, rB, u, fout, st, zlo, zhi);
     }
     return cudaErrorInvalidValue;
 }

@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         __syncthreads();
         process(cur, 0, 0, 0, 0);
     } else {
-        const int z0 = blockIdx.z * a.zchunk;
-        const int z1 = min(z0 + a.zchunk, nz);
+        const int z0 = a.zbase + blockIdx.z * a.zchunk;
+        const int z1 = min(z0 + a.zchunk, a.zend);
         {
             C tmp[2][Q];
             density_plane(0, z0 == 0 ? nz - 1 : z0 - 1, tmp);
@@ -421,19 +421,21 @@ __global__ void __launch_bounds__(NT) sc_diag_finish_kernel(const double* __rest
     }
 }
 
-// Populations of the rest / moving equilibrium: the buffer slot of direction i
+// Populations of the rest / moving equilibrium (planes [zlo, zhi)): the buffer slot of direction i
 // at node x holds f^eq_i(rho_s(x + c_i), u(x + c_i)), so pulling it at x + c_i
 // gives f_i(x + c_i, 0) = f^eq_i of that node.  The ghost columns and rows get
 // the values of their periodic images.
 template <class L, class S>
 __global__ void __launch_bounds__(256)
     sc_init_kernel(const LatticeArgs<S> a, const typename Codec<S>::C* __restrict__ rhoA,
-                   const typename Codec<S>::C* __restrict__ rhoB, const typename Codec<S>::C* __restrict__ u) {
+                   const typename Codec<S>::C* __restrict__ rhoB, const typename Codec<S>::C* __restrict__ u, int zlo,
+                   int zhi) {
     using C = typename Codec<S>::C;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int ex = nx + 4, ey = ny + 4;  // cells x in [-2, nx + 1], y in [-2, ny + 1]
-    const long long ncells = (long long)ex * ey * nz;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells;
+    // the cells of planes [zlo, zhi); they read the fields of planes zlo - 1 .. zhi (periodic)
+    const long long ncells = (long long)ex * ey * zhi;
+    for (long long k = (long long)ex * ey * zlo + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ncells;
          k += (long long)gridDim.x * blockDim.x) {
         const int cx = (int)(k % ex) - 2;
         const int cy = (int)((k / ex) % ey) - 2;

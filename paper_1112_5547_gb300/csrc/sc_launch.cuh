@@ -148,6 +148,7 @@ struct MomentsOut {
     void* p;
     double* partials;       // per-CTA diagnostics, or null
     double win[5];          // cx, cy, cz, r_in, r_out (r_in < 0: no inner window)
+    int zlo = 0, zhi = 0;   // zhi > 0: fields of planes [zlo, zhi) only (D3Q19, no partials)
 };
 
 inline dim3 fused_grid(const Plan& p) {
@@ -167,8 +168,9 @@ inline long long fused_blocks(const Plan& p) {
 }
 
 cudaError_t d2q9_step(const Plan& p, const void* fin, void* fout, cudaStream_t st);
+// init of planes [zlo, zhi) (zhi = 0: all planes)
 cudaError_t d2q9_init(const Plan& p, const void* rA, const void* rB, const void* u, void* fout,
-                      cudaStream_t st);
+                      cudaStream_t st, int zlo = 0, int zhi = 0);
 cudaError_t d2q9_moments(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st);
 cudaError_t d3q19_step(const Plan& p, const void* fin, void* fout, cudaStream_t st);
 // the step of each storage precision (sc_d3q19_step_*.cu)
@@ -179,7 +181,7 @@ cudaError_t d3q19_step_f16(const Plan& p, const void* fin, void* fout, cudaStrea
 cudaError_t d3q19_step_bf16_rest(const Plan& p, const void* fin, void* fout, cudaStream_t st);
 cudaError_t d3q19_step_f16_rest(const Plan& p, const void* fin, void* fout, cudaStream_t st);
 cudaError_t d3q19_init(const Plan& p, const void* rA, const void* rB, const void* u, void* fout,
-                       cudaStream_t st);
+                       cudaStream_t st, int zlo = 0, int zhi = 0);
 cudaError_t d3q19_moments(const Plan& p, const void* fin, const MomentsOut& o, cudaStream_t st);
 cudaError_t diag_finish(const double* partials, long long nparts, double* out, cudaStream_t st);
 

@@ -205,7 +205,8 @@ __device__ __forceinline__ void tma_pulled_pair(const unsigned char* sb, int i, 
 
 // Density rho_s of frame node (fx, fy) for one species s (a run-time value:
 // the same instructions read the other species' planes or half-words), with
-// the values decoded and summed exactly as node_density sums a node's pulls.
+// the values decoded and summed exactly as node_density sums a node's pulls
+// (moving populations in order, the rest population last).
 template <int TX, int TY, int S, class St>
 __device__ __forceinline__ float tma_density(const unsigned char* sb, int s, int fx, int fy, float ref_s) {
     using L = D3Q19;
@@ -222,10 +223,10 @@ __device__ __forceinline__ float tma_density(const unsigned char* sb, int s, int
             return tma_pulled<TX, TY, S, St>(sb, s, i, fx, fy, ref_s);
         }
     };
-    float r = pulled(0);
+    float r = pulled(1);
 #pragma unroll
-    for (int i = 1; i < L::Q; ++i) r = __fadd_rn(r, pulled(i));
-    return r;
+    for (int i = 2; i < L::Q; ++i) r = __fadd_rn(r, pulled(i));
+    return __fadd_rn(r, pulled(0));
 }
 
 // The item a CTA runs after the current one (batch kernels): the elected

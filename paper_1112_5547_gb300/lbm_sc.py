@@ -61,9 +61,27 @@ EXPORTS = (
 # Tile 9 gives each lattice its own tile: 64x4 when it is at least 64 wide, else 32x8;
 # tiles 10 (32x12) and 11 (64x6 / 32x12 per lattice) run 384-thread CTAs.
 BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (32, 12),
-               (32, 12))
-BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True, True, True)
-BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True, True, True)
+               (32, 12), (32, 12))
+BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True, True, True, True)
+BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True, True, True, True)
+BATCH_TILE_SHAPE3 = 12  # each lattice in the best of 64x6, 48x8, 32x12 for its size
+SHAPE3 = ((32, 12), (64, 6), (48, 8))
+
+
+def batch_shape3(nx: int, ny: int) -> int:
+    """Mirror of the library's choice of a lattice's tile in batch tile 12: the index
+    into SHAPE3 of the shape with the fewest staged nodes per lattice node (ragged
+    padding times halo boxes), among the shapes at most as large as the lattice;
+    -1 if none fits."""
+    best, best_cost = -1, 0.0
+    for k, (tx, ty) in enumerate(SHAPE3):
+        if nx < tx or ny < ty:
+            continue
+        pad = (-(-nx // tx) * tx) * (-(-ny // ty) * ty) / (nx * ny)
+        cost = pad * (tx + 8) * (ty + 2) / (tx * ty)
+        if best < 0 or cost < best_cost - 1e-12:
+            best, best_cost = k, cost
+    return best
 
 
 def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
@@ -74,8 +92,12 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
         return True
     tx, ty = BATCH_TILES[tile]
     p = lattice.params
-    return (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT
-            and p.model == LBM_MODEL_SC and p.nx >= tx and p.ny >= ty)
+    if not (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT
+            and p.model == LBM_MODEL_SC):
+        return False
+    if tile == BATCH_TILE_SHAPE3:
+        return batch_shape3(p.nx, p.ny) >= 0
+    return p.nx >= tx and p.ny >= ty
 
 # CTA tiles (x columns by y columns) the step kernel can be launched with, and
 # their shared-memory stages or CTAs per SM.

@@ -35,6 +35,9 @@ MIX3_MIXED = [((40, 20, 48), 1.0, 1.0, G0), ((17, 33, 70), 0.8, 1.3, 2.0), ((20,
 # every lattice at least 32 x 12: the 384-thread batch tiles (10: 32x12; 11: 64x6 or 32x12 per lattice)
 MIX3_TALL = [((40, 20, 48), 1.0, 1.0, G0), ((17, 33, 70), 0.8, 1.3, 2.0), ((20, 16, 32), 1.1, 0.9, 2.2),
              ((33, 65, 65), 1.2, 1.2, 1.6), ((9, 12, 128), 1.0, 1.0, G0)]
+# batch tile 12 gives each lattice the best of 64x6, 48x8 and 32x12: one lattice of each
+MIX3_SHAPE3 = [((12, 64, 64), 1.0, 1.0, G0), ((10, 40, 48), 0.8, 1.3, 2.0), ((9, 24, 32), 1.1, 0.9, 2.2),
+               ((20, 17, 96), 1.2, 1.2, 1.6)]
 MIX2 = [((64, 64), 1.0, 1.0, G0), ((37, 50), 0.8, 1.3, 2.0), ((7, 130), 1.0, 1.0, 2.2), ((96, 33), 1.1, 0.9, G0)]
 
 
@@ -65,7 +68,8 @@ def _assert_same(a, b, what):
 @pytest.mark.parametrize("lattice,mix,precision", [(1, MIX3, "f32"), (0, MIX2, "f64"), (1, MIX3, "bf16"),
                                                    (0, MIX2, "f16"), (1, MIX3_TMA, "f32"),
                                                    (1, MIX3, "bf16_rest"), (0, MIX2, "f16_rest"),
-                                                   (1, MIX3_MIXED, "f32"), (1, MIX3_TALL, "f32")])
+                                                   (1, MIX3_MIXED, "f32"), (1, MIX3_TALL, "f32"),
+                                                   (1, MIX3_SHAPE3, "f32")])
 def test_batch_equals_solo(sc, lattice, mix, precision):
     steps = 13
     solo = _make(sc, lattice, mix, precision)
@@ -73,8 +77,12 @@ def test_batch_equals_solo(sc, lattice, mix, precision):
         lat.step(steps)
     ref = [_state(lat) for lat in solo]
     tiles = [t for t in range(len(sc.BATCH_TILES)) if all(sc.batch_tile_fits(t, lat) for lat in solo)]
-    if mix is MIX3_TMA:  # every tile of at most 8 rows (one lattice is 8 tall)
-        assert tiles == [t for t in range(len(sc.BATCH_TILES)) if sc.BATCH_TILES[t][1] <= 8]
+    if mix is MIX3_TMA:  # every tile of at most 8 rows (one lattice is 8 tall), and tile 12 (48x8 for it)
+        assert tiles == [t for t in range(len(sc.BATCH_TILES))
+                         if sc.BATCH_TILES[t][1] <= 8 or t == sc.BATCH_TILE_SHAPE3]
+    if mix is MIX3_SHAPE3:
+        assert sc.BATCH_TILE_SHAPE3 in tiles
+        assert sorted(sc.batch_shape3(shape[2], shape[1]) for shape, *_ in mix[:3]) == [0, 1, 2]
     if mix is MIX3_MIXED:
         assert 9 in tiles
     if mix is MIX3_TALL:

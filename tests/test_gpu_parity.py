@@ -173,12 +173,16 @@ def test_diagnostics_match_oracle_fields(sc, oracle_mod):
     assert d["status"] == sc.LBM_OK
 
 
-def test_run_host_equals_device_path(sc):
-    """lbm_sc_run_host (host buffers, copies inside) gives the device path's result bitwise."""
+@pytest.mark.parametrize("shape,with_u", [((16, 20, 24), False), ((100, 12, 40), True), ((256, 8, 32), False)])
+def test_run_host_equals_device_path(sc, shape, with_u):
+    """lbm_sc_run_host (host buffers, copies inside) gives the device path's result bitwise,
+    also when its copies overlap the kernels in z slabs (64 planes or more: 100 planes make
+    4 slabs of whole 32-plane chunks and a ragged last one, 256 planes the full 8), with and
+    without an initial velocity, and on two calls in a row."""
     import torch
-    shape = (16, 20, 24)
     rA, rB = inputs.drop(shape, 5, seed=3, dtype=np.float32)
-    dev = sc.Lattice(1, shape, 1.0, 1.0, G0, "f32").init(rA, rB).step(25)
+    u0 = (1e-3 * np.random.default_rng(4).standard_normal(shape + (3,))).astype(np.float32) if with_u else None
+    dev = sc.Lattice(1, shape, 1.0, 1.0, G0, "f32").init(rA, rB, u0).step(25)
     ref = _gpu_fields(dev)
     lat = sc.Lattice(1, shape, 1.0, 1.0, G0, "f32")
     nbytes = sc.lbm_sc_host_staging_bytes(lat.params)
@@ -189,12 +193,16 @@ def test_run_host_equals_device_path(sc):
     N = rA.size
     oA, oB, oP = (torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(3))
     oU = torch.empty(3 * N, dtype=torch.float32).pin_memory()
-    sc.lbm_sc_run_host(lat.handle, sp, nbytes, hA.data_ptr(), hB.data_ptr(), None, 25,
-                       oA.data_ptr(), oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
-    assert np.array_equal(oA.numpy().reshape(shape), ref[0].astype(np.float32))
-    assert np.array_equal(oB.numpy().reshape(shape), ref[1].astype(np.float32))
-    assert np.array_equal(oU.numpy().reshape(3, -1).T.reshape(shape + (3,)), ref[2].astype(np.float32))
-    assert np.array_equal(oP.numpy().reshape(shape), ref[3].astype(np.float32))
+    hU = torch.from_numpy(np.ascontiguousarray(np.moveaxis(u0, -1, 0)).reshape(-1)).pin_memory() if with_u else None
+    for _ in range(2):
+        for t in (oA, oB, oP, oU):
+            t.fill_(-1.0)
+        sc.lbm_sc_run_host(lat.handle, sp, nbytes, hA.data_ptr(), hB.data_ptr(), hU.data_ptr() if with_u else None,
+                           25, oA.data_ptr(), oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
+        assert np.array_equal(oA.numpy().reshape(shape), ref[0].astype(np.float32))
+        assert np.array_equal(oB.numpy().reshape(shape), ref[1].astype(np.float32))
+        assert np.array_equal(oU.numpy().reshape(3, -1).T.reshape(shape + (3,)), ref[2].astype(np.float32))
+        assert np.array_equal(oP.numpy().reshape(shape), ref[3].astype(np.float32))
 
 
 def test_unstable_state_reported(sc):
