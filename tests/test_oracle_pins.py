@@ -877,3 +877,25 @@ def test_sc_and_fe_relax_to_the_same_interface_profile(oracle_mod):
     # and both are relaxed flat interfaces: two crossings of phi = 0 at the slab edges
     phi = (a1 - b1)[0]
     assert np.count_nonzero(np.diff(np.sign(phi)) != 0) == 2
+
+
+def test_stored_long_runs_obey_laplace_in_2d_and_3d():
+    """The oracle's long runs stored in tests/golden (written by make_config_goldens.py,
+    which calls only the oracle): the D2Q9 batch (20000 steps) gives dP linear in 1/R
+    with a vanishing intercept (Laplace, Sec. 4.1, dP = sigma / R in 2D), a flat
+    interface without a jump, and conserves each species' mass to 1e-11; the D3Q19
+    drop (5000 steps) obeys the 3D law dP = 2 sigma / R with the same sigma within
+    5 % (the interface tension belongs to the planar interface profile, which the
+    two lattices resolve alike), so a mis-weighted or mis-signed off-plane force term
+    of the D3Q19 oracle, which changes the 3D tension, fails here."""
+    d2 = json.load(open(os.path.join(GOLDEN, "laplace_batch_256.json")))
+    d3 = json.load(open(os.path.join(GOLDEN, "drop3d_128_5000.json")))
+    fit = d2["fit"]
+    assert fit["sigma"] > 0 and fit["r2"] > 0.99
+    dPmax = max(c["dP"] for c in d2["cases"].values() if "dP" in c)
+    assert abs(fit["c0"]) < 0.05 * dPmax
+    assert abs(d2["cases"]["slab"]["dP_flat"]) < 1e-4 * dPmax  # seeded noise only
+    for c in list(d2["cases"].values()) + [d3]:
+        assert abs(c["mass_A"] / c["mass_A0"] - 1) < 1e-11 and abs(c["mass_B"] / c["mass_B0"] - 1) < 1e-11
+    sigma3 = d3["dP"] * d3["R"] / 2
+    assert abs(sigma3 / fit["sigma"] - 1) < 0.05, (sigma3, fit["sigma"])
