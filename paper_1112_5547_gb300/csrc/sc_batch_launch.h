@@ -36,12 +36,13 @@ constexpr int kBatchTileMixed384 = 11;
 constexpr int kBatchTileShape3 = 12;
 
 // The 384-thread tile shapes of batch tile 12, and the one a lattice takes:
-// the shape with the fewest nodes staged per node of the lattice, counting the
-// padding of ragged edge tiles ((tiles_x TX)(tiles_y TY) / (nx ny)) times the
-// halo boxes read per tile node ((TX + 8)(TY + 2) / (TX TY)), among the shapes
-// at most as large as the lattice.  A lattice 48 or 96 wide gets 48x8 with no
-// ragged tile (32- or 64-wide tiles would leave a quarter of the threads idle
-// in every second tile), 64 wide 64x6, 32 wide 32x12.  -1: none fits.
+// the shape with the least work per node of the lattice, counting the padding
+// of ragged edge tiles ((tiles_x TX)(tiles_y TY) / (nx ny)) times the columns
+// its boxes read per tile column ((TX + 8) / TX: the halo rows in y mostly come
+// from L2, the extra columns in x do not), among the shapes at most as large
+// as the lattice.  Lattices 32 wide get 32x12, 48 and 96 wide 48x8 (no ragged
+// tile: a 64-wide tile on 96 columns leaves half of every second tile idle),
+// 64 and 128 wide 64x6.  -1: none fits.
 constexpr int kShape3X[3] = {32, 64, 48};
 constexpr int kShape3Y[3] = {12, 6, 8};
 inline int batch_shape3(const Plan& p) {
@@ -51,7 +52,7 @@ inline int batch_shape3(const Plan& p) {
         const int tx = kShape3X[k], ty = kShape3Y[k];
         if (p.nx < tx || p.ny < ty) continue;
         const double pad = (double)((p.nx + tx - 1) / tx * tx) * ((p.ny + ty - 1) / ty * ty) / ((double)p.nx * p.ny);
-        const double cost = pad * (tx + 8) * (ty + 2) / (double)(tx * ty);
+        const double cost = pad * (tx + 8) / (double)tx;
         if (best < 0 || cost < best_cost - 1e-12) {
             best = k;
             best_cost = cost;

@@ -98,11 +98,18 @@ __device__ __forceinline__ void store_node(const LatticeArgs<S>& a, int x, int y
     if constexpr (Codec<S>::kRest) base = make_float2(rA, rB);
     store_cell<L, S>(a, cell(a, x, y, z), f, base);
     const int nx = a.nx, ny = a.ny;
-    if (x < 2 || x >= nx - 2 || y < 2 || y >= ny - 2) {
+    // x images: the two ghost columns the pulls read, widened to a whole 32-byte
+    // sector on each side (columns -GX .. -1 and nx .. nx + GX - 1) when the
+    // lattice is at least that wide, so the ghost sectors are written whole: a
+    // partly written sector costs a read of the sector from HBM besides its
+    // write (measured: 20 % more write traffic on 128-wide rows without it)
+    constexpr int kSector = 32 / (int)sizeof(S) > 2 ? 32 / (int)sizeof(S) : 2;
+    const int GX = nx >= kSector ? kSector : 2;
+    if (x < GX || x >= nx - GX || y < 2 || y >= ny - 2) {
 #pragma unroll 1
         for (int ix = -2; ix <= 2; ++ix) {
             const int xi = x + ix * nx;
-            if (xi < -2 || xi > nx + 1) continue;
+            if (xi < -GX || xi > nx + GX - 1) continue;
 #pragma unroll 1
             for (int iy = -2; iy <= 2; ++iy) {
                 const int yi = y + iy * ny;

@@ -57,16 +57,19 @@ inline int population_planes(int lattice, int precision) {
 // segment of a tile starting at a multiple of 32 nodes is whole cache lines
 // (a misaligned store would leave partial sectors shared with the next CTA's
 // tile).  The ghost columns x = -2, -1, nx, nx+1 and rows y = -2, -1, ny, ny+1
-// hold periodic images; the columns up to 16 bytes beyond them exist so that
-// 16-byte-aligned TMA boxes of x0 - 16 bytes .. x0 + TX + 16 bytes stay inside
-// the row.
+// hold periodic images; on lattices at least a sector wide the images fill the
+// whole 32-byte sector on each side of the row (store_node), and the row has
+// room for it, which also keeps 16-byte-aligned TMA boxes of x0 - 16 bytes ..
+// x0 + TX + 16 bytes inside the row.
 inline void storage_geometry(int nx, int ny, int nz, int elem_bytes, int& px, int& py, int& gxo, int& gyo,
                              long long& Np) {
     const int line = 128 / elem_bytes;  // values per 128 bytes
-    const int box_pad = 16 / elem_bytes;
+    // right margin: the 32-byte sector of ghost images beyond column nx - 1
+    // (store_node), which also covers the 16-byte pad of the TMA boxes
+    const int margin = 32 / elem_bytes;
     gxo = line;
     gyo = 2;
-    px = (nx + gxo + box_pad + line - 1) / line * line;
+    px = (nx + gxo + margin + line - 1) / line * line;
     py = ny + 2 * gyo;
     Np = (long long)px * py * nz;
 }

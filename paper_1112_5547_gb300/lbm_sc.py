@@ -70,15 +70,15 @@ SHAPE3 = ((32, 12), (64, 6), (48, 8))
 
 def batch_shape3(nx: int, ny: int) -> int:
     """Mirror of the library's choice of a lattice's tile in batch tile 12: the index
-    into SHAPE3 of the shape with the fewest staged nodes per lattice node (ragged
-    padding times halo boxes), among the shapes at most as large as the lattice;
-    -1 if none fits."""
+    into SHAPE3 of the shape with the least work per lattice node (ragged padding
+    times the box columns read per tile column), among the shapes at most as large
+    as the lattice; -1 if none fits."""
     best, best_cost = -1, 0.0
     for k, (tx, ty) in enumerate(SHAPE3):
         if nx < tx or ny < ty:
             continue
         pad = (-(-nx // tx) * tx) * (-(-ny // ty) * ty) / (nx * ny)
-        cost = pad * (tx + 8) * (ty + 2) / (tx * ty)
+        cost = pad * (tx + 8) / tx
         if best < 0 or cost < best_cost - 1e-12:
             best, best_cost = k, cost
     return best
