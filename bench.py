@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--profile", default=None, choices=list(PROFILE_CASES),
                     help="run one small fixed workload for ncu and exit (no JSON line)")
     ap.add_argument("--batch-tile", type=int, default=5, help="batch tile of the --profile batch cases")
+    ap.add_argument("--ragged-n", type=int, default=64, help="lattices of the --profile ragged case (same recipe)")
     return ap.parse_args()
 
 
@@ -98,7 +99,7 @@ def profile_case(a):
                      in --precision, --tile / --zchunk, solo steps
       step2d         the same on an L^2 D2Q9 lattice
       solo_vs_batch  the D3Q19 drop stepped twice alone, then twice as a batch of one
-      ragged         the 64-lattice ragged batch (inputs.ragged_drop_specs), --batch-tile
+      ragged         the ragged batch (inputs.ragged_drop_specs, --ragged-n lattices), --batch-tile
       pfm            the phase-field solver (FP32) on an L^3 drop (rho_A 1.2 / rho_B 0.2,
                      tau 0.6, g 0.3, dt 0.1)
 
@@ -139,10 +140,11 @@ def profile_case(a):
             b.close()
         else:
             lats = []
-            for sp in inputs.ragged_drop_specs():
+            for sp in inputs.ragged_drop_specs(n=a.ragged_n):
                 rA, rB = inputs.spec_fields(sp, dtype=np.float32)
                 lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32",
                                            stream=st).init(rA, rB))
+            print("ragged batch: %d lattices, %d nodes" % (len(lats), sum(x.N for x in lats)))
             b = lbm_sc.Batch(lats, tile=a.batch_tile, zchunk=a.zchunk, stream=st)
             b.step(a.steps)
             st.synchronize()

@@ -163,7 +163,7 @@ class Server:
         if check_every % chunk:
             raise ValueError("chunk must divide check_every")
         self.torch = torch
-        self.budget = float(hbm_budget)
+        self.budget = float(hbm_budget) - self.RESERVE_BYTES  # the lattices' and their batches' share
         self.max_active_nodes = max_active_nodes
         self.chunk = int(chunk)
         self.check_every = int(check_every)
@@ -177,12 +177,30 @@ class Server:
         self._diag = None
 
     # -- helpers -------------------------------------------------------------
+    # Device memory the server holds besides the lattices' own workspaces, kept
+    # out of the HBM budget: the diagnostics rows of one check (one lbm_sc_diag
+    # per due request), the batches' CUDA graphs and allocator rounding.
+    RESERVE_BYTES = 64 << 20
+    # A lattice's share of its batch workspace: its descriptor (both parities,
+    # two tensor maps and two argument blocks, under 2 KiB) and its work items
+    # (16 bytes each), at most one per 32 x 4 column tile and plane (every batch
+    # tile is at least that large, every z chunk at least one plane).
+    BATCH_DESCRIPTOR_BYTES = 2048
+
+    @staticmethod
+    def batch_share(req: Request) -> int:
+        """Upper bound of the bytes a request adds to its batch's workspace."""
+        ny, nx = req.shape[-2], req.shape[-1]
+        nz = req.shape[0] if len(req.shape) == 3 else 1
+        items = -(-nx // 32) * -(-ny // 4) * nz
+        return Server.BATCH_DESCRIPTOR_BYTES + 16 * items
+
     @staticmethod
     def footprint(req: Request) -> int:
         """Device bytes a resident request holds: its workspace (two population
-        buffers and diagnostics scratch)."""
+        buffers and diagnostics scratch) and its share of the batch workspace."""
         p = lbm_sc.make_params(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision)
-        return int(lbm_sc.lbm_sc_workspace_bytes(p))
+        return int(lbm_sc.lbm_sc_workspace_bytes(p)) + Server.batch_share(req)
 
     @staticmethod
     def batch_shape(lats):
@@ -216,7 +234,7 @@ class Server:
             lat = lbm_sc.Lattice(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision,
                                  device=self.device, stream=self.stream)
             lat.init(f[0], f[1])
-        return _Slot(req, lat, lat.workspace_bytes, now)
+        return _Slot(req, lat, lat.workspace_bytes + self.batch_share(req), now)
 
     def _retire(self, s: _Slot, now, converged: bool, umax: float) -> Result:
         """Copy the result (the density field of component A) to host memory,

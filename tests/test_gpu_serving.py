@@ -53,7 +53,8 @@ def test_admission_respects_budget(sv):
     the rest wait, and every request still finishes with its own result."""
     reqs = sv.poisson_requests(5, rate=1000.0, seed=5, d3_fraction=1.0, sizes3=(40,))
     fp = sv.Server.footprint(reqs[0])
-    srv = sv.Server(hbm_budget=2.5 * fp, chunk=100, check_every=500, max_steps=1000, keep_fields=True)
+    srv = sv.Server(hbm_budget=sv.Server.RESERVE_BYTES + 2.5 * fp, chunk=100, check_every=500, max_steps=1000,
+                    keep_fields=True)
     res, st = srv.run(reqs)
     assert st.max_resident == 2
     assert [r.rid for r in res] == list(range(5))

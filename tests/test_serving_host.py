@@ -23,13 +23,27 @@ def test_poisson_stream_is_seeded_and_in_range():
         assert len(r.centre) == len(r.shape)
 
 
-def test_footprint_is_the_workspace():
+def test_footprint_is_the_workspace_and_the_batch_share():
+    """A request's footprint is its workspace plus a bound on its share of the batch
+    workspace, and that bound covers lbm_sc_batch_workspace_bytes for every batch
+    tile the request's lattice takes (handles are host-only: no GPU needed)."""
     from paper_1112_5547_gb300 import lbm_sc, serving
     r = serving.poisson_requests(1, seed=1, d3_fraction=1.0, sizes3=(192,))[0]
     p = lbm_sc.make_params(r.lattice, r.shape, r.tau_A, r.tau_B, r.G, "f32")
-    assert serving.Server.footprint(r) == lbm_sc.lbm_sc_workspace_bytes(p)
+    assert serving.Server.footprint(r) == lbm_sc.lbm_sc_workspace_bytes(p) + serving.Server.batch_share(r)
     # the largest D3Q19 request: two FP32 buffers of 2 x 19 values per node
     assert serving.Server.footprint(r) >= 2 * 2 * 19 * 4 * 192 ** 3
+    for req in serving.poisson_requests(12, seed=2, sizes2=(64, 1024), sizes3=(32, 40, 192)):
+        q = lbm_sc.make_params(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision)
+        h = lbm_sc.lbm_sc_create(q, 256 * 1024, lbm_sc.lbm_sc_workspace_bytes(q), 0)
+        try:
+            for tile in range(len(lbm_sc.BATCH_TILES)):
+                for zc in (0, 1, 16):
+                    ws = lbm_sc.lbm_sc_batch_workspace_bytes([h], tile, zc)
+                    # one lattice's batch: its share plus the queue counters and the alignment slack
+                    assert ws <= serving.Server.batch_share(req) + 1024, (req.shape, tile, zc, ws)
+        finally:
+            lbm_sc.lbm_sc_destroy(h)
 
 
 def test_ragged_batch_specs_seeded_and_in_range():
