@@ -19,23 +19,26 @@
 // rho(x - c_i)) leaves a force of about one ulp in uniform regions; in FP32
 // that random-walks the total momentum and lets a drop drift by about 1e-5
 // lattice units per 1000 steps.  The rest population of the equilibrium is closed as
-// f^eq_0 = rho - sum_{i>0} f^eq_i: equal to w_0 rho (...) in exact arithmetic,
-// it keeps FP32 mass conservation at rounding noise (the rounded weights
-// float(1/9), float(4/9), float(1/36) all err upwards and would otherwise
-// create about 7e-9 of mass per step at tau = 1).
+// f^eq_0 = rho - sum_{i>0} f^eq_i (equal to w_0 rho (...) in exact arithmetic;
+// the rounded weights float(1/9), float(4/9), float(1/36) all err upwards and
+// would otherwise create about 7e-9 of mass per step at tau = 1), and that
+// closure is evaluated as f^eq_0 - f_0 = -sum_{i>0} (f^eq_i - f_i), with
+// rho = sum_i f_i: the rest population relaxes by minus the sum of the very
+// increments the moving ones receive, so the collision conserves mass up to
+// the roundings of that short sum of non-equilibrium parts (a few ulp of
+// |f^eq - f|, not of rho) and of the final updates.  Summing rho and
+// sum_{i>0} f^eq_i separately instead rounds both at the scale of rho; at
+// nodes that repeat the same values those roundings do not average out, and a
+// 20000-step FP32 drop drifts in mass by several 1e-6.
 #pragma once
 
 #include "sc_common.cuh"
 
 namespace lbmsc {
 
-// rho = (f_1 + f_2 + ... + f_{Q-1}) + f_0: the moving populations summed in
-// the order the collision sums their equilibria (the closure of f^eq_0 below),
-// the rest population last.  In a steady uniform region the pulled f_i (i > 0)
-// are the equilibria of the previous step, so both running sums round alike
-// and the collision conserves the FP32 mass exactly there; summing from f_0
-// instead leaves a fixed rounding difference at every such node, which a
-// 20000-step FP32 run accumulates into a mass drift of several 1e-6.
+// rho = (f_1 + f_2 + ... + f_{Q-1}) + f_0, the moving populations first and
+// the rest population last, in one fixed order.  rho enters the equilibria
+// and the velocity; the closure of f^eq_0 below does not round through it.
 template <class L, class C> __device__ __forceinline__ C node_density(const C (&f)[L::Q]) {
     C r = f[1];
 #pragma unroll
@@ -158,22 +161,23 @@ template <class L, class C> __device__ __forceinline__ C node_cu(int i, const C 
 
 // BGK relaxation of one species towards f^eq(rho, u), each moving population
 // relaxed as soon as its equilibrium is formed (fewer live values), the rest
-// population last from the closure f^eq_0 = rho - sum_{i>0} f^eq_i.
+// population last from the closure f^eq_0 = rho - sum_{i>0} f^eq_i, taken as
+// f^eq_0 - f_0 = -sum_{i>0} (f^eq_i - f_i).
 template <class L, class C> __device__ __forceinline__ void node_relax(C (&f)[L::Q], C rho, const C (&u)[3], C omega) {
     using A = Ar<C>;
     C uu = L::D == 3 ? A::fma(u[0], u[0], A::fma(u[1], u[1], A::mul(u[2], u[2]))) : A::fma(u[0], u[0], A::mul(u[1], u[1]));
     const C base = A::fma((C)-1.5, uu, (C)1);
-    SignedSum<C> moved;
+    SignedSum<C> neq;  // sum_{i>0} (f^eq_i - f_i)
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
         const C cu = node_cu<L, C>(i, u);
         const C wr = A::mul((C)L::w(i), rho);
         const C feq = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
-        moved.add(feq);
-        f[i] = A::fma(omega, A::sub(feq, f[i]), f[i]);
+        const C d = A::sub(feq, f[i]);
+        neq.add(d);
+        f[i] = A::fma(omega, d, f[i]);
     }
-    const C feq0 = A::sub(rho, moved.get());
-    f[0] = A::fma(omega, A::sub(feq0, f[0]), f[0]);
+    f[0] = A::fma(omega, -neq.get(), f[0]);  // f^eq_0 - f_0 = -sum_{i>0} (f^eq_i - f_i)
 }
 
 // Collision of both species of one node: common velocity shifted by tau_s g_s.
@@ -203,7 +207,7 @@ __device__ __forceinline__ void node_collide(C (&f)[2][L::Q], C rA, C rB, const 
 //   f_is += (1 / tau_s) (f^eq_i(rho_s, u_G) - f_is) + (1 - 1 / (2 tau_s)) S_is
 //   S_is = w_i [3 (c_i - u_G).F_s + 9 (c_i.u_G) (c_i.F_s)]
 // The source's rest component is closed as S_0 = -sum_{i>0} S_i (its sum over
-// i vanishes in exact arithmetic), like f^eq_0.  Opposite directions share
+// i vanishes in exact arithmetic), and f^eq_0 as in node_relax.  Opposite directions share
 // their terms: with t1 = 9 (c.u)(c.F) - 3 u.F and t2 = 3 c.F (c = c_i),
 // S_i = w_i (t1 + t2) and S_{i+1} = w_i (t1 - t2), since c_{i+1} = -c_i.
 template <class L, class C>
@@ -215,7 +219,7 @@ __device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)
     const C keep = A::fma((C)-0.5, omega, (C)1);  // 1 - 1 / (2 tau)
     const C m3uF = A::mul((C)-3, uF);
     static_assert(opposite_pairs<L>(), "velocity order must pair c_{i+1} = -c_i");
-    SignedSum<C> moved, sources;
+    SignedSum<C> neq, sources;
 #pragma unroll
     for (int i = 1; i < L::Q; i += 2) {
         const C cu = node_cu<L, C>(i, u);  // c_{i+1}.u = -cu exactly (a signed sum of the same terms)
@@ -224,20 +228,21 @@ __device__ __forceinline__ void node_relax_guo(C (&f)[L::Q], C rho, const C (&u)
         const C wr = A::mul(w, rho);
         const C feq_p = A::mul(wr, A::fma(cu, A::fma((C)4.5, cu, (C)3), base));
         const C feq_m = A::mul(wr, A::fma(-cu, A::fma((C)4.5, -cu, (C)3), base));
-        moved.add(feq_p);
-        moved.add(feq_m);
+        const C d_p = A::sub(feq_p, f[i]);
+        const C d_m = A::sub(feq_m, f[i + 1]);
+        neq.add(d_p);
+        neq.add(d_m);
         const C t1 = A::fma(A::mul((C)9, cu), cF, m3uF);
         const C t2 = A::mul((C)3, cF);
         const C src_p = A::mul(w, A::add(t1, t2));
         const C src_m = A::mul(w, A::sub(t1, t2));
         sources.add(src_p);
         sources.add(src_m);
-        f[i] = A::fma(keep, src_p, A::fma(omega, A::sub(feq_p, f[i]), f[i]));
-        f[i + 1] = A::fma(keep, src_m, A::fma(omega, A::sub(feq_m, f[i + 1]), f[i + 1]));
+        f[i] = A::fma(keep, src_p, A::fma(omega, d_p, f[i]));
+        f[i + 1] = A::fma(keep, src_m, A::fma(omega, d_m, f[i + 1]));
     }
-    const C feq0 = A::sub(rho, moved.get());
     const C src0 = -sources.get();
-    f[0] = A::fma(keep, src0, A::fma(omega, A::sub(feq0, f[0]), f[0]));
+    f[0] = A::fma(keep, src0, A::fma(omega, -neq.get(), f[0]));
 }
 
 template <class L, class C>
@@ -305,7 +310,8 @@ __device__ __forceinline__ double fe_log(double x) { return log(x); }
 //   g_i^eq = w_i [phi + 3 phi c.u + 9/2 ((Gamma mu - cs2 phi)(c.c - D cs2) + phi ((c.u)^2 - cs2 u.u))]
 // (the Hermite term (c_a c_b - cs2 d_ab) M_ab / (2 cs2^2) written out for the
 // isotropic-plus-dyadic M of each population), rest components closed as
-// rho - sum_{i>0} and phi - sum_{i>0}.  omega = 1/tau, omega_g = 1/tau_g.
+// rho - sum_{i>0} and phi - sum_{i>0} (each taken, as in node_relax, as minus
+// the sum of the moving populations' increments f^eq_i - f_i).  omega = 1/tau, omega_g = 1/tau_g.
 template <class L, class C>
 __device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, const C (&gp)[3], C lp, C omega,
                                                 C omega_g, C g, C kappa, C gamma) {
@@ -329,7 +335,7 @@ __device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, c
                        A::mul(cs2, rho));
     const C sg = A::sub(A::mul(gamma, mu), A::mul(cs2, phi));
     const C ku = A::mul(cs2, uu), kg = A::mul(cs2, gg);
-    SignedSum<C> fsum, gsum;
+    SignedSum<C> fneq, gneq;  // sum_{i>0} (f^eq_i - f_i), sum_{i>0} (g^eq_i - g_i)
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
         const C cu = node_cu<L, C>(i, u);
@@ -345,15 +351,15 @@ __device__ __forceinline__ void node_collide_fe(C (&f)[2][L::Q], C rho, C phi, c
         const C feq = A::mul(w, A::fma((C)4.5, hf, A::fma(A::mul((C)3, rho), cu, rho)));
         const C hg = A::fma(sg, iso, A::mul(phi, quad_u));
         const C geq = A::mul(w, A::fma((C)4.5, hg, A::fma(A::mul((C)3, phi), cu, phi)));
-        fsum.add(feq);
-        gsum.add(geq);
-        f[0][i] = A::fma(omega, A::sub(feq, f[0][i]), f[0][i]);
-        f[1][i] = A::fma(omega_g, A::sub(geq, f[1][i]), f[1][i]);
+        const C df = A::sub(feq, f[0][i]);
+        const C dg = A::sub(geq, f[1][i]);
+        fneq.add(df);
+        gneq.add(dg);
+        f[0][i] = A::fma(omega, df, f[0][i]);
+        f[1][i] = A::fma(omega_g, dg, f[1][i]);
     }
-    const C feq0 = A::sub(rho, fsum.get());
-    const C geq0 = A::sub(phi, gsum.get());
-    f[0][0] = A::fma(omega, A::sub(feq0, f[0][0]), f[0][0]);
-    f[1][0] = A::fma(omega_g, A::sub(geq0, f[1][0]), f[1][0]);
+    f[0][0] = A::fma(omega, -fneq.get(), f[0][0]);
+    f[1][0] = A::fma(omega_g, -gneq.get(), f[1][0]);
 }
 
 // The collision of the lattice's forcing scheme, chosen at run time (kernels
