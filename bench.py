@@ -672,11 +672,12 @@ def main():
         sb = lbm_sc.lbm_sc_host_staging_bytes(lat2.params)
         staging = torch.empty(sb + 256, dtype=torch.uint8, device="cuda")
         sp = (staging.data_ptr() + 255) // 256 * 256
+        # page-locked host buffers of the library's allocator (driver-allocated)
         tdt = torch.float64 if prec == "f64" else torch.float32
-        hA = torch.from_numpy(np.ascontiguousarray(rA).reshape(-1)).pin_memory()
-        hB = torch.from_numpy(np.ascontiguousarray(rB).reshape(-1)).pin_memory()
-        oA, oB, oP = (torch.empty(N, dtype=tdt).pin_memory() for _ in range(3))
-        oU = torch.empty(3 * N, dtype=tdt).pin_memory()
+        hbufs = [lbm_sc.HostBuffer(n, tdt) for n in (N, N, N, N, N, 3 * N)]
+        hA, hB, oA, oB, oP, oU = (b.tensor for b in hbufs)
+        hA.copy_(torch.from_numpy(np.ascontiguousarray(rA).reshape(-1)))
+        hB.copy_(torch.from_numpy(np.ascontiguousarray(rB).reshape(-1)))
         # untimed warm-up job (W steps): first touch of the pinned buffers and the copy path
         lbm_sc.lbm_sc_run_host(lat2.handle, sp, sb, hA.data_ptr(), hB.data_ptr(), None, args.warmup,
                                oA.data_ptr(), oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
@@ -715,10 +716,13 @@ def main():
                "seconds": e2e_s, "jobs_seconds": jobs, "link_gbs": {"h2d": h2d_gbs, "d2h": d2h_gbs},
                "floor_seconds": K * ms_per_step / 1e3 + copy_s,
                "note": "one job of %d steps through lbm_sc_run_host: H2D rho_A, rho_B; D2H rho_A, rho_B, u(3), p "
-                       "(copies overlapped with init and moments in z slabs), the median of three jobs; "
+                       "(copies overlapped with init and moments in z slabs; host buffers of lbm_sc_host_alloc), "
+                       "the median of three jobs; "
                        "bytes per step = job bytes / steps; "
                        "floor = the steps alone + every copy at the measured link rate, unoverlapped" % K}
         del staging, hA, hB, oA, oB, oP, oU, lat2
+        for b in hbufs:
+            b.close()
 
     bt = None
     del lat

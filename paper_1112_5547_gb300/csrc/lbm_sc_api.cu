@@ -1,6 +1,8 @@
 // C-ABI of the GB300 Shan-Chen lattice Boltzmann library (declared in
 // include/lbm_sc.h).  Host code only: validation, workspace carving, stream
 // handling and dispatch to the per-lattice launchers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -352,6 +354,120 @@ void io_release(lbm_sc_handle* h) {
 }
 
 }  // namespace
+
+namespace {
+
+// Driver calls of lbm_sc_host_alloc's virtual-memory allocation, reached through
+// the runtime's driver entry points (no link against the driver library).
+struct HostVmm {
+    PFN_cuMemGetAllocationGranularity_v10020 granularity = nullptr;
+    PFN_cuMemCreate_v10020 create = nullptr;
+    PFN_cuMemRelease_v10020 release = nullptr;
+    PFN_cuMemAddressReserve_v10020 reserve = nullptr;
+    PFN_cuMemAddressFree_v10020 address_free = nullptr;
+    PFN_cuMemMap_v10020 map = nullptr;
+    PFN_cuMemUnmap_v10020 unmap = nullptr;
+    PFN_cuMemSetAccess_v10020 set_access = nullptr;
+    bool ok = false;
+};
+
+void* driver_entry(const char* name) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+        return nullptr;
+    return ptr;
+}
+
+const HostVmm& host_vmm() {
+    static const HostVmm v = [] {
+        HostVmm t;
+        t.granularity = (PFN_cuMemGetAllocationGranularity_v10020)driver_entry("cuMemGetAllocationGranularity");
+        t.create = (PFN_cuMemCreate_v10020)driver_entry("cuMemCreate");
+        t.release = (PFN_cuMemRelease_v10020)driver_entry("cuMemRelease");
+        t.reserve = (PFN_cuMemAddressReserve_v10020)driver_entry("cuMemAddressReserve");
+        t.address_free = (PFN_cuMemAddressFree_v10020)driver_entry("cuMemAddressFree");
+        t.map = (PFN_cuMemMap_v10020)driver_entry("cuMemMap");
+        t.unmap = (PFN_cuMemUnmap_v10020)driver_entry("cuMemUnmap");
+        t.set_access = (PFN_cuMemSetAccess_v10020)driver_entry("cuMemSetAccess");
+        t.ok = t.granularity && t.create && t.release && t.reserve && t.address_free && t.map && t.unmap &&
+               t.set_access;
+        return t;
+    }();
+    return v;
+}
+
+// Pinned host memory on the host NUMA node nearest the current device (node 0
+// where the system has no NUMA), and the mapping size of a buffer of `bytes`
+// (whole allocation granules).
+bool host_prop(CUmemAllocationProp& prop, int& device, size_t bytes, size_t& size) {
+    const HostVmm& v = host_vmm();
+    if (!v.ok || cudaFree(nullptr) != cudaSuccess || cudaGetDevice(&device) != cudaSuccess) return false;
+    int numa = -1;
+    if (cudaDeviceGetAttribute(&numa, cudaDevAttrHostNumaId, device) != cudaSuccess || numa < 0) numa = 0;
+    memset(&prop, 0, sizeof(prop));
+    prop.type = CU_MEM_ALLOCATION_TYPE_PINNED;
+    prop.location.type = CU_MEM_LOCATION_TYPE_HOST_NUMA;
+    prop.location.id = numa;
+    size_t gran = 0;
+    if (v.granularity(&gran, &prop, CU_MEM_ALLOC_GRANULARITY_RECOMMENDED) != CUDA_SUCCESS || gran == 0) return false;
+    if (bytes > SIZE_MAX - gran) return false;
+    size = (bytes + gran - 1) / gran * gran;
+    return true;
+}
+
+}  // namespace
+
+lbm_status lbm_sc_host_alloc(size_t bytes, void** out) {
+    if (!out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (bytes == 0) return LBM_ERR_INVALID_ARG;
+    CUmemAllocationProp prop;
+    int device = 0;
+    size_t size = 0;
+    if (!host_prop(prop, device, bytes, size)) return LBM_ERR_CUDA;
+    const HostVmm& v = host_vmm();
+    CUmemGenericAllocationHandle handle;
+    const CUresult cr = v.create(&handle, size, &prop, 0);
+    if (cr != CUDA_SUCCESS) return cr == CUDA_ERROR_OUT_OF_MEMORY ? LBM_ERR_OUT_OF_MEMORY : LBM_ERR_CUDA;
+    CUdeviceptr va = 0;
+    if (v.reserve(&va, size, 0, 0, 0) != CUDA_SUCCESS) {
+        v.release(handle);
+        return LBM_ERR_CUDA;
+    }
+    const bool mapped = v.map(va, size, 0, handle, 0) == CUDA_SUCCESS;
+    v.release(handle);  // the mapping keeps the memory until it is unmapped
+    CUmemAccessDesc access[2];
+    memset(access, 0, sizeof(access));
+    access[0].location.type = CU_MEM_LOCATION_TYPE_DEVICE;
+    access[0].location.id = device;
+    access[0].flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+    access[1].location = prop.location;
+    access[1].flags = CU_MEM_ACCESS_FLAGS_PROT_READWRITE;
+    if (!mapped || v.set_access(va, size, access, 2) != CUDA_SUCCESS) {
+        if (mapped) v.unmap(va, size);
+        v.address_free(va, size);
+        return LBM_ERR_CUDA;
+    }
+    memset(reinterpret_cast<void*>(va), 0, size);
+    *out = reinterpret_cast<void*>(va);
+    return LBM_OK;
+}
+
+lbm_status lbm_sc_host_free(void* p, size_t bytes) {
+    if (!p) return LBM_OK;
+    if (bytes == 0) return LBM_ERR_INVALID_ARG;
+    CUmemAllocationProp prop;
+    int device = 0;
+    size_t size = 0;
+    if (!host_prop(prop, device, bytes, size)) return LBM_ERR_CUDA;
+    const HostVmm& v = host_vmm();
+    const CUdeviceptr va = reinterpret_cast<CUdeviceptr>(p);
+    const bool unmapped = v.unmap(va, size) == CUDA_SUCCESS;
+    const bool freed = v.address_free(va, size) == CUDA_SUCCESS;
+    return unmapped && freed ? LBM_OK : LBM_ERR_CUDA;
+}
 
 lbm_status lbm_sc_run_host(lbm_sc_handle* h, void* d_staging, size_t staging_bytes, const void* h_rhoA,
                            const void* h_rhoB, const void* h_u, int nsteps, void* h_rhoA_out, void* h_rhoB_out,

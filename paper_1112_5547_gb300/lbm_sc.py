@@ -52,7 +52,7 @@ EXPORTS = (
     "lbm_sc_moments", "lbm_sc_diagnostics", "lbm_sc_host_staging_bytes", "lbm_sc_run_host", "lbm_sc_layout",
     "lbm_sc_destroy", "lbm_sc_status_string", "lbm_sc_set_tuning", "lbm_sc_get_tuning",
     "lbm_sc_diagnostics_noalloc", "lbm_sc_batch_workspace_bytes", "lbm_sc_batch_create", "lbm_sc_batch_step",
-    "lbm_sc_batch_destroy", "lbm_sc_set_wait_probe", "lbm_sc_error_word",
+    "lbm_sc_batch_destroy", "lbm_sc_set_wait_probe", "lbm_sc_error_word", "lbm_sc_host_alloc", "lbm_sc_host_free",
 )
 
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
@@ -209,6 +209,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_sc_host_staging_bytes.argtypes = [P]
     lib.lbm_sc_host_staging_bytes.restype = ctypes.c_size_t
     lib.lbm_sc_run_host.argtypes = [vp, vp, ctypes.c_size_t, vp, vp, vp, ctypes.c_int, vp, vp, vp, vp]
+    lib.lbm_sc_host_alloc.argtypes = [ctypes.c_size_t, ctypes.POINTER(vp)]
+    lib.lbm_sc_host_free.argtypes = [vp, ctypes.c_size_t]
     ip = ctypes.POINTER(ctypes.c_int)
     lib.lbm_sc_layout.argtypes = [vp, ip, ip, ip, ip, ip, ip, ctypes.POINTER(vp)]
     lib.lbm_sc_set_tuning.argtypes = [vp, ctypes.POINTER(lbm_sc_tuning)]
@@ -234,7 +236,7 @@ def load(path: str = LIB_PATH):
     for name in ("lbm_sc_create", "lbm_sc_set_stream", "lbm_sc_init_fields", "lbm_sc_step", "lbm_sc_moments",
                  "lbm_sc_diagnostics", "lbm_sc_run_host", "lbm_sc_layout", "lbm_sc_set_tuning",
                  "lbm_sc_get_tuning", "lbm_sc_batch_create", "lbm_sc_batch_step", "lbm_sc_set_wait_probe",
-                 "lbm_sc_error_word"):
+                 "lbm_sc_error_word", "lbm_sc_host_alloc", "lbm_sc_host_free"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -321,6 +323,43 @@ def lbm_sc_run_host(h: int, d_staging: int, staging_bytes: int, h_rhoA: int, h_r
     _check(load().lbm_sc_run_host(v(h), v(d_staging), ctypes.c_size_t(staging_bytes), v(h_rhoA), v(h_rhoB),
                                   v(h_u or 0), int(nsteps), v(h_rhoA_out or 0), v(h_rhoB_out or 0), v(h_u_out or 0),
                                   v(h_p_out or 0)), "lbm_sc_run_host")
+
+
+def lbm_sc_host_alloc(nbytes: int) -> int:
+    """Address of a driver-allocated, page-locked host buffer of nbytes (release with lbm_sc_host_free)."""
+    p = ctypes.c_void_p()
+    _check(load().lbm_sc_host_alloc(ctypes.c_size_t(nbytes), ctypes.byref(p)), "lbm_sc_host_alloc")
+    return p.value
+
+
+def lbm_sc_host_free(p: int, nbytes: int) -> None:
+    _check(load().lbm_sc_host_free(ctypes.c_void_p(p), ctypes.c_size_t(nbytes)), "lbm_sc_host_free")
+
+
+class HostBuffer:
+    """A buffer of lbm_sc_host_alloc seen as a CPU torch tensor of `count` values
+    of `dtype` (``.tensor``); freed by close() or when the object goes away (the
+    tensor must not outlive it)."""
+
+    def __init__(self, count: int, dtype=None):
+        import torch
+        dtype = dtype or torch.float32
+        self.nbytes = int(count) * torch.empty((), dtype=dtype).element_size()
+        self.ptr = lbm_sc_host_alloc(max(self.nbytes, 1))
+        raw = (ctypes.c_uint8 * self.nbytes).from_address(self.ptr)
+        self.tensor = torch.frombuffer(raw, dtype=dtype, count=int(count)) if count else torch.empty(0, dtype=dtype)
+
+    def close(self) -> None:
+        if self.ptr:
+            self.tensor = None
+            lbm_sc_host_free(self.ptr, max(self.nbytes, 1))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lbm_sc_layout(h: int):

@@ -187,6 +187,19 @@ def test_status_strings(lib):
     assert "unknown" in lib.lbm_sc_status_string(99)
 
 
+def test_host_alloc_argument_checks_without_touching_the_gpu(lib):
+    """lbm_sc_host_alloc rejects a zero size or a NULL out pointer (and leaves *out
+    NULL), lbm_sc_host_free of NULL is a no-op and of a zero size is rejected;
+    none of these reaches a CUDA call."""
+    so = lib.load()
+    out = ctypes.c_void_p(1234)
+    assert so.lbm_sc_host_alloc(ctypes.c_size_t(0), ctypes.byref(out)) == lib.LBM_ERR_INVALID_ARG
+    assert out.value is None
+    assert so.lbm_sc_host_alloc(ctypes.c_size_t(4096), None) == lib.LBM_ERR_INVALID_ARG
+    assert so.lbm_sc_host_free(None, ctypes.c_size_t(4096)) == lib.LBM_OK
+    assert so.lbm_sc_host_free(ctypes.c_void_p(4096), ctypes.c_size_t(0)) == lib.LBM_ERR_INVALID_ARG
+
+
 def test_batch_workspace_and_validation(lib):
     """Batch sizing counts one descriptor per lattice and one 16-byte item per
     (x tile, y tile, z chunk); mixed lattice kinds or precisions, unknown tiles,

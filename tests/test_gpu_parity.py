@@ -205,6 +205,38 @@ def test_run_host_equals_device_path(sc, shape, with_u):
         assert np.array_equal(oP.numpy().reshape(shape), ref[3].astype(np.float32))
 
 
+def test_run_host_with_library_host_buffers(sc):
+    """lbm_sc_run_host on buffers of lbm_sc_host_alloc (driver-allocated, page-locked)
+    gives the device path's result bitwise; the buffers arrive zero-filled and are
+    usable to their last byte."""
+    import torch
+    shape = (72, 16, 40)
+    rA, rB = inputs.drop(shape, 6, seed=5, dtype=np.float32)
+    ref = _gpu_fields(sc.Lattice(1, shape, 1.0, 1.0, G0, "f32").init(rA, rB).step(12))
+    lat = sc.Lattice(1, shape, 1.0, 1.0, G0, "f32")
+    nbytes = sc.lbm_sc_host_staging_bytes(lat.params)
+    staging = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    sp = (staging.data_ptr() + 255) // 256 * 256
+    N = rA.size
+    bufs = [sc.HostBuffer(n) for n in (N, N, N, N, 3 * N, N)]
+    hA, hB, oA, oB, oU, oP = (b.tensor for b in bufs)
+    assert all(not t.any() for t in (hA, oU))
+    hA.copy_(torch.from_numpy(rA.reshape(-1)))
+    hB.copy_(torch.from_numpy(rB.reshape(-1)))
+    sc.lbm_sc_run_host(lat.handle, sp, nbytes, hA.data_ptr(), hB.data_ptr(), None, 12, oA.data_ptr(),
+                       oB.data_ptr(), oU.data_ptr(), oP.data_ptr())
+    assert np.array_equal(oA.numpy().reshape(shape), ref[0].astype(np.float32))
+    assert np.array_equal(oB.numpy().reshape(shape), ref[1].astype(np.float32))
+    assert np.array_equal(oU.numpy().reshape(3, -1).T.reshape(shape + (3,)), ref[2].astype(np.float32))
+    assert np.array_equal(oP.numpy().reshape(shape), ref[3].astype(np.float32))
+    for b in bufs:
+        b.close()
+    big = sc.HostBuffer(3 * N + 5)  # not a whole number of granules
+    big.tensor[-1] = 2.0
+    assert big.tensor[-1] == 2.0 and not big.tensor[:-1].any()
+    big.close()
+
+
 def test_unstable_state_reported(sc):
     """A negative density in the initial fields is reported as LBM_ERR_UNSTABLE."""
     shape = (8, 8)
