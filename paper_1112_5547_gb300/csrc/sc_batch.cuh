@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(TX* TY, 1)
     // drift apart and lose the halo rows they share in L2).
     int nit = 0;
     BatchItem wn{0, 0, 0, 0};
-    TmaNext nxt{nullptr, 0, 0, 0, 0, 0, 0, 0};
+    TmaNext nxt{nullptr, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll 1
     for (;;) {
         const int it = s_next;
@@ -212,11 +212,12 @@ __global__ void __launch_bounds__(TX* TY, 1)
                     nxt.gyo = an.gyo;
                     nxt.nz = an.nz;
                     nxt.nplanes = min(wn.z0 + an.zchunk, an.nz) - wn.z0 + 2;
+                    nxt.down = tma_march_down(wn.z0, an.zchunk);
                 }
             }
         };
         const int n = tma_item<TX, TY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, qbase, sm, l->err,
-                                          preissued, &nxt, hook);
+                                          preissued, &nxt, hook, true);
         if (n < 0) break;  // a lost wait: the lattice's error word is raised
         qbase += (unsigned)n;
         // the next item's first planes went out with this one (the elected
@@ -246,11 +247,13 @@ __global__ void __launch_bounds__(WX* WY, 1)
     if (l->wide) {
         TmaSmem<WX, WY, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<WX, WY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<WX, WY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false, nullptr,
+                            TmaNoHook(), true);
     } else {
         TmaSmem<NX, NY, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<NX, NY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<NX, NY, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false, nullptr,
+                            TmaNoHook(), true);
     }
 }
 
@@ -274,15 +277,18 @@ __global__ void __launch_bounds__(384, 1)
     if (l->wide == 1) {
         TmaSmem<64, 6, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<64, 6, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<64, 6, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false, nullptr,
+                           TmaNoHook(), true);
     } else if (l->wide == 2) {
         TmaSmem<48, 8, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<48, 8, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<48, 8, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false, nullptr,
+                           TmaNoHook(), true);
     } else {
         TmaSmem<32, 12, S> sm(smem_raw);
         sm.init_barriers();
-        tma_item<32, 12, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err);
+        tma_item<32, 12, S>(&l->map[parity], nullptr, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false, nullptr,
+                            TmaNoHook(), true);
     }
 }
 

@@ -132,18 +132,15 @@ template <int TX, int TY, int S, class St = float> struct TmaSmem {
     }
 };
 
-// The copies of plane q of a work item (tile x0, y0; planes z0 - 1 .. z1 of
-// its chunk) into the stage of pipeline slot g: 38 population boxes, one per
-// species and direction (19 paired boxes and 3 density boxes for rest-offset
-// storage), completing on the slot's mbarrier.  Elected thread only.
+// The copies of plane z (0 <= z < nz) of a work item (tile x0, y0) into the
+// stage of pipeline slot g: 38 population boxes, one per species and
+// direction (19 paired boxes and 3 density boxes for rest-offset storage),
+// completing on the slot's mbarrier.  Elected thread only.
 template <int TX, int TY, int S, class St>
-__device__ __forceinline__ void tma_issue_plane(const CUtensorMap* pmap, const CUtensorMap* rmap, int x0, int y0, int z0,
-                                                int gxo, int gyo, int nz, int q, unsigned g,
-                                                const TmaSmem<TX, TY, S, St>& sm) {
+__device__ __forceinline__ void tma_issue_plane(const CUtensorMap* pmap, const CUtensorMap* rmap, int x0, int y0, int z,
+                                                int gxo, int gyo, int nz, unsigned g, const TmaSmem<TX, TY, S, St>& sm) {
     using L = D3Q19;
     using T = TmaTile<TX, TY, S, St>;
-    int z = z0 - 1 + q;
-    z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
     const unsigned st = g % S;
     mbar_arrive_expect_tx(&sm.bars[st], T::tx_bytes);
     unsigned char* sb = sm.stage + (size_t)st * T::stage_bytes;
@@ -235,7 +232,28 @@ __device__ __forceinline__ float tma_density(const unsigned char* sb, int s, int
 struct TmaNext {
     const CUtensorMap* map;
     int x0, y0, z0, gxo, gyo, nz, nplanes;  // nplanes = 0: no next item
+    int down;                               // the item marches down (tma_march_down)
 };
+
+// In the batch kernels the z chunks of a lattice march in alternating
+// directions: chunk k = z0 / zchunk upwards (planes z0 - 1, z0, ..., z1) if k
+// is even, downwards (z1, z1 - 1, ..., z0 - 1) if k is odd.  Two neighbouring
+// chunks then reach the planes they both read (each one's boundary planes,
+// z0 - 1 and z1) at the same time when they run together, at the start of
+// both or at the end of both, instead of one at its start and the other at
+// its end.  A batch's work list places a lattice's chunks a few dozen items
+// apart, so they do run together (ragged 64-lattice set: 12.85 -> 13.05
+// GLUPS, 96^3 lattices 12.5 -> 13.0); the solo grid launches the chunks of a
+// plane of tiles hundreds of CTAs apart, and there the alternation measured
+// 0.2 - 0.9 % slower, so the solo kernel marches every chunk upwards.
+__device__ __forceinline__ bool tma_march_down(int z0, int zchunk) { return ((z0 / zchunk) & 1) != 0; }
+
+// Plane of pipeline step q (0 .. nplanes - 1) of an item of planes z0 .. z0 +
+// nplanes - 3 (periodic in nz).
+__device__ __forceinline__ int tma_plane(int z0, int nplanes, int nz, bool down, int q) {
+    const int z = down ? z0 + nplanes - 2 - q : z0 - 1 + q;
+    return z < 0 ? z + nz : (z >= nz ? z - nz : z);
+}
 
 // Called by the elected thread at the start of every plane of an item (plane
 // q of nplanes); the persistent batch kernel uses it to take its next work
@@ -252,11 +270,12 @@ struct TmaNoHook {
 // planes the item used, or -1 if a wait was lost (the error word is then
 // raised, and the copies still in flight have been waited for, again with a
 // bound).  The caller must synchronise the CTA between two items.
+// alternate: odd chunks march downwards (tma_march_down; batch kernels).
 template <int TX, int TY, int S, class St = float, class Hook = TmaNoHook, int FORCING = kForcingShift>
 __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorMap* rmap, const LatticeArgs<St>& a,
                                         int x0, int y0, int z0, unsigned qbase, const TmaSmem<TX, TY, S, St>& sm,
                                         int* __restrict__ err, bool preissued = false, const TmaNext* nxt = nullptr,
-                                        Hook hook = Hook()) {
+                                        Hook hook = Hook(), bool alternate = false) {
     using L = D3Q19;
     using T = TmaTile<TX, TY, S, St>;
     using C = float;
@@ -296,15 +315,13 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
     int hfx, hfy;
     halo_cell<TX, TY>(halo ? (kSplit ? hid >> 1 : hid) : 0, hfx, hfy);
 
-    auto zof = [&](int q) {
-        const int z = z0 - 1 + q;
-        return z < 0 ? z + nz : (z >= nz ? z - nz : z);
-    };
+    const bool down = alternate && tma_march_down(z0, a.zchunk);
+    auto zof = [&](int q) { return tma_plane(z0, nplanes, nz, down, q); };
     // elected thread: the boxes of plane q into its stage.  (Spreading the 38
     // copy instructions over the lanes of a warp measured 1.8x slower.)
     auto issue = [&](int q) {
         fence_proxy_async_smem();  // earlier generic reads of the stage precede the async refill
-        tma_issue_plane<TX, TY, S, St>(pmap, rmap, x0, y0, z0, a.gxo, a.gyo, nz, q, qbase + q, sm);
+        tma_issue_plane<TX, TY, S, St>(pmap, rmap, x0, y0, zof(q), a.gxo, a.gyo, nz, qbase + q, sm);
     };
     const bool issuer = tid == 0;
     auto try_plane = [&](int q) {
@@ -354,7 +371,8 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
         }
     };
     auto collide = [&](int q, C (&X)[2][Q]) {
-        const int sm_ = (q - 1) & 3, sc = q & 3, sp = (q + 1) & 3;
+        // ring slots of the planes z - 1, z, z + 1 (steps q - 1 and q + 1 swap roles downwards)
+        const int sc = q & 3, sm_ = (down ? q + 1 : q - 1) & 3, sp = (down ? q - 1 : q + 1) & 3;
         const C rA = ring[sc][0][ty + 1][tx + 1];
         const C rB = ring[sc][1][ty + 1][tx + 1];
         auto nbr = [&](int s, int i) -> C {
@@ -388,8 +406,9 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
                 issue(r);
             } else if (nxt && r - nplanes < nxt->nplanes) {
                 fence_proxy_async_smem();
-                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0, nxt->z0, nxt->gxo, nxt->gyo, nxt->nz,
-                                               r - nplanes, qbase + r, sm);
+                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0,
+                                               tma_plane(nxt->z0, nxt->nplanes, nxt->nz, nxt->down != 0, r - nplanes),
+                                               nxt->gxo, nxt->gyo, nxt->nz, qbase + r, sm);
             }
         }
         if (q == 0 && a.wait_probe > 0 && issuer && x0 == 0 && y0 == 0 && z0 == 0) {
@@ -425,8 +444,9 @@ __device__ __forceinline__ int tma_item(const CUtensorMap* pmap, const CUtensorM
                 issue(r);
             } else if (nxt && r - nplanes < nxt->nplanes) {
                 fence_proxy_async_smem();
-                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0, nxt->z0, nxt->gxo, nxt->gyo, nxt->nz,
-                                               r - nplanes, qbase + r, sm);
+                tma_issue_plane<TX, TY, S, St>(nxt->map, nullptr, nxt->x0, nxt->y0,
+                                               tma_plane(nxt->z0, nxt->nplanes, nxt->nz, nxt->down != 0, r - nplanes),
+                                               nxt->gxo, nxt->gyo, nxt->nz, qbase + r, sm);
             }
         }
         if (q >= 2) collide(q - 1, Xp);
