@@ -20,7 +20,9 @@
  *   - The caller owns all device memory and the CUDA stream.  The library never
  *     allocates or frees device memory and never synchronises the device, except
  *     where an entry point says it does (lbm_sc_diagnostics, lbm_sc_run_host).
- *     lbm_sc_create allocates only the small host-side handle (malloc).
+ *     lbm_sc_create allocates only the small host-side handle (malloc);
+ *     lbm_sc_host_alloc / lbm_sc_host_free allocate and free pinned HOST memory
+ *     through the driver (their mapping calls are synchronous driver calls).
  *   - "Device pointer" arguments must be device (or managed) memory on the
  *     current device; "host pointer" arguments ordinary host memory (pinned
  *     memory makes the copies asynchronous-capable and faster).
