@@ -290,12 +290,12 @@ class Server:
                     for b in batches.values():
                         b.close()
                     batches = {}
-                    for kind in (lbm_sc.LBM_D2Q9, lbm_sc.LBM_D3Q19):
-                        lats = [s.lat for s in resident if s.req.lattice == kind]
-                        if lats:
-                            tile, zc = self.batch_shape(lats)
-                            batches[kind] = lbm_sc.Batch(lats, tile=tile, zchunk=zc, graph_steps=self.graph_steps,
-                                                         stream=self.stream)
+                    # one batch per lattice kind and storage precision (a batch holds one of each)
+                    for key in sorted({(s.req.lattice, s.req.precision) for s in resident}):
+                        lats = [s.lat for s in resident if (s.req.lattice, s.req.precision) == key]
+                        tile, zc = self.batch_shape(lats)
+                        batches[key] = lbm_sc.Batch(lats, tile=tile, zchunk=zc, graph_steps=self.graph_steps,
+                                                    stream=self.stream)
                     rebuilds += 1
                     dirty = False
                 for b in batches.values():

@@ -48,6 +48,23 @@ def test_drops_and_interfaces_served_equal_alone(sv):
         assert res[r.rid].steps == alone.steps and np.array_equal(res[r.rid].rhoA, alone.rhoA), r.rid
 
 
+def test_mixed_storage_precisions_served_equal_alone(sv):
+    """Requests that store their populations in FP32, bf16 rest-offset or fp16
+    rest-offset words arrive in one stream: the server steps each lattice kind
+    and storage precision as its own batch, and each result (field and step
+    count) is the same served in the mix as solved alone."""
+    import dataclasses
+    precs = ("f32", "bf16_rest", "f16_rest")
+    reqs = [dataclasses.replace(r, precision=precs[r.rid % 3]) for r in _small_requests(sv, n=9, seed=21)]
+    assert {r.precision for r in reqs} == set(precs)
+    srv = sv.Server(hbm_budget=80e9, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+    res, st = srv.run(reqs)
+    assert len(res) == len(reqs) and st.max_resident >= 2
+    for r in reqs:
+        alone, _ = sv.solve_alone(r, chunk=100, check_every=500, max_steps=1500, keep_fields=True)
+        assert res[r.rid].steps == alone.steps and np.array_equal(res[r.rid].rhoA, alone.rhoA), (r.rid, r.precision)
+
+
 def test_admission_respects_budget(sv):
     """A budget that holds only two of these lattices: at most two are resident,
     the rest wait, and every request still finishes with its own result."""
