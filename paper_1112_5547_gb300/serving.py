@@ -36,7 +36,16 @@ DIAG_DOUBLES = ctypes.sizeof(lbm_sc.lbm_sc_diag) // 8
 
 def max_speed_of(row) -> float:
     """max|u_phys| of one lbm_sc_diag record held as DIAG_DOUBLES doubles."""
-    return float(lbm_sc.lbm_sc_diag.from_buffer_copy(np.ascontiguousarray(row, dtype=np.float64).tobytes()).max_speed)
+    return check_of(row)[0]
+
+
+def check_of(row):
+    """(max|u_phys|, unstable) of one lbm_sc_diag record held as DIAG_DOUBLES
+    doubles; unstable: a non-finite value, or a species density that is no
+    longer positive anywhere (the state the diagnostics call LBM_ERR_UNSTABLE)."""
+    d = lbm_sc.lbm_sc_diag.from_buffer_copy(np.ascontiguousarray(row, dtype=np.float64).tobytes())
+    unstable = d.nonfinite > 0 or not (d.min_rho_A > 0 and d.min_rho_B > 0)
+    return float(d.max_speed), bool(unstable)
 
 
 @dataclass
@@ -109,6 +118,7 @@ class Result:
     done: float
     umax: float
     rhoA: Optional[np.ndarray] = None
+    unstable: bool = False  # retired at a check that saw a non-positive density or a non-finite value
 
     @property
     def latency(self) -> float:
@@ -214,8 +224,8 @@ class Server:
                 return tile, 16
         return 1, 0
 
-    def _check(self, slots: List[_Slot]) -> List[float]:
-        """max|u_phys| of each slot's current state, one synchronisation for all."""
+    def _check(self, slots: List[_Slot]):
+        """(max|u_phys|, unstable) of each slot's current state, one synchronisation for all."""
         torch = self.torch
         n = len(slots)
         width = DIAG_DOUBLES
@@ -227,7 +237,7 @@ class Server:
             lbm_sc.lbm_sc_diagnostics_noalloc(s.lat.params, ptr, None, self._diag[k].data_ptr(),
                                               self.stream.cuda_stream)
         host = self._diag[:n].cpu().numpy()  # on the current stream, which is self.stream
-        return [max_speed_of(host[k]) for k in range(n)]
+        return [check_of(host[k]) for k in range(n)]
 
     def _admit(self, req: Request, f, now: float) -> _Slot:
         with self.torch.cuda.stream(self.stream):
@@ -236,7 +246,7 @@ class Server:
             lat.init(f[0], f[1])
         return _Slot(req, lat, lat.workspace_bytes + self.batch_share(req), now)
 
-    def _retire(self, s: _Slot, now, converged: bool, umax: float) -> Result:
+    def _retire(self, s: _Slot, now, converged: bool, umax: float, unstable: bool = False) -> Result:
         """Copy the result (the density field of component A) to host memory,
         release the lattice; ``now()`` after the copy is the completion time."""
         with self.torch.cuda.stream(self.stream):
@@ -244,7 +254,7 @@ class Server:
         done = now()
         s.lat.close()
         return Result(s.req.rid, s.req.nodes, s.steps, converged, s.req.arrival, s.admitted, done, umax,
-                      rho if self.keep_fields else None)
+                      rho if self.keep_fields else None, unstable)
 
     # -- the serving loop ----------------------------------------------------
     def run(self, requests: List[Request], clock=time.perf_counter):
@@ -306,11 +316,12 @@ class Server:
                     lu += float(s.req.nodes) * self.chunk
                 due = [s for s in resident if s.steps % self.check_every == 0]
                 if due:
-                    umax = self._check(due)
-                    for s, u in zip(due, umax):
-                        conv = s.last_umax is not None and abs(u - s.last_umax) < self.tol * max(s.last_umax, 1e-300)
-                        if conv or s.steps >= self.max_steps:
-                            results.append(self._retire(s, lambda: clock() - t0, conv, u))
+                    checks = self._check(due)
+                    for s, (u, bad) in zip(due, checks):
+                        conv = (not bad and s.last_umax is not None
+                                and abs(u - s.last_umax) < self.tol * max(s.last_umax, 1e-300))
+                        if conv or bad or s.steps >= self.max_steps:
+                            results.append(self._retire(s, lambda: clock() - t0, conv, u, bad))
                             resident.remove(s)
                             used -= s.nbytes
                             dirty = True
@@ -338,7 +349,7 @@ def solve_alone(req: Request, chunk: int = 100, check_every: int = 500, tol: flo
         t0 = clock()
         lat = lbm_sc.Lattice(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision, stream=stream)
         lat.init(f[0], f[1])
-        steps, last, conv, u = 0, None, False, float("nan")
+        steps, last, conv, bad, u = 0, None, False, False, float("nan")
         diag = torch.empty(DIAG_DOUBLES, dtype=torch.float64, device="cuda")
         while True:
             lat.step(chunk)
@@ -346,15 +357,15 @@ def solve_alone(req: Request, chunk: int = 100, check_every: int = 500, tol: flo
             if steps % check_every == 0:
                 eb, q, px, py, gx, gy, ptr = lbm_sc.lbm_sc_layout(lat.handle)
                 lbm_sc.lbm_sc_diagnostics_noalloc(lat.params, ptr, None, diag.data_ptr(), stream.cuda_stream)
-                u = max_speed_of(diag.cpu().numpy())
-                conv = last is not None and abs(u - last) < tol * max(last, 1e-300)
-                if conv or steps >= max_steps:
+                u, bad = check_of(diag.cpu().numpy())
+                conv = not bad and last is not None and abs(u - last) < tol * max(last, 1e-300)
+                if conv or bad or steps >= max_steps:
                     break
                 last = u
         rho = lat.moments()[0].cpu().numpy()
         t1 = clock()
         lat.close()
-    return Result(req.rid, req.nodes, steps, conv, 0.0, 0.0, t1 - t0, u, rho if keep_fields else None), t1 - t0
+    return Result(req.rid, req.nodes, steps, conv, 0.0, 0.0, t1 - t0, u, rho if keep_fields else None, bad), t1 - t0
 
 
 def serial_baseline(requests: List[Request], **kw):
@@ -402,7 +413,8 @@ def main(argv=None):
                "max_active_nodes": cap, "order": order,
                "served_mlups": st.mlups, "wall_s": st.wall_s, "p50_s": st.p50_s, "p99_s": st.p99_s,
                "mean_s": st.mean_s, "max_resident": st.max_resident, "chunks": st.chunks, "rebuilds": st.rebuilds,
-               "converged": sum(r.converged for r in res), "steps_total": sum(r.steps for r in res),
+               "converged": sum(r.converged for r in res), "unstable": sum(r.unstable for r in res),
+               "steps_total": sum(r.steps for r in res),
                "lattice_updates": st.lattice_updates}
         if not a.no_serial:
             if serial is None:  # the same requests (arrival times do not matter one at a time)

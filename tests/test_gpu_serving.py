@@ -121,6 +121,6 @@ def test_diagnostics_check_of_65_slots_stays_in_its_rows(sv):
         got = srv._check(slots)
         srv.stream.synchronize()
     assert np.all(buf[n * w:].cpu().numpy() == guard)
-    for s, u in zip(slots, got):
-        assert u == s.lat.diagnostics()["max_speed"]
+    for s, (u, unstable) in zip(slots, got):
+        assert u == s.lat.diagnostics()["max_speed"] and not unstable
         s.lat.close()

@@ -83,3 +83,30 @@ def test_interface_requests():
     prof = rA.reshape(-1, L).mean(0)
     assert prof[d < r.R - 4].min() > 0.9 and prof[d > r.R + 4].max() < 0.1
     assert serving.Server.footprint(r) > 0
+
+
+def test_check_flags_non_positive_densities_and_non_finite_values():
+    """check_of reads max|u_phys| and the instability rule from one diagnostics
+    row: a species density that is zero or negative somewhere, or a non-finite
+    value, marks the request unstable (the server retires it at that check)."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1112_5547_gb300 import lbm_sc, serving
+
+    def row(**kw):
+        d = lbm_sc.lbm_sc_diag()
+        d.min_rho_A, d.min_rho_B, d.max_speed = 0.04, 0.04, 0.02
+        for k, v in kw.items():
+            setattr(d, k, v)
+        buf = np.frombuffer(bytes(d), dtype=np.float64)
+        assert buf.size == serving.DIAG_DOUBLES == ctypes.sizeof(lbm_sc.lbm_sc_diag) // 8
+        return buf
+
+    assert serving.check_of(row()) == (0.02, False)
+    assert serving.max_speed_of(row(max_speed=0.5)) == 0.5
+    assert serving.check_of(row(min_rho_A=-1e-4))[1]
+    assert serving.check_of(row(min_rho_B=0.0))[1]
+    assert serving.check_of(row(nonfinite=3.0))[1]
+    assert serving.check_of(row(min_rho_A=float("nan")))[1]
