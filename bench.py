@@ -18,7 +18,8 @@ drop with Guo forcing, Sec. 2.3), "fe" (the free-energy model of Sec. 2.2 on
 the same lattice), "pfm" (the phase-field model of Sec. 3 against the SC step
 on a 256^3 grid), "batch"
 (64 ragged D3Q19 lattices advanced by one launch per step against the same
-lattices stepped one at a time) and "serving" (a seeded Poisson stream of
+lattices stepped one at a time), "batch_rest16" (the same with the paired
+16-bit rest-offset storage) and "serving" (a seeded Poisson stream of
 drop-relaxation requests served with continuous batching against serial
 solves, p50/p99 time to result).  Under torchrun each rank advances its own
 lattice (independent replicas, no collective on the data path); the timed
@@ -273,9 +274,10 @@ def cpu_baseline(seconds: float, L: int = 128):
                             "sample": "D3Q19 %d^3 drop, 1 thread, %d steps in %.1f s" % (Ls, n1, el1)}}
 
 
-def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
+def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3, precision: str = "f32"):
     """Ragged batch against one-lattice-at-a-time on the same lattices: n
-    independent D3Q19 FP32 drop lattices, L from {32, 48, 64, 96, 128}, per
+    independent D3Q19 drop lattices (storage `precision`: FP32, or the paired
+    16-bit rest-offset words), L from {32, 48, 64, 96, 128}, per
     lattice G rho_tot in [2.2, 2.8], tau_A, tau_B in [0.6, 1.5], R in [L/8, L/3]
     at a random centre (inputs.ragged_drop_specs).  Serial: every lattice
     stepped alone with its own autotuned launch shape (tuned once per size),
@@ -292,7 +294,7 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
     with torch.cuda.stream(st):
         for sp in specs:
             rA, rB = inputs.spec_fields(sp, dtype=np.float32)
-            lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32",
+            lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], precision,
                                        stream=st).init(rA, rB))
         st.synchronize()
         N = sum(lat.N for lat in lats)
@@ -321,17 +323,19 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3):
         b.close()
     sizes = sorted({lat.shape[0] for lat in lats})
     traffic = None  # ncu DRAM bytes per LU of this launch shape on this workload, if the kernels are unchanged
-    if os.path.exists(TRAFFIC_FILE) and n == 64 and seed == 3 and (tile, zc) == (12, 16):
+    if os.path.exists(TRAFFIC_FILE) and n == 64 and seed == 3 and (tile, zc) == (12, 16) and precision == "f32":
         tf = json.load(open(TRAFFIC_FILE))
         if tf.get("batch_ragged64_f32", {}).get("source_hash") == kernel_source_hash():
             traffic = tf["batch_ragged64_f32"]["dram_bytes_per_lu"]
-    out = {"workload": "%d ragged D3Q19 FP32 drop lattices, L in %s, %.1fM nodes, seed %d" % (n, sizes, N / 1e6, seed),
+    storage = "FP32" if precision == "f32" else precision + " (FP32 arithmetic)"
+    out = {"workload": "%d ragged D3Q19 %s drop lattices, L in %s, %.1fM nodes, seed %d"
+                       % (n, storage, sizes, N / 1e6, seed),
            "nodes": N, "steps": steps, "batched_mlups": N / bat_ms / 1e3, "serial_mlups": N / ser_ms / 1e3,
            "batched_ms_per_step": bat_ms, "serial_ms_per_step": ser_ms, "speedup": ser_ms / bat_ms,
            "batch_launch": {"tile_id": tile, "tile": list(lbm_sc.BATCH_TILES[tile]), "tma": lbm_sc.BATCH_TILE_TMA[tile],
                             "zchunk": zc, "graph_steps": gs, "candidates": len(table)},
            "gpu_launches_per_step": {"batched": 1, "serial": n},
-           "dram_bytes_per_lu": traffic, "algorithmic_bytes_per_lu": 304}
+           "dram_bytes_per_lu": traffic, "algorithmic_bytes_per_lu": bytes_per_lu(precision)}
     del lats
     torch.cuda.empty_cache()
     return out
@@ -764,8 +768,10 @@ def main():
     pm = None
     if not args.no_pfm and rank == 0 and prec == "f32":
         pm = pfm_compare(256, max(10, K // 2), args.warmup)
+    bt16 = None
     if not args.no_batch and rank == 0:
         bt = batch_compare(args.batch_steps, args.warmup)
+        bt16 = batch_compare(args.batch_steps, args.warmup, precision="bf16_rest")
     sv = None
     if args.serve_requests > 0 and rank == 0:
         sv = serve_compare(args.serve_requests, args.serve_rate)
@@ -800,6 +806,8 @@ def main():
         line["e2e"] = e2e
     if bt is not None:
         line["batch"] = bt
+    if bt16 is not None:
+        line["batch_rest16"] = bt16
     if sv is not None:
         line["serving"] = sv
     if s16 is not None:

@@ -389,9 +389,15 @@ LBM_SC_API lbm_status lbm_sc_error_word(lbm_sc_handle* h, int* host_out);
  *           item, each lattice with its own tile: 64x4 if it is at least 64
  *           wide, else 32x8 (same requirements as 5); 10 = 32x12 and 11 =
  *           64x6 / 32x12 per lattice, the same with 384-thread CTAs (every
- *           lattice at least 32 x 12).  The TMA-fed tiles (3-6, 9-11) need
- *           every lattice on LBM_MODEL_SC with LBM_FORCING_SHIFT; the
- *           z-marching ones take lattices of any forcing and model, mixed.
+ *           lattice at least 32 x 12); 12 = each lattice in the one of 64x6,
+ *           48x8 and 32x12 with the least work per node for its size (384
+ *           threads, one CTA per item).  13 = the TMA-fed kernel for
+ *           LBM_F32_STORE_BF16_REST / LBM_F32_STORE_F16_REST (D3Q19, every
+ *           lattice at least 32 x 8): 32x8 tiles, two CTAs per SM, one CTA
+ *           per item.  The TMA-fed tiles (3-6, 9-13) need every lattice on
+ *           LBM_MODEL_SC with LBM_FORCING_SHIFT; in the TMA batches odd z
+ *           chunks march downwards (results unchanged); the z-marching ones
+ *           take lattices of any forcing and model, mixed.
  *   zchunk  z planes per work item (D3Q19; 0 = 32; capped at each nz)
  *   graph_steps  steps per captured graph (even, >= 0; 0 = no graphs) */
 typedef struct lbm_sc_batch lbm_sc_batch;

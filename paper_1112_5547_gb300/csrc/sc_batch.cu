@@ -108,12 +108,25 @@ cudaError_t launch_batch_tma_shape3(const void* lats, const BatchItem* items, in
     return cudaGetLastError();
 }
 
+template <class St>
+cudaError_t launch_batch_tma_rest(const void* lats, const BatchItem* items, int nitems, int parity, cudaStream_t st) {
+    using T = TmaTile<32, 8, 2, St>;
+    constexpr auto kern = sc_batch_tma_rest_kernel<St>;
+    const cudaError_t attr = dynamic_smem_once<kern>((int)T::smem_bytes);
+    if (attr != cudaSuccess) return attr;
+    if (nitems < 1) return cudaSuccess;
+    kern<<<(unsigned)nitems, 256, T::smem_bytes, st>>>(static_cast<const BatchTmaRestLattice<St>*>(lats), items,
+                                                        nitems, parity);
+    return cudaGetLastError();
+}
+
 template <class L, class S>
 cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int nitems, int parity, int sm_count,
                         int* ctr, cudaStream_t st) {
-    static_assert(kNumBatchTiles == 13 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
+    static_assert(kNumBatchTiles == 14 && kBatchTileX[6] == 64 && kBatchTileGrid[5] && kBatchTileTma[6] &&
                       !kBatchTileTma[7] && kBatchTileY[8] == 4 && kBatchTileMixed == 9 && kBatchTileY[10] == 12 &&
-                      kBatchTileMixed384 == 11 && kBatchTileShape3 == 12,
+                      kBatchTileMixed384 == 11 && kBatchTileShape3 == 12 && kBatchTileRest == 13 &&
+                      kBatchTileX[13] == 32 && kBatchTileY[13] == 8,
                   "batch tile table and dispatch disagree");
     switch (tile) {
         case 0: return launch_batch<L, S, 32, 8>(lats, items, nitems, parity, sm_count, ctr, false, st);
@@ -134,6 +147,9 @@ cudaError_t batch_typed(int tile, const void* lats, const BatchItem* items, int 
             case 12: return launch_batch_tma_shape3<2>(lats, items, nitems, parity, st);
         }
     }
+    if constexpr (std::is_same<L, D3Q19>::value && Codec<S>::kRest) {
+        if (tile == kBatchTileRest) return launch_batch_tma_rest<S>(lats, items, nitems, parity, st);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -151,6 +167,28 @@ cudaError_t batch_lat(int precision, int tile, const void* lats, const BatchItem
     return cudaErrorInvalidValue;
 }
 
+// Descriptor of batch tile 13: both parities' arguments and their population
+// and density maps (the boxes of the 32x8 rest-offset tile).
+template <class St>
+cudaError_t fill_rest(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, void* dst) {
+    using T = TmaTile<32, 8, 2, St>;
+    BatchTmaRestLattice<St> bl;
+    memset(&bl, 0, sizeof(bl));
+    const void* bufs[2] = {b0, b1};
+    for (int par = 0; par < 2; ++par) {
+        const int src = cur0 ^ par;
+        bl.a[par] = make_args<St>(p, bufs[src], const_cast<void*>(bufs[src ^ 1]));
+        bl.a[par].zchunk = zchunk;
+        cudaError_t e = encode_population_map(p, bl.a[par].fin, T::BX, T::BY, &bl.maps[par].pop, 3, T::E, T::Q2);
+        if (e == cudaSuccess)
+            e = encode_rho_map(p, rest_rho<D3Q19>(bl.a[par].fin, p.Np), T::RBX, T::RBY, &bl.maps[par].rho, 3);
+        if (e != cudaSuccess) return e;
+    }
+    bl.err = p.err;
+    memcpy(dst, &bl, sizeof(bl));
+    return cudaSuccess;
+}
+
 template <class S> void fill_typed(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, void* dst) {
     BatchLattice<S> bl;
     const void* bufs[2] = {b0, b1};
@@ -165,6 +203,9 @@ template <class S> void fill_typed(const Plan& p, const void* b0, const void* b1
 }  // namespace
 
 size_t batch_lattice_bytes(int precision, int tile) {
+    if (tile == kBatchTileRest)
+        return precision == 4 ? sizeof(BatchTmaRestLattice<bf16_rest>)
+                              : (precision == 5 ? sizeof(BatchTmaRestLattice<f16_rest>) : 0);
     if (tile >= 0 && tile < kNumBatchTiles && kBatchTileTma[tile]) return sizeof(BatchTmaLattice);
     switch (precision) {
         case 0: return sizeof(BatchLattice<double>);
@@ -180,6 +221,9 @@ size_t batch_lattice_bytes(int precision, int tile) {
 cudaError_t batch_lattice_fill(const Plan& p, const void* b0, const void* b1, int cur0, int zchunk, int tile,
                                void* dst) {
     if (!batch_tile_fits(tile, p)) return cudaErrorInvalidValue;
+    if (tile == kBatchTileRest)
+        return p.precision == 4 ? fill_rest<bf16_rest>(p, b0, b1, cur0, zchunk, dst)
+                                : fill_rest<f16_rest>(p, b0, b1, cur0, zchunk, dst);
     if (kBatchTileTma[tile]) {
         BatchTmaLattice bl;
         memset(&bl, 0, sizeof(bl));

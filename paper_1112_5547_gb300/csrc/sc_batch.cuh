@@ -292,4 +292,35 @@ __global__ void __launch_bounds__(384, 1)
     }
 }
 
+// Descriptor of one lattice of a rest-offset TMA batch (batch tile 13): the
+// population and density maps and the arguments of both parities.
+template <class St> struct BatchTmaRestLattice {
+    TmaMaps maps[2];
+    LatticeArgs<St> a[2];
+    int* err;
+};
+
+// Batch tile 13, one CTA per work item: the paired 16-bit rest-offset storage
+// through the TMA pipeline of the solo kernel's tile 43 (32x8 tiles, 2 stages,
+// two CTAs per SM at 128 registers), odd z chunks marching downwards.
+template <class St>
+__global__ void __launch_bounds__(256, 2)
+    sc_batch_tma_rest_kernel(const BatchTmaRestLattice<St>* __restrict__ lats, const BatchItem* __restrict__ items,
+                             int nitems, int parity) {
+    extern __shared__ unsigned char smem_raw[];
+    const int it = blockIdx.x;
+    if (it >= nitems) return;
+    const BatchItem w = items[it];
+    const BatchTmaRestLattice<St>* l = lats + w.lat;
+    const LatticeArgs<St> a = l->a[parity];
+    if (threadIdx.x == 0) {
+        tma_prefetch_map(&l->maps[parity].pop);
+        tma_prefetch_map(&l->maps[parity].rho);
+    }
+    TmaSmem<32, 8, 2, St> sm(smem_raw);
+    sm.init_barriers();
+    tma_item<32, 8, 2, St>(&l->maps[parity].pop, &l->maps[parity].rho, a, w.x0, w.y0, w.z0, 0u, sm, l->err, false,
+                           nullptr, TmaNoHook(), true);
+}
+
 }  // namespace lbmsc

@@ -23,17 +23,20 @@ struct BatchItem {
 // 64 wide, else 32x8 (kBatchTileX/Y give the narrow one); with 384 threads
 // (12 warps per SM, 2 stages): 10 = 32x12 TMA-fed one CTA per item, 11 = the
 // mixed form with 64x6 and 32x12; 12 = each lattice in the best of 64x6, 48x8
-// and 32x12 for its size (batch_shape3).
-constexpr int kNumBatchTiles = 13;
-constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32, 32, 32, 32};
-constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8, 12, 12, 12};
+// and 32x12 for its size (batch_shape3).  13 = the TMA-fed kernel for the
+// paired 16-bit rest-offset storages (D3Q19, lattices at least 32 x 8): 32x8
+// tiles, 2 stages, two CTAs per SM, one CTA per item (the solo tile 43 shape).
+constexpr int kNumBatchTiles = 14;
+constexpr int kBatchTileX[kNumBatchTiles] = {32, 32, 64, 32, 64, 32, 64, 32, 64, 32, 32, 32, 32, 32};
+constexpr int kBatchTileY[kNumBatchTiles] = {8, 4, 4, 8, 4, 8, 4, 8, 4, 8, 12, 12, 12, 8};
 constexpr bool kBatchTileTma[kNumBatchTiles] = {false, false, false, true, true, true, true,
-                                                false, false, true, true, true, true};
+                                                false, false, true, true, true, true, true};
 constexpr bool kBatchTileGrid[kNumBatchTiles] = {false, false, false, false, false, true, true,
-                                                 true, true, true, true, true, true};
+                                                 true, true, true, true, true, true, true};
 constexpr int kBatchTileMixed = 9;
 constexpr int kBatchTileMixed384 = 11;
 constexpr int kBatchTileShape3 = 12;
+constexpr int kBatchTileRest = 13;
 
 // The 384-thread tile shapes of batch tile 12, and the one a lattice takes:
 // the shape with the least work per node of the lattice, counting the padding
@@ -78,6 +81,9 @@ inline void batch_item_tile(int tile, const Plan& p, int& tx, int& ty) {
 inline bool batch_tile_fits(int tile, const Plan& p) {
     if (tile < 0 || tile >= kNumBatchTiles) return false;
     if (!kBatchTileTma[tile]) return true;  // the z-marching batch kernel chooses the collision at run time
+    if (tile == kBatchTileRest)
+        return p.lattice == 1 && rest_precision(p.precision) && p.forcing == kForcingShift && p.model == kModelSC &&
+               p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];
     if (!(p.lattice == 1 && p.precision == 1 && p.forcing == kForcingShift && p.model == kModelSC)) return false;
     if (tile == kBatchTileShape3) return batch_shape3(p) >= 0;
     return p.nx >= kBatchTileX[tile] && p.ny >= kBatchTileY[tile];

@@ -56,15 +56,17 @@ EXPORTS = (
 )
 
 # CTA tiles of the ragged-batch step (x columns by y columns); the TMA-fed ones
-# take D3Q19 lattices with FP32 storage at least one tile wide in x and y.
+# take D3Q19 lattices with FP32 storage at least one tile wide in x and y
+# (tile 13: the paired 16-bit rest-offset storages instead).
 # Persistent grids over an atomic work counter, or (GRID) one CTA per work item.
 # Tile 9 gives each lattice its own tile: 64x4 when it is at least 64 wide, else 32x8;
 # tiles 10 (32x12) and 11 (64x6 / 32x12 per lattice) run 384-thread CTAs.
 BATCH_TILES = ((32, 8), (32, 4), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (64, 4), (32, 8), (32, 12),
-               (32, 12), (32, 12))
-BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True, True, True, True)
-BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True, True, True, True)
+               (32, 12), (32, 12), (32, 8))
+BATCH_TILE_TMA = (False, False, False, True, True, True, True, False, False, True, True, True, True, True)
+BATCH_TILE_GRID = (False, False, False, False, False, True, True, True, True, True, True, True, True, True)
 BATCH_TILE_SHAPE3 = 12  # each lattice in the best of 64x6, 48x8, 32x12 for its size
+BATCH_TILE_REST = 13    # rest-offset 16-bit storage, 32x8 tiles, two CTAs per SM
 SHAPE3 = ((32, 12), (64, 6), (48, 8))
 
 
@@ -92,8 +94,8 @@ def batch_tile_fits(tile: int, lattice: "Lattice") -> bool:
         return True
     tx, ty = BATCH_TILES[tile]
     p = lattice.params
-    if not (p.lattice == LBM_D3Q19 and p.precision == LBM_F32 and p.forcing == LBM_FORCING_SHIFT
-            and p.model == LBM_MODEL_SC):
+    storage_ok = p.precision in REST_PRECISIONS if tile == BATCH_TILE_REST else p.precision == LBM_F32
+    if not (p.lattice == LBM_D3Q19 and storage_ok and p.forcing == LBM_FORCING_SHIFT and p.model == LBM_MODEL_SC):
         return False
     if tile == BATCH_TILE_SHAPE3:
         return batch_shape3(p.nx, p.ny) >= 0

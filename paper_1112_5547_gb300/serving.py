@@ -217,9 +217,10 @@ class Server:
         """(tile, zchunk) of a batch: the TMA-fed tiles with one CTA per work item and
         16-plane chunks when every lattice takes them (D3Q19, FP32): 384-thread
         64x6 / 32x12 per lattice (at least 32 x 12), else 32x8 (at least 32 x 8);
+        for the rest-offset 16-bit storages the 32x8 TMA tile (at least 32 x 8);
         otherwise the persistent 32 x 4 z-marching one (the fastest on ragged D2Q9
         batches: 28 GLUPS on 32 lattices of 64^2 .. 1024^2 against 21 one at a time)."""
-        for tile in (11, 5):
+        for tile in (11, 5, lbm_sc.BATCH_TILE_REST):
             if all(lbm_sc.batch_tile_fits(tile, lat) for lat in lats):
                 return tile, 16
         return 1, 0

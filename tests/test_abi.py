@@ -219,11 +219,27 @@ def test_batch_workspace_and_validation(lib):
         assert lib.lbm_sc_batch_workspace_bytes(hs, len(lib.BATCH_TILES), 0) == 0
         for t in range(len(lib.BATCH_TILES)):
             tma = lib.BATCH_TILE_TMA[t]
+            if t == lib.BATCH_TILE_REST:  # rest-offset storage only: no FP32 set fits
+                assert all(lib.lbm_sc_batch_workspace_bytes(x, t, 0) == 0 for x in (hs, hs[1:], hs[2:]))
+                continue
             # TMA-fed tiles need every lattice at least one tile wide (nx = 24 < 32 here)
             assert (lib.lbm_sc_batch_workspace_bytes(hs, t, 0) == 0) == tma
             assert lib.lbm_sc_batch_workspace_bytes(hs[2:], t, 0) > 0
             fits = not tma or lib.BATCH_TILES[t][0] <= 9
             assert (lib.lbm_sc_batch_workspace_bytes(hs[1:], t, 0) > 0) == fits  # nx = 9
+        # the rest-offset TMA tile takes rest-offset lattices at least 32 x 8 (and nothing narrower)
+        pr = [lib.make_params(lib.LBM_D3Q19, s, 1.0, 0.8, 2.0, prec) for s, prec in
+              (((16, 8, 32), "bf16_rest"), ((16, 8, 24), "bf16_rest"), ((16, 8, 32), "f16_rest"))]
+        hr = [lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0) for p in pr]
+        try:
+            assert lib.lbm_sc_batch_workspace_bytes(hr[:1], lib.BATCH_TILE_REST, 0) > 0
+            assert lib.lbm_sc_batch_workspace_bytes(hr[2:], lib.BATCH_TILE_REST, 0) > 0
+            assert lib.lbm_sc_batch_workspace_bytes(hr[:2], lib.BATCH_TILE_REST, 0) == 0  # 24 columns
+            assert lib.lbm_sc_batch_workspace_bytes([hr[0], hr[2]], lib.BATCH_TILE_REST, 0) == 0  # two storages
+            assert lib.lbm_sc_batch_workspace_bytes(hr[:1], 12, 0) == 0  # the FP32 TMA tiles take no 16-bit words
+        finally:
+            for h in hr:
+                lib.lbm_sc_destroy(h)
         assert lib.lbm_sc_batch_workspace_bytes(hs, -1, 0) == 0
         assert lib.lbm_sc_batch_workspace_bytes(hs, 0, -1) == 0
         assert lib.lbm_sc_batch_workspace_bytes([], 0, 0) == 0

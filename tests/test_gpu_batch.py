@@ -68,6 +68,7 @@ def _assert_same(a, b, what):
 @pytest.mark.parametrize("lattice,mix,precision", [(1, MIX3, "f32"), (0, MIX2, "f64"), (1, MIX3, "bf16"),
                                                    (0, MIX2, "f16"), (1, MIX3_TMA, "f32"),
                                                    (1, MIX3, "bf16_rest"), (0, MIX2, "f16_rest"),
+                                                   (1, MIX3_TMA, "bf16_rest"), (1, MIX3_TMA, "f16_rest"),
                                                    (1, MIX3_MIXED, "f32"), (1, MIX3_TALL, "f32"),
                                                    (1, MIX3_SHAPE3, "f32")])
 def test_batch_equals_solo(sc, lattice, mix, precision):
@@ -77,9 +78,13 @@ def test_batch_equals_solo(sc, lattice, mix, precision):
         lat.step(steps)
     ref = [_state(lat) for lat in solo]
     tiles = [t for t in range(len(sc.BATCH_TILES)) if all(sc.batch_tile_fits(t, lat) for lat in solo)]
-    if mix is MIX3_TMA:  # every tile of at most 8 rows (one lattice is 8 tall), and tile 12 (48x8 for it)
+    if mix is MIX3_TMA and precision == "f32":
+        # every FP32 tile of at most 8 rows (one lattice is 8 tall), and tile 12 (48x8 for it)
+        assert tiles == [t for t in range(len(sc.BATCH_TILES)) if t != sc.BATCH_TILE_REST
+                         and (sc.BATCH_TILES[t][1] <= 8 or t == sc.BATCH_TILE_SHAPE3)]
+    if mix is MIX3_TMA and precision.endswith("_rest"):  # the z-marching tiles and the rest-offset TMA tile
         assert tiles == [t for t in range(len(sc.BATCH_TILES))
-                         if sc.BATCH_TILES[t][1] <= 8 or t == sc.BATCH_TILE_SHAPE3]
+                         if not sc.BATCH_TILE_TMA[t] or t == sc.BATCH_TILE_REST]
     if mix is MIX3_SHAPE3:
         assert sc.BATCH_TILE_SHAPE3 in tiles
         assert sorted(sc.batch_shape3(shape[2], shape[1]) for shape, *_ in mix[:3]) == [0, 1, 2]
