@@ -216,6 +216,35 @@ def test_ragged_batch_full_size(sc, oracle_mod):
     torch.cuda.empty_cache()
 
 
+def test_ragged_batch_rest16_full_size(sc):
+    """The bench's 64 ragged lattices in paired bf16 rest-offset storage:
+    batched on the rest-offset TMA tile (13: 32x8, one CTA per item, 32-plane
+    chunks with odd chunks marching downwards, graph chunks of 8) equals every
+    lattice stepped alone bitwise after 16 steps."""
+    import torch
+    specs = inputs.ragged_drop_specs()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        mk = lambda sp: sc.Lattice(1, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "bf16_rest",
+                                   stream=stream).init(*inputs.spec_fields(sp, dtype=np.float32))
+        ref = []
+        for sp in specs:
+            lat = mk(sp)
+            lat.step(16)
+            ref.append([t.cpu().numpy() for t in lat.moments()])
+            lat.close()
+        lats = [mk(sp) for sp in specs]
+        assert all(sc.batch_tile_fits(sc.BATCH_TILE_REST, lat) for lat in lats)
+        b = sc.Batch(lats, tile=sc.BATCH_TILE_REST, zchunk=32, graph_steps=8, stream=stream)
+        b.step(16)
+        stream.synchronize()
+        b.close()
+        for k, lat in enumerate(lats):
+            for x, y in zip((t.cpu().numpy() for t in lat.moments()), ref[k]):
+                assert np.array_equal(x, y), k
+    torch.cuda.empty_cache()
+
+
 def test_128_drop_whole_field_vs_oracle(sc, oracle_mod):
     L, steps = 128, 100
     f = inputs.drop((L, L, L), L / 4, seed=2)
