@@ -101,7 +101,7 @@ def profile_case(a):
                      in --precision, --tile / --zchunk, solo steps
       step2d         the same on an L^2 D2Q9 lattice
       solo_vs_batch  the D3Q19 drop stepped twice alone, then twice as a batch of one
-      ragged         the ragged batch (inputs.ragged_drop_specs, --ragged-n lattices), --batch-tile
+      ragged         the ragged batch (inputs.ragged_drop_specs, --ragged-n lattices, --precision), --batch-tile
       pfm            the phase-field solver (FP32) on an L^3 drop (rho_A 1.2 / rho_B 0.2,
                      tau 0.6, g 0.3, dt 0.1)
 
@@ -144,7 +144,7 @@ def profile_case(a):
             lats = []
             for sp in inputs.ragged_drop_specs(n=a.ragged_n):
                 rA, rB = inputs.spec_fields(sp, dtype=np.float32)
-                lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], "f32",
+                lats.append(lbm_sc.Lattice(lbm_sc.LBM_D3Q19, sp["shape"], sp["tau_A"], sp["tau_B"], sp["G"], a.precision,
                                            stream=st).init(rA, rB))
             print("ragged batch: %d lattices, %d nodes" % (len(lats), sum(x.N for x in lats)))
             b = lbm_sc.Batch(lats, tile=a.batch_tile, zchunk=a.zchunk, stream=st)
@@ -323,10 +323,15 @@ def batch_compare(steps: int, warmup: int, n: int = 64, seed: int = 3, precision
         b.close()
     sizes = sorted({lat.shape[0] for lat in lats})
     traffic = None  # ncu DRAM bytes per LU of this launch shape on this workload, if the kernels are unchanged
-    if os.path.exists(TRAFFIC_FILE) and n == 64 and seed == 3 and (tile, zc) == (12, 16) and precision == "f32":
+    # the captured launches: FP32 on batch tile 12 with 16-plane chunks, bf16 rest-offset
+    # on tile 13 with 32-plane chunks (zchunk 0 means 32)
+    captured = {"f32": (12, 16), "bf16_rest": (13, 32)}
+    key = "batch_ragged64_%s" % precision
+    if (os.path.exists(TRAFFIC_FILE) and n == 64 and seed == 3 and precision in captured
+            and (tile, zc or 32) == captured[precision]):
         tf = json.load(open(TRAFFIC_FILE))
-        if tf.get("batch_ragged64_f32", {}).get("source_hash") == kernel_source_hash():
-            traffic = tf["batch_ragged64_f32"]["dram_bytes_per_lu"]
+        if tf.get(key, {}).get("source_hash") == kernel_source_hash():
+            traffic = tf[key]["dram_bytes_per_lu"]
     storage = "FP32" if precision == "f32" else precision + " (FP32 arithmetic)"
     out = {"workload": "%d ragged D3Q19 %s drop lattices, L in %s, %.1fM nodes, seed %d"
                        % (n, storage, sizes, N / 1e6, seed),
