@@ -418,3 +418,33 @@ def test_tuning_cache_keys_separate_the_collisions(lib):
     keys = {autotune.cache_key(Fake()), autotune.cache_key(Fake(forcing="guo")),
             autotune.cache_key(Fake(model=lib.LBM_MODEL_FE, kappa=0.05, gamma=1.0))}
     assert keys == {"D3Q19/f32/64x64x64", "D3Q19/f32/64x64x64/guo", "D3Q19/f32/64x64x64/fe"}
+
+
+def test_batch_tile_rule_mirror_matches_the_library(lib):
+    """The binding's batch_tile_fits (used by the autotuner and the server)
+    gives the library's answer (a batch workspace size above zero) for every
+    batch tile, on lattices of both kinds, every storage precision, a range of
+    sizes, and the forcing schemes and models the TMA tiles exclude."""
+    import types
+    shapes = [(8, 8, 8), (16, 8, 32), (16, 12, 32), (16, 8, 24), (20, 6, 64), (10, 12, 64), (9, 12, 48),
+              (12, 40, 96), (8, 64, 128), (16, 16), (64, 64)]
+    checked = 0
+    for prec in lib.PRECISIONS:
+        for shape in shapes:
+            kind = lib.LBM_D3Q19 if len(shape) == 3 else lib.LBM_D2Q9
+            for forcing, model in (("shift", lib.LBM_MODEL_SC), ("guo", lib.LBM_MODEL_SC),
+                                   ("shift", lib.LBM_MODEL_FE)):
+                p = lib.make_params(kind, shape, 1.0, 0.9, 2.0, prec, forcing=forcing, model=model, gamma=0.5)
+                ws = lib.lbm_sc_workspace_bytes(p)
+                if ws == 0:  # a combination the library does not take (the FE model stores FP32 / FP64 only)
+                    assert model == lib.LBM_MODEL_FE and prec not in ("f32", "f64")
+                    continue
+                h = lib.lbm_sc_create(p, 256 * 1024, ws, 0)
+                try:
+                    for t in range(len(lib.BATCH_TILES)):
+                        fits = lib.lbm_sc_batch_workspace_bytes([h], t, 0) > 0
+                        assert lib.batch_tile_fits(t, types.SimpleNamespace(params=p)) == fits, (prec, shape, t)
+                        checked += fits
+                finally:
+                    lib.lbm_sc_destroy(h)
+    assert checked > 100
