@@ -448,3 +448,31 @@ def test_batch_tile_rule_mirror_matches_the_library(lib):
                 finally:
                     lib.lbm_sc_destroy(h)
     assert checked > 100
+
+
+def test_tma_box_origins_are_16_byte_aligned(lib):
+    """Every tensor copy the TMA kernels issue starts its x coordinate on a
+    16-byte boundary (the hardware's rule; an unaligned one is an illegal
+    instruction): the population box of a tile at x0 starts at x0 + ghost_x - 16
+    bytes of values and the density box of the rest-offset storages at node
+    x0 + ghost_x - 2 (two floats a node), for every TMA tile (solo and batch),
+    storage precision and lattice width, with the library's own geometry."""
+    widths = (32, 33, 40, 48, 63, 64, 65, 70, 96, 127, 128, 130, 512)
+    solo = {t for t, k in enumerate(lib.TILE_KIND) if k in (5, 6)}
+    tile_x = {lib.TILES[t][0] for t in solo} | {lib.BATCH_TILES[t][0] for t in range(len(lib.BATCH_TILES))
+                                                 if lib.BATCH_TILE_TMA[t]} | {x for x, _ in lib.SHAPE3}
+    for prec in ("f32", "bf16", "f16", "bf16_rest", "f16_rest"):
+        for nx in widths:
+            p = lib.make_params(lib.LBM_D3Q19, (16, 12, nx), 1.0, 1.0, 2.0, prec)
+            h = lib.lbm_sc_create(p, 256 * 1024, lib.lbm_sc_workspace_bytes(p), 0)
+            try:
+                e, q, px, py, gx, gy, _ = lib.lbm_sc_layout(h)
+            finally:
+                lib.lbm_sc_destroy(h)
+            assert (px * e) % 16 == 0
+            pad = 16 // e
+            for tx in tile_x:
+                for x0 in range(0, nx, tx):
+                    assert ((x0 + gx - pad) * e) % 16 == 0, (prec, nx, tx, x0)
+                    if prec.endswith("_rest"):
+                        assert (2 * (x0 + gx - 2) * 4) % 16 == 0, (prec, nx, tx, x0)
