@@ -26,14 +26,17 @@ def test_poisson_stream_is_seeded_and_in_range():
 def test_footprint_is_the_workspace_and_the_batch_share():
     """A request's footprint is its workspace plus a bound on its share of the batch
     workspace, and that bound covers lbm_sc_batch_workspace_bytes for every batch
-    tile the request's lattice takes (handles are host-only: no GPU needed)."""
+    tile the request's lattice takes, FP32 and rest-offset storage alike (handles
+    are host-only: no GPU needed)."""
     from paper_1112_5547_gb300 import lbm_sc, serving
     r = serving.poisson_requests(1, seed=1, d3_fraction=1.0, sizes3=(192,))[0]
     p = lbm_sc.make_params(r.lattice, r.shape, r.tau_A, r.tau_B, r.G, "f32")
     assert serving.Server.footprint(r) == lbm_sc.lbm_sc_workspace_bytes(p) + serving.Server.batch_share(r)
     # the largest D3Q19 request: two FP32 buffers of 2 x 19 values per node
     assert serving.Server.footprint(r) >= 2 * 2 * 19 * 4 * 192 ** 3
-    for req in serving.poisson_requests(12, seed=2, sizes2=(64, 1024), sizes3=(32, 40, 192)):
+    reqs = [q for prec in ("f32", "bf16_rest", "f16_rest")
+            for q in serving.poisson_requests(12, seed=2, sizes2=(64, 1024), sizes3=(32, 40, 192), precision=prec)]
+    for req in reqs:
         q = lbm_sc.make_params(req.lattice, req.shape, req.tau_A, req.tau_B, req.G, req.precision)
         h = lbm_sc.lbm_sc_create(q, 256 * 1024, lbm_sc.lbm_sc_workspace_bytes(q), 0)
         try:
